@@ -1,0 +1,217 @@
+"""CPU oracle for the Panther / Panther++ hot path (TEST INFRASTRUCTURE ONLY).
+
+Plain, slow, single-threaded C (``panther_oracle.c``) behind ctypes. Only the
+tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may
+import this package; the product path never does, and shares no code with it.
+
+Every function states the passage of the paper it follows (arXiv 1504.02577):
+Algorithm 3 (path generation), Eq. (3) (transition probabilities), the
+inverted index of Sec. 3.1, Algorithm 1 with Eq. (4) (counting + top-k),
+Sec. 3.3 / Algorithm 2 (Panther++ vectors and nearest neighbours) and the
+sample-size bound of Sec. 3.2 (Theorem 1 with Lemma 1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "panther_oracle.c")
+_LIB = os.path.join(_HERE, "_liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PREFIX, ALIAS = 0, 1
+
+
+def build() -> str:
+    """Compile the oracle with plain gcc (no fast-math, no vectorisation tricks)."""
+    if os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            vp, i64, u64, u32, i32, dbl, ci = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64,
+                                               ctypes.c_uint32, ctypes.c_int32, ctypes.c_double,
+                                               ctypes.c_int)
+            sig = {
+                "po_philox4x32_10": ([vp, vp, vp], None),
+                "po_draw": ([u64, u32, u64, u32, u32, vp], None),
+                "po_lemire": ([u64, u64, vp], ci),
+                "po_sample_size": ([dbl, dbl, dbl, ci], i64),
+                "po_select_prefix": ([vp, i64, u64], i64),
+                "po_alias_row": ([vp, i64, vp, vp], None),
+                "po_select_alias": ([vp, vp, i64, u64, u64], i64),
+                "po_alias_tables": ([i64, vp, vp, vp, vp], None),
+                "po_sample_paths": ([i64, vp, vp, vp, vp, vp, u64, i64, i64, ci, ci, vp], ci),
+                "po_build_index": ([i64, i64, ci, vp, vp, vp], i64),
+                "po_topk": ([i64, ci, vp, vp, vp, i32, ci, vp, vp, vp], i64),
+                "po_theta": ([i64, ci, vp, vp, vp, i32, ci, vp, vp], None),
+                "po_dist2": ([vp, vp, ci, vp], ci),
+                "po_knn": ([i64, ci, vp, i32, ci, vp, vp], ci),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray | None) -> int | None:
+    return None if a is None else a.ctypes.data
+
+
+# ---------------------------------------------------------------- RNG ---
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.empty(4, dtype=np.uint32)
+    _load().po_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def draw(seed: int, stream: int, r: int, t: int, attempt: int = 0) -> np.ndarray:
+    out = np.empty(4, dtype=np.uint32)
+    _load().po_draw(seed, stream, r, t, attempt, _p(out))
+    return out
+
+
+def lemire(U: int, S: int):
+    out = np.zeros(1, dtype=np.uint64)
+    ok = _load().po_lemire(U, S, _p(out))
+    return bool(ok), int(out[0])
+
+
+def sample_size(eps: float, delta: float, c: float, T: int) -> int:
+    """Sec. 3.2: R = ceil(c/eps^2 (log2 C(T,2) + 1 + ln 1/delta)); -1 if undefined."""
+    return int(_load().po_sample_size(eps, delta, c, T))
+
+
+# ---------------------------------------------------------- selection ---
+def select_prefix(w: np.ndarray, x: int) -> int:
+    w = np.ascontiguousarray(w, dtype=np.uint32)
+    return int(_load().po_select_prefix(_p(w), w.shape[0], x))
+
+
+def alias_row(w: np.ndarray):
+    w = np.ascontiguousarray(w, dtype=np.uint32)
+    thr = np.empty(w.shape[0], dtype=np.uint64)
+    al = np.empty(w.shape[0], dtype=np.int32)
+    _load().po_alias_row(_p(w), w.shape[0], _p(thr), _p(al))
+    return thr, al
+
+
+def select_alias(thr: np.ndarray, al: np.ndarray, c: int, u: int) -> int:
+    return int(_load().po_select_alias(_p(thr), _p(al), thr.shape[0], c, u))
+
+
+def alias_tables(g):
+    thr = np.zeros(max(g.m, 1), dtype=np.uint64)
+    al = np.zeros(max(g.m, 1), dtype=np.int32)
+    _load().po_alias_tables(g.n, _p(g.row_ptr), _p(g.w), _p(thr), _p(al))
+    return thr, al
+
+
+# -------------------------------------------------------------- paths ---
+def sample_paths(g, seed: int, R: int, T: int, mode: int = PREFIX, r0: int = 0, tables=None) -> np.ndarray:
+    """Algorithm 3: paths r0 .. r0+R-1 as int32[R][T+1]."""
+    lib = _load()
+    thr = al = None
+    if mode == ALIAS:
+        thr, al = tables if tables is not None else alias_tables(g)
+    out = np.empty((R, T + 1), dtype=np.int32)
+    col = g.col if g.m else np.zeros(1, np.int32)
+    w = g.w if g.m else np.zeros(1, np.uint32)
+    rc = lib.po_sample_paths(g.n, _p(g.row_ptr), _p(col), _p(w), _p(thr), _p(al),
+                             seed, r0, r0 + R, T, mode, _p(out))
+    if rc != 0:
+        raise ValueError("po_sample_paths: bad arguments")
+    return out
+
+
+def build_index(n: int, paths: np.ndarray):
+    """Sec. 3.1 inverted index: (off int64[n+1], pid int32[nnz])."""
+    lib = _load()
+    paths = np.ascontiguousarray(paths, dtype=np.int32)
+    R, L = paths.shape
+    off = np.empty(n + 1, dtype=np.int64)
+    nnz = lib.po_build_index(n, R, L, _p(paths), _p(off), None)
+    pid = np.empty(max(nnz, 1), dtype=np.int32)
+    lib.po_build_index(n, R, L, _p(paths), _p(off), _p(pid))
+    return off, pid[:nnz]
+
+
+class Oracle:
+    """Counting / top-k / theta over one (paths, index) pair, with reusable work space."""
+
+    def __init__(self, n: int, paths: np.ndarray, off: np.ndarray | None = None, pid: np.ndarray | None = None):
+        self.n = n
+        self.paths = np.ascontiguousarray(paths, dtype=np.int32)
+        self.L = self.paths.shape[1]
+        if off is None:
+            off, pid = build_index(n, self.paths)
+        self.off, self.pid = off, (pid if pid.shape[0] else np.zeros(1, np.int32))
+        self._work = np.zeros(n, dtype=np.uint32)
+        self._lib = _load()
+
+    def topk(self, v: int, k: int):
+        """Algorithm 1 + Eq. (4): top-k (ids, counts) by (count desc, id asc)."""
+        ids = np.empty(k, dtype=np.int32)
+        cnt = np.empty(k, dtype=np.uint32)
+        self._lib.po_topk(self.n, self.L, _p(self.paths), _p(self.off), _p(self.pid), int(v), k,
+                          _p(self._work), _p(ids), _p(cnt))
+        return ids, cnt
+
+    def topk_many(self, queries, k: int):
+        q = np.asarray(queries)
+        ids = np.empty((q.shape[0], k), dtype=np.int32)
+        cnt = np.empty((q.shape[0], k), dtype=np.uint32)
+        for i, v in enumerate(q):
+            ids[i], cnt[i] = self.topk(int(v), k)
+        return ids, cnt
+
+    def theta(self, v: int, D: int) -> np.ndarray:
+        """Sec. 3.3: the D largest counts of v (excluding v), descending, zero-padded."""
+        out = np.empty(D, dtype=np.uint32)
+        self._lib.po_theta(self.n, self.L, _p(self.paths), _p(self.off), _p(self.pid), int(v), D,
+                           _p(self._work), _p(out))
+        return out
+
+    def theta_all(self, D: int) -> np.ndarray:
+        out = np.empty((self.n, D), dtype=np.uint32)
+        for v in range(self.n):
+            out[v] = self.theta(v, D)
+        return out
+
+
+def dist2(a: np.ndarray, b: np.ndarray) -> int:
+    a = np.ascontiguousarray(a, dtype=np.uint32)
+    b = np.ascontiguousarray(b, dtype=np.uint32)
+    out = np.zeros(1, dtype=np.uint64)
+    if _load().po_dist2(_p(a), _p(b), a.shape[0], _p(out)) != 0:
+        raise OverflowError("squared distance exceeds 64 bits")
+    return int(out[0])
+
+
+def knn(theta: np.ndarray, v: int, k: int):
+    """Sec. 3.3 / Algorithm 2: k nearest u != v by (squared L2 asc, id asc)."""
+    theta = np.ascontiguousarray(theta, dtype=np.uint32)
+    n, D = theta.shape
+    ids = np.empty(k, dtype=np.int32)
+    d2 = np.empty(k, dtype=np.uint64)
+    if _load().po_knn(n, D, _p(theta), int(v), k, _p(ids), _p(d2)) != 0:
+        raise OverflowError("squared distance exceeds 64 bits")
+    return ids, d2

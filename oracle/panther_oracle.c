@@ -1,0 +1,344 @@
+/*
+ * Panther / Panther++ CPU ORACLE.
+ *
+ * TEST INFRASTRUCTURE ONLY. This is the plain, slow, single-threaded
+ * statement of what the GPU path computes. Only the tests, the smoke check
+ * and the benchmark's CPU-baseline leg may load it; the product path never
+ * calls it and shares no code, header, table or constant with it.
+ *
+ * Paper: Zhang, Tang, Ma, Tong, Jing, Li, "Panther: Fast Top-k Similarity
+ * Search in Large Networks" (arXiv 1504.02577, KDD 2015).
+ *
+ * What each function follows:
+ *   po_sample_size      Theorem 1 with Lemma 1 ("Sample Size Guarantee", Sec. 3.2)
+ *   po_select_prefix    Eq. (3) transition probability t_ij = w_ij / sum_k w_ik
+ *   po_alias_row        Eq. (3), realised by an exact integer alias table
+ *   po_sample_paths     Algorithm 3 (GenerateRandomPath), Sec. 3.1
+ *   po_build_index      the vertex-to-path inverted index P_v (Sec. 3.1, Alg. 3)
+ *   po_topk             Algorithm 1 (count each unique co-occurring vertex of
+ *                       every path in P_v once), Eq. (4), then top-k
+ *   po_theta            Sec. 3.3 feature vector theta(v): the D largest S_RP
+ *   po_knn              Sec. 3.3 S_RP++ = 1 / ||theta(v_i) - theta(v_j)||
+ *
+ * Readings of points the paper leaves open (kept identical on both sides):
+ *   - exactly R paths of exactly T+1 vertices (the loop conditions printed in
+ *     Algorithm 3 are inverted);
+ *   - P_v is a set: a path that visits v twice is listed once;
+ *   - the query vertex itself is not a candidate (top-k ranks the OTHER
+ *     vertices); theta excludes it too;
+ *   - a vertex with no neighbour keeps the walk where it is (the draw for that
+ *     step is still consumed, so later steps keep their counters);
+ *   - ranking is by integer count desc, then vertex id asc (count/R orders the
+ *     same); k-NN ranks by exact squared distance asc, then id asc;
+ *   - fewer than k candidates: pad with id -1 (count 0, or distance UINT64_MAX);
+ *   - R is rounded up.
+ *
+ * Random draws: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written
+ * here from its published definition. Draw (r, t, attempt) of stream s uses
+ *   key = (lo32(seed), hi32(seed)), counter = (lo32(r), hi32(r), (s<<16)|t, attempt)
+ * and Uniform[0,S) is Lemire's multiply-shift with rejection (ACM TOMACS
+ * 2019): U = x0 | x1<<32, m = U*S (128-bit); reject if low64(m) < 2^64 mod S
+ * (then attempt+1), else return high64(m).
+ *
+ * Parity pins (what holds this file to something other than itself): see the
+ * CPU tests. Philox itself has no CPU pin beyond bijectivity and uniformity;
+ * its pin is the GPU cross-check against curand's Philox4_32_10.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+typedef unsigned __int128 po_u128;
+
+/* ------------------------------------------------------------- Philox --- */
+void po_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* The four words of draw (r, t, attempt) on stream s. */
+void po_draw(uint64_t seed, uint32_t stream, uint64_t r, uint32_t t, uint32_t attempt, uint32_t out[4]) {
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t ctr[4] = { (uint32_t)r, (uint32_t)(r >> 32), (stream << 16) | t, attempt };
+    po_philox4x32_10(ctr, key, out);
+}
+
+/* Lemire: returns 1 and sets *out if U is accepted for range S (S >= 1). */
+int po_lemire(uint64_t U, uint64_t S, uint64_t* out) {
+    po_u128 m = (po_u128)U * S;
+    uint64_t lo = (uint64_t)m;
+    if (lo < S) {
+        uint64_t thr = (0 - S) % S;            /* (2^64 - S) mod S = 2^64 mod S */
+        if (lo < thr) return 0;
+    }
+    *out = (uint64_t)(m >> 64);
+    return 1;
+}
+
+/* ------------------------------------------------------ sample size R --- */
+/* Theorem 1: |S| = c/eps^2 (d + ln 1/delta); Lemma 1: d = log2 C(T,2) + 1.
+ * Returns -1 when the formula is undefined (T < 2 or parameters out of range). */
+int64_t po_sample_size(double eps, double delta, double c, int T) {
+    if (!(eps > 0 && eps < 1) || !(delta > 0 && delta < 1) || !(c > 0) || T < 2) return -1;
+    double pairs = (double)T * (double)(T - 1) / 2.0;         /* C(T, 2) */
+    double d = log2(pairs) + 1.0;
+    double R = c / (eps * eps) * (d + log(1.0 / delta));
+    return (int64_t)ceil(R);
+}
+
+/* ------------------------------------------------------------ Eq. (3) --- */
+/* Prefix selection: the unique j with sum_{i<j} w_i <= x < sum_{i<=j} w_i,
+ * for x drawn uniformly in [0, sum w). Linear scan. */
+int64_t po_select_prefix(const uint32_t* w, int64_t d, uint64_t x) {
+    uint64_t acc = 0;
+    for (int64_t j = 0; j < d; ++j) {
+        acc += w[j];
+        if (x < acc) return j;
+    }
+    return -1;
+}
+
+/* Integer alias table of one row (Vose): q_j = w_j * d, every column holds
+ * capacity S = sum w. Worklists are filled in ascending j; each step takes the
+ * LAST small and the LAST large entry; leftovers get thr = S, alias = self.
+ * Column c with coin u in [0,S) selects c if u < thr[c], else alias[c]. */
+void po_alias_row(const uint32_t* w, int64_t d, uint64_t* thr, int32_t* alias) {
+    uint64_t S = 0;
+    for (int64_t j = 0; j < d; ++j) S += w[j];
+    uint64_t* q = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(d > 0 ? d : 1));
+    int64_t* small = (int64_t*)malloc(sizeof(int64_t) * (size_t)(d > 0 ? d : 1));
+    int64_t* large = (int64_t*)malloc(sizeof(int64_t) * (size_t)(d > 0 ? d : 1));
+    int64_t ns = 0, nl = 0;
+    for (int64_t j = 0; j < d; ++j) {
+        q[j] = (uint64_t)w[j] * (uint64_t)d;
+        if (q[j] < S) small[ns++] = j; else large[nl++] = j;
+    }
+    while (ns > 0 && nl > 0) {
+        int64_t s = small[--ns];
+        int64_t l = large[--nl];
+        thr[s] = q[s];
+        alias[s] = (int32_t)l;
+        q[l] -= S - q[s];
+        if (q[l] < S) small[ns++] = l; else large[nl++] = l;
+    }
+    while (nl > 0) { int64_t l = large[--nl]; thr[l] = S; alias[l] = (int32_t)l; }
+    while (ns > 0) { int64_t s = small[--ns]; thr[s] = S; alias[s] = (int32_t)s; }
+    free(q); free(small); free(large);
+}
+
+int64_t po_select_alias(const uint64_t* thr, const int32_t* alias, int64_t d, uint64_t c, uint64_t u) {
+    if ((int64_t)c >= d) return -1;
+    return u < thr[c] ? (int64_t)c : (int64_t)alias[c];
+}
+
+/* Alias tables of every row, in CSR order. */
+void po_alias_tables(int64_t n, const int64_t* row_ptr, const uint32_t* w, uint64_t* thr, int32_t* alias) {
+    for (int64_t v = 0; v < n; ++v) {
+        int64_t s = row_ptr[v], d = row_ptr[v + 1] - s;
+        if (d > 0) po_alias_row(w + s, d, thr + s, alias + s);
+    }
+}
+
+/* ------------------------------------------------------- Algorithm 3 --- */
+/* Paths r0..r1-1, each T+1 vertices, written row-major to out[(r-r0)*(T+1)+i].
+ * mode 0 = prefix selection, 1 = alias selection (thr/alias from
+ * po_alias_tables; ignored in prefix mode). Returns 0, or -1 on bad input. */
+int po_sample_paths(int64_t n, const int64_t* row_ptr, const int32_t* col, const uint32_t* w,
+                    const uint64_t* thr, const int32_t* alias,
+                    uint64_t seed, int64_t r0, int64_t r1, int T, int mode, int32_t* out) {
+    if (n < 1 || T < 0 || T > 65535 || (mode != 0 && mode != 1)) return -1;
+    int L = T + 1;
+    for (int64_t r = r0; r < r1; ++r) {
+        int32_t* p = out + (r - r0) * L;
+        uint32_t x[4];
+        uint64_t v = 0;
+        /* start vertex: uniform over V (Alg. 3, "sample current vertex uniformly") */
+        for (uint32_t att = 0;; ++att) {
+            po_draw(seed, 0, (uint64_t)r, 0, att, x);
+            uint64_t U = (uint64_t)x[0] | ((uint64_t)x[1] << 32);
+            if (po_lemire(U, (uint64_t)n, &v)) break;
+        }
+        p[0] = (int32_t)v;
+        /* T steps, each to a neighbour with probability t_ij (Eq. 3) */
+        for (int t = 1; t <= T; ++t) {
+            int64_t s = row_ptr[v], d = row_ptr[v + 1] - s;
+            if (d == 0) { p[t] = (int32_t)v; continue; }    /* isolated: stay put */
+            uint64_t S = 0;
+            for (int64_t j = 0; j < d; ++j) S += w[s + j];
+            int64_t j = -1;
+            for (uint32_t att = 0;; ++att) {
+                po_draw(seed, 0, (uint64_t)r, (uint32_t)t, att, x);
+                uint64_t U0 = (uint64_t)x[0] | ((uint64_t)x[1] << 32);
+                if (mode == 0) {
+                    uint64_t xr;
+                    if (!po_lemire(U0, S, &xr)) continue;
+                    j = po_select_prefix(w + s, d, xr);
+                    break;
+                } else {
+                    uint64_t U1 = (uint64_t)x[2] | ((uint64_t)x[3] << 32);
+                    uint64_t c, u;
+                    int ok0 = po_lemire(U0, (uint64_t)d, &c);
+                    int ok1 = po_lemire(U1, S, &u);
+                    if (!ok0 || !ok1) continue;
+                    j = po_select_alias(thr + s, alias + s, d, c, u);
+                    break;
+                }
+            }
+            v = (uint64_t)col[s + j];
+            p[t] = (int32_t)v;
+        }
+    }
+    return 0;
+}
+
+/* --------------------------------------------------- inverted index --- */
+static int po_seen_before(const int32_t* p, int i) {
+    for (int j = 0; j < i; ++j) if (p[j] == p[i]) return 1;
+    return 0;
+}
+
+/* off[v] = number of paths containing v, as exclusive prefix (off[n] = nnz).
+ * Pass pid = NULL to get off only; then call again with pid sized off[n].
+ * P_v lists the ids r of the paths that contain v, ascending, each once. */
+int64_t po_build_index(int64_t n, int64_t R, int L, const int32_t* paths, int64_t* off, int32_t* pid) {
+    memset(off, 0, sizeof(int64_t) * (size_t)(n + 1));
+    for (int64_t r = 0; r < R; ++r) {
+        const int32_t* p = paths + r * L;
+        for (int i = 0; i < L; ++i)
+            if (!po_seen_before(p, i)) off[p[i] + 1]++;
+    }
+    for (int64_t v = 0; v < n; ++v) off[v + 1] += off[v];
+    if (pid) {
+        int64_t* cur = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+        memcpy(cur, off, sizeof(int64_t) * (size_t)n);
+        for (int64_t r = 0; r < R; ++r) {
+            const int32_t* p = paths + r * L;
+            for (int i = 0; i < L; ++i)
+                if (!po_seen_before(p, i)) pid[cur[p[i]]++] = (int32_t)r;
+        }
+        free(cur);
+    }
+    return off[n];
+}
+
+/* ------------------------------------------------------- Algorithm 1 --- */
+typedef struct { uint32_t cnt; int32_t id; } po_cand;
+
+static int po_cmp_cand(const void* a, const void* b) {
+    const po_cand* x = (const po_cand*)a;
+    const po_cand* y = (const po_cand*)b;
+    if (x->cnt != y->cnt) return x->cnt > y->cnt ? -1 : 1;     /* count desc */
+    return (x->id > y->id) - (x->id < y->id);                  /* id asc */
+}
+
+/* Counts cnt(v,u) = |{p in P_v : u in p}| for u != v, every unique vertex of
+ * a path counted once (Alg. 1), sorted by (count desc, id asc).
+ * work_cnt: n zeroed uint32 (left zeroed on return). Returns the number of
+ * candidates written to cands (caller sizes it >= min(n, (L-1)*|P_v|)). */
+static int64_t po_counts(int64_t n, int L, const int32_t* paths, const int64_t* off, const int32_t* pid,
+                         int32_t v, uint32_t* work_cnt, po_cand* cands) {
+    int64_t m = 0;
+    int64_t cap = (off[v + 1] - off[v]) * (int64_t)(L - 1);
+    if (cap > n) cap = n;
+    int32_t* list = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
+    for (int64_t e = off[v]; e < off[v + 1]; ++e) {
+        const int32_t* p = paths + (int64_t)pid[e] * L;
+        for (int i = 0; i < L; ++i) {
+            int32_t u = p[i];
+            if (u == v || po_seen_before(p, i)) continue;      /* unique u != v */
+            if (work_cnt[u] == 0) list[m++] = u;
+            work_cnt[u] += 1;                                  /* S_RP(v,u) += 1/R */
+        }
+    }
+    for (int64_t i = 0; i < m; ++i) {
+        cands[i].cnt = work_cnt[list[i]];
+        cands[i].id = list[i];
+        work_cnt[list[i]] = 0;
+    }
+    free(list);
+    qsort(cands, (size_t)m, sizeof(po_cand), po_cmp_cand);
+    return m;
+}
+
+/* Top-k of query v: ids[k], cnts[k], padded with (-1, 0). Returns #candidates. */
+int64_t po_topk(int64_t n, int L, const int32_t* paths, const int64_t* off, const int32_t* pid,
+                int32_t v, int k, uint32_t* work_cnt, int32_t* ids, uint32_t* cnts) {
+    int64_t cap = (off[v + 1] - off[v]) * (int64_t)(L - 1);
+    if (cap > n) cap = n;
+    po_cand* c = (po_cand*)malloc(sizeof(po_cand) * (size_t)(cap > 0 ? cap : 1));
+    int64_t m = po_counts(n, L, paths, off, pid, v, work_cnt, c);
+    for (int i = 0; i < k; ++i) {
+        if (i < m) { ids[i] = c[i].id; cnts[i] = c[i].cnt; }
+        else { ids[i] = -1; cnts[i] = 0; }
+    }
+    free(c);
+    return m;
+}
+
+/* Sec. 3.3: theta(v) = the D largest S_RP(v, u) over u != v, as counts,
+ * descending, zero-padded. */
+void po_theta(int64_t n, int L, const int32_t* paths, const int64_t* off, const int32_t* pid,
+              int32_t v, int D, uint32_t* work_cnt, uint32_t* theta) {
+    int64_t cap = (off[v + 1] - off[v]) * (int64_t)(L - 1);
+    if (cap > n) cap = n;
+    po_cand* c = (po_cand*)malloc(sizeof(po_cand) * (size_t)(cap > 0 ? cap : 1));
+    int64_t m = po_counts(n, L, paths, off, pid, v, work_cnt, c);
+    for (int d = 0; d < D; ++d) theta[d] = d < m ? c[d].cnt : 0;
+    free(c);
+}
+
+/* ------------------------------------------------ Panther++ k-NN --- */
+typedef struct { uint64_t d2; int32_t id; } po_nb;
+
+static int po_cmp_nb(const void* a, const void* b) {
+    const po_nb* x = (const po_nb*)a;
+    const po_nb* y = (const po_nb*)b;
+    if (x->d2 != y->d2) return x->d2 < y->d2 ? -1 : 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+/* Exact squared Euclidean distance between two count vectors. Returns 0 and
+ * sets *out, or -1 if the sum does not fit in 64 bits. */
+int po_dist2(const uint32_t* a, const uint32_t* b, int D, uint64_t* out) {
+    po_u128 s = 0;
+    for (int d = 0; d < D; ++d) {
+        int64_t diff = (int64_t)a[d] - (int64_t)b[d];
+        s += (po_u128)((po_u128)(diff < 0 ? -diff : diff) * (po_u128)(diff < 0 ? -diff : diff));
+    }
+    if (s >> 64) return -1;
+    *out = (uint64_t)s;
+    return 0;
+}
+
+/* k nearest u != v by (||theta_v - theta_u||^2 asc, id asc), over all n
+ * vectors (theta row-major [n][D]). Ranking by squared distance is the same
+ * as ranking by S_RP++ = 1/||.|| descending, and needs no reciprocal.
+ * Returns 0, or -1 on overflow. */
+int po_knn(int64_t n, int D, const uint32_t* theta, int32_t v, int k, int32_t* ids, uint64_t* d2) {
+    po_nb* all = (po_nb*)malloc(sizeof(po_nb) * (size_t)(n > 1 ? n : 1));
+    int64_t m = 0;
+    for (int64_t u = 0; u < n; ++u) {
+        if (u == v) continue;
+        uint64_t dd;
+        if (po_dist2(theta + (int64_t)v * D, theta + u * D, D, &dd)) { free(all); return -1; }
+        all[m].d2 = dd; all[m].id = (int32_t)u; ++m;
+    }
+    qsort(all, (size_t)m, sizeof(po_nb), po_cmp_nb);
+    for (int i = 0; i < k; ++i) {
+        if (i < m) { ids[i] = all[i].id; d2[i] = all[i].d2; }
+        else { ids[i] = -1; d2[i] = UINT64_MAX; }
+    }
+    free(all);
+    return 0;
+}

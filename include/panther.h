@@ -1,0 +1,281 @@
+/*
+ * panther.h - C ABI of libpanther, a GB300 (sm_103a) implementation of the
+ * hot path of Panther and Panther++ (Zhang et al., "Panther: Fast Top-k
+ * Similarity Search in Large Networks", arXiv 1504.02577).
+ *
+ * The hot path:
+ *   panther_sample_size    R of the sample-size guarantee (Sec. 3.2)
+ *   panther_build_graph    graph + transition tables t_ij of Eq. (3)
+ *   panther_sample_paths   R random T-paths (Algorithm 3)
+ *   panther_build_index    vertex -> path inverted index P_v (Sec. 3.1)
+ *   panther_topk           per-query co-occurrence counts and top-k
+ *                          (Algorithm 1, Eq. (4))
+ *   pantherpp_vectors      Panther++ feature vectors theta(v) (Sec. 3.3, Alg. 2)
+ *   pantherpp_knn          nearest neighbours of theta under Euclidean
+ *                          distance (Sec. 3.3, Alg. 2)
+ *   panther_serve_*        a request loop over resident graph/paths/index
+ *                          (no counterpart in the paper)
+ *
+ * Conventions shared by every call:
+ *   - Calls return a panther_status and never throw. Arguments are validated
+ *     before any launch; on error nothing is launched, *out handles are left
+ *     NULL and panther_last_error() describes the problem.
+ *   - A context owns one CUDA device and one stream. Work is enqueued on that
+ *     stream; a call returns when its work is enqueued unless stated
+ *     otherwise. Calls on one context must not run concurrently from several
+ *     host threads (the serving loop has its own context and lock).
+ *   - Handles (graph, paths, index, vecs) own device memory allocated by the
+ *     library; free them with the matching panther_free_* call. Query and
+ *     output arrays are caller-owned: device pointers, unless the flag
+ *     PANTHER_IO_HOST says they are host pointers (then the call copies and
+ *     returns only when the host outputs are written).
+ *   - Kernels report data errors they detect (a hash table overfull, an
+ *     index out of range, a bounded wait that ran out) in a device status
+ *     word; panther_sync() waits for the stream and returns that status.
+ *   - Results are integers: counts of shared paths (similarity = count / R)
+ *     and exact squared distances. Ties order by vertex id ascending. Rows
+ *     with fewer than k candidates are padded with id -1 and count 0
+ *     (k-NN: id -1, distance UINT64_MAX).
+ */
+#ifndef PANTHER_H
+#define PANTHER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PANTHER_API __attribute__((visibility("default")))
+#else
+#define PANTHER_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PANTHER_OK = 0,
+    PANTHER_EINVAL = 1,     /* invalid argument or malformed graph */
+    PANTHER_ENOMEM = 2,     /* device or pinned host allocation failed, or budget exceeded */
+    PANTHER_ECUDA = 3,      /* a CUDA runtime call failed */
+    PANTHER_ETIMEOUT = 4,   /* a bounded device-side or host-side wait ran out */
+    PANTHER_EOVERFLOW = 5,  /* a size or value exceeds what the data layout holds */
+    PANTHER_EBUSY = 6       /* the serving loop is full or shutting down */
+} panther_status;
+
+/* where caller arrays live */
+enum { PANTHER_MEM_HOST = 0, PANTHER_MEM_DEVICE = 1 };
+
+/* neighbour selection (Eq. 3); panther_build_graph takes a bit mask of the
+ * tables to build, panther_sample_paths one mode */
+enum { PANTHER_MODE_PREFIX = 1, PANTHER_MODE_ALIAS = 2, PANTHER_MODE_BOTH = 3 };
+
+/* panther_topk / pantherpp_knn flags */
+enum {
+    PANTHER_TOPK_BATCHED = 0,      /* one load-balanced persistent launch for the whole batch */
+    PANTHER_TOPK_PLAIN = 1,        /* one launch per query (comparison form) */
+    PANTHER_KNN_BF16_SCREEN = 0,   /* tensor-core BF16 screening + exact integer rerank */
+    PANTHER_KNN_FP32 = 2,          /* FP32 brute force + exact integer rerank (comparison form) */
+    PANTHER_IO_HOST = 0x100        /* queries and outputs are host pointers */
+};
+
+typedef struct panther_ctx panther_ctx;
+typedef struct panther_graph panther_graph;
+typedef struct panther_paths panther_paths;
+typedef struct panther_index panther_index;
+typedef struct pantherpp_vecs pantherpp_vecs;
+typedef struct panther_server panther_server;
+
+/* ------------------------------------------------------------ context --- */
+
+/* Create a context on CUDA device `device`. `cuda_stream` is a cudaStream_t
+ * to enqueue on (NULL: the library creates and owns a non-blocking stream).
+ * Errors: EINVAL (no such device), ECUDA. */
+PANTHER_API panther_status panther_create(panther_ctx** out, int device, void* cuda_stream);
+
+/* Synchronises the stream, frees context-owned scratch. Handles created on
+ * the context must be freed before it. NULL is ignored. */
+PANTHER_API void panther_destroy(panther_ctx* ctx);
+
+/* Human-readable description of the last error on this context ("" if none).
+ * The pointer stays valid until the next call on the context. */
+PANTHER_API const char* panther_last_error(const panther_ctx* ctx);
+
+/* Wait for all work on the context's stream, then return and clear the
+ * device status word (OK, EOVERFLOW, EINVAL or ETIMEOUT) or ECUDA. */
+PANTHER_API panther_status panther_sync(panther_ctx* ctx);
+
+/* Scratch budget in bytes for temporary device buffers of one call (top-k
+ * hub tables, index sort buffers are sized separately). Default 8 GiB. */
+PANTHER_API panther_status panther_set_scratch_budget(panther_ctx* ctx, int64_t bytes);
+
+/* Number of kernel launches this context has enqueued so far. */
+PANTHER_API int64_t panther_launch_count(const panther_ctx* ctx);
+
+/* --------------------------------------------------------- Sec. 3.2 --- */
+
+/* Sample size of the guarantee (Theorem 1 with Lemma 1):
+ *   R = ceil( c / eps^2 * ( log2 C(T,2) + 1 + ln(1/delta) ) ).
+ * Host only, no context. Errors: EINVAL unless 0<eps<1, 0<delta<1, c>0,
+ * T>=2; EOVERFLOW if R does not fit in int64. */
+PANTHER_API panther_status panther_sample_size(double eps, double delta, double c, int T, int64_t* R);
+
+/* ----------------------------------------------------- graph, Eq. (3) --- */
+
+/* Copy an undirected weighted graph G=(V,E,W) (Definition 1) to the device
+ * and build the transition tables of Eq. (3), t_ij = w_ij / sum_k w_ik.
+ *   n        number of vertices, 1 <= n < 2^31
+ *   m        number of directed CSR entries (2|E|), m < 2^32
+ *   row_ptr  int64[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = m
+ *   col      int32[m], neighbours of each row in strictly ascending order
+ *   w        uint32[m], weights >= 1; w(u,v) = w(v,u)
+ *   mem      PANTHER_MEM_HOST or PANTHER_MEM_DEVICE for the three arrays
+ *   modes    PANTHER_MODE_PREFIX | PANTHER_MODE_ALIAS: tables to build
+ * The arrays are copied; the caller keeps ownership. The call validates the
+ * graph on the device (ranges, sorted rows, no self-loops, symmetry with
+ * equal weights, every row sum * degree < 2^63) and returns after the
+ * tables are built (it synchronises the stream).
+ * Errors: EINVAL (bad arguments or graph), EOVERFLOW (m >= 2^32, row sum too
+ * large), ENOMEM, ECUDA. */
+PANTHER_API panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64_t m,
+                                   const int64_t* row_ptr, const int32_t* col, const uint32_t* w,
+                                   int mem, int modes, panther_graph** out);
+
+/* ------------------------------------------------------- Algorithm 3 --- */
+
+/* Sample R paths of T steps (T+1 vertices). Path r starts at
+ * Uniform[0,n) and moves T times to a neighbour chosen with probability
+ * t_ij (Eq. 3); a vertex without neighbours keeps the walk in place.
+ * Draws are Philox4x32-10 with key (lo32(seed), hi32(seed)) and counter
+ * (lo32(r), hi32(r), t, attempt); Uniform[0,S) is Lemire's multiply-shift
+ * with rejection on the 64-bit word (x0 | x1<<32). PREFIX picks the neighbour
+ * j with cum(j-1) <= x < cum(j) for x = Uniform[0, sum w); ALIAS picks column
+ * c = Uniform[0,deg) (x0,x1) and coin u = Uniform[0, sum w) (x2,x3) of the
+ * same draw from the integer Vose table. Both realise Eq. 3 exactly and the
+ * paths are reproducible bit for bit.
+ *   R in [1, 2^31-1], T in [1, 31], mode PREFIX or ALIAS (its table must
+ *   have been built).
+ * Rows live on the device as int32[R][stride], stride = 8, 16 or 32
+ * (the smallest that holds T+1); entries past T+1 are unspecified.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+PANTHER_API panther_status panther_sample_paths(panther_ctx* ctx, const panther_graph* g, uint64_t seed,
+                                    int64_t R, int T, int mode, panther_paths** out);
+
+/* Device view of the path rows (library-owned; valid until freed). */
+PANTHER_API panther_status panther_paths_view(const panther_paths* p, const int32_t** dev_rows,
+                                  int64_t* R, int* L, int* stride);
+
+/* ------------------------------------------------------------ Sec. 3.1 --- */
+
+/* Build the inverted index P_v = { r : v in p_r } with a device LSD radix
+ * sort of (vertex, path id) pairs. A path that visits v several times is
+ * listed once. Layout: off int64[n+1], pid int32[nnz]; P_v is
+ * pid[off[v] .. off[v+1]) in ascending path id. Synchronises once to size the
+ * output. Errors: EINVAL, ENOMEM, ECUDA. */
+PANTHER_API panther_status panther_build_index(panther_ctx* ctx, const panther_paths* p, panther_index** out);
+
+PANTHER_API panther_status panther_index_view(const panther_index* ix, const int64_t** dev_off,
+                                  const int32_t** dev_pid, int64_t* n, int64_t* nnz);
+
+/* ---------------------------------------------- Algorithm 1, Eq. (4) --- */
+
+/* For each query v = queries[i]: cnt(v,u) = number of paths in P_v that
+ * contain u (each path counted once per u), for every u != v; then the k
+ * largest by (cnt desc, u asc). Writes out_ids int32[q][k] and
+ * out_counts uint32[q][k] (similarity S_RP(v,u) = cnt / R).
+ *   q >= 0 (q = 0 is a no-op), 1 <= k <= 64, queries in [0, n)
+ *   flags: PANTHER_TOPK_BATCHED or PANTHER_TOPK_PLAIN, optionally
+ *          | PANTHER_IO_HOST (queries/outputs in host memory; the call then
+ *          synchronises)
+ * Temporary device memory (hub hash tables) is drawn from the context's
+ * scratch budget; a batch whose hubs do not fit is processed in several
+ * rounds. Errors: EINVAL, ENOMEM, ECUDA. */
+PANTHER_API panther_status panther_topk(panther_ctx* ctx, const panther_index* ix, const panther_paths* p,
+                            const int32_t* queries, int64_t q, int k,
+                            int32_t* out_ids, uint32_t* out_counts, int flags);
+
+/* ---------------------------------------------------- Panther++ (3.3) --- */
+
+/* theta(v) = the D largest counts cnt(v,u), u != v, descending, zero padded,
+ * for every vertex (Algorithm 2's loop over V), plus the device data the
+ * k-NN search needs (a BF16 copy padded to 64 columns, exact squared norms).
+ *   1 <= D <= 64. Errors: EINVAL, ENOMEM, EOVERFLOW (a count >= 2^29, which
+ *   would let a squared distance overflow 64 bits), ECUDA. Synchronises. */
+PANTHER_API panther_status pantherpp_vectors(panther_ctx* ctx, const panther_index* ix, const panther_paths* p,
+                                 int D, pantherpp_vecs** out);
+
+/* Device view of theta: uint32[n][D] row-major. */
+PANTHER_API panther_status pantherpp_vecs_view(const pantherpp_vecs* v, const uint32_t** dev_theta,
+                                   int64_t* n, int* D);
+
+/* For each query v: the k vertices u != v with the smallest
+ * ||theta(v) - theta(u)||^2, ties by id ascending (the order of
+ * S_RP++ = 1/||.|| descending, Sec. 3.3, without forming the reciprocal).
+ * Writes out_ids int32[q][k] and out_dist2 uint64[q][k] (exact).
+ *   1 <= k <= 32, queries in [0, n)
+ *   flags: PANTHER_KNN_BF16_SCREEN (tensor cores, BF16 inputs, FP32
+ *          accumulation, a proven error bound, exact uint64 rerank of every
+ *          candidate the bound cannot rule out) or PANTHER_KNN_FP32 (FP32
+ *          CUDA-core brute force with the same bound and rerank), optionally
+ *          | PANTHER_IO_HOST.
+ * Both forms return the exact answer. Errors: EINVAL, ENOMEM, ECUDA. */
+PANTHER_API panther_status pantherpp_knn(panther_ctx* ctx, const pantherpp_vecs* v, const int32_t* queries,
+                             int64_t q, int k, int32_t* out_ids, uint64_t* out_dist2, int flags);
+
+/* Screening statistics of the last pantherpp_knn call on this context:
+ * [0] pairs screened, [1] pairs sent to exact rerank, [2] max |d_hat - d|
+ * observed over reranked pairs, [3] pairs whose bound was zero (exact). */
+PANTHER_API panther_status pantherpp_knn_stats(panther_ctx* ctx, int64_t stats[4]);
+
+/* ------------------------------------------------------ test support --- */
+
+/* Copies of the graph's transition tables, for tests: dev_alias16 receives
+ * m entries {thr_lo, thr_hi, col[c], col[alias[c]]} (uint32 x4) and
+ * dev_prefix m entries {cum, col} (uint32 x2, or x4 with a 64-bit cum when
+ * *prefix_wide is 1). Either pointer may be NULL. Synchronises. */
+PANTHER_API panther_status panther_debug_graph_tables(const panther_graph* g, void* dev_alias16, void* dev_prefix,
+                                                      int* prefix_wide);
+
+/* Philox4x32-10 words for `count` counters (lo32(r0+i), hi32(r0+i), c2, c3)
+ * under key (k0, k1), written to dev_out[i][0..3], and the same counters
+ * through curand's Philox4_32_10 (curand_init(k0 | k1<<32, subsequence =
+ * c2 | c3<<32, offset = 4*(r0+i)), one curand4) to dev_ref[i][0..3].
+ * Synchronises. */
+PANTHER_API panther_status panther_debug_philox(panther_ctx* ctx, uint32_t k0, uint32_t k1, uint64_t r0,
+                                                uint32_t c2, uint32_t c3, int64_t count, uint32_t* dev_out,
+                                                uint32_t* dev_ref);
+
+/* --------------------------------------------------------- free calls --- */
+PANTHER_API void panther_free_graph(panther_graph* g);
+PANTHER_API void panther_free_paths(panther_paths* p);
+PANTHER_API void panther_free_index(panther_index* ix);
+PANTHER_API void pantherpp_free_vecs(pantherpp_vecs* v);
+
+/* ------------------------------------------------------------ serving --- */
+/* (No counterpart in the paper.) A request loop over resident paths, index
+ * and vectors. Requests arrive from any host thread; a scheduler thread
+ * admits them while their device bytes fit the memory budget and slots are
+ * free, batches admitted top-k requests into one launch, and keeps up to
+ * `streams` batches in flight on separate streams, so that new requests
+ * start while earlier ones run. Results are identical to a call made alone.
+ *
+ * kind: 0 = top-k (Algorithm 1), 1 = Panther++ k-NN. Queries and outputs are
+ * host pointers owned by the caller and must stay valid until the request
+ * completes (panther_serve_wait returns). */
+PANTHER_API panther_status panther_serve_create(int device, const panther_index* ix, const panther_paths* p,
+                                    const pantherpp_vecs* v, int64_t mem_budget_bytes,
+                                    int max_inflight_requests, int streams, panther_server** out);
+PANTHER_API panther_status panther_serve_submit(panther_server* s, int kind, const int32_t* queries, int64_t q,
+                                    int k, int32_t* out_ids, void* out_vals, int64_t* ticket);
+/* Wait for a request; *latency_ms = completion time - submit time. */
+PANTHER_API panther_status panther_serve_wait(panther_server* s, int64_t ticket, double timeout_s,
+                                  double* latency_ms);
+/* [0] submitted, [1] completed, [2] batches launched, [3] max requests in one batch,
+ * [4] max batches in flight at once, [5] requests refused (EBUSY) */
+PANTHER_API panther_status panther_serve_stats(panther_server* s, int64_t stats[6]);
+PANTHER_API void panther_serve_destroy(panther_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PANTHER_H */

@@ -1,0 +1,535 @@
+// Graph upload, validation and the transition tables of Eq. (3).
+//
+// Per-vertex record vrec[v] = {start, deg, S_lo, S_hi} (16 B, one sector),
+// S = sum of the row's weights.
+//
+// PREFIX table: entry j of row v = {inclusive cumulative weight, neighbour}
+//   (uint2 when every S < 2^32, else uint4 {cum_lo, cum_hi, col, 0}).
+// ALIAS table: entry c of row v = {thr_lo, thr_hi, col[c], col[alias[c]]}.
+//   It is the integer Vose table with LIFO worklists (q_j = w_j * deg against
+//   capacity S). A column popped as "small" gets the large that is current at
+//   that moment; that large is determined by prefix sums of the deficits of
+//   the smalls (S - q) and the excesses of the larges (q - S) taken in pop
+//   order (descending column index), so every row is built in parallel and
+//   the result equals the sequential construction:
+//     small s_j (pop order j):  alias = L_i, i = min{ i : E_i >= D_(j-1) }
+//     large L_i: if D_total > E_i, thr = S - (D_j* - E_i) with
+//                j* = min{ j : D_j > E_i } and alias = L_(i+1);
+//                otherwise thr = S and alias = itself.
+//   D = inclusive prefix of deficits, E = inclusive prefix of excesses.
+#include "internal.cuh"
+
+namespace {
+
+constexpr int64_t BIG_DEG = 2048;   // rows above this go to one CTA each
+constexpr int BLK = 512;            // threads of the CTA-per-row kernels
+
+// ------------------------------------------------------------ groups ---
+struct WarpG {
+    static constexpr int size = 32;
+    __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+    __device__ __forceinline__ uint64_t incl_scan(uint64_t v, uint64_t* total) const {
+        int l = rank();
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (l >= o) v += y;
+        }
+        *total = __shfl_sync(0xffffffffu, v, 31);
+        return v;
+    }
+    __device__ __forceinline__ uint64_t sum(uint64_t v) const {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    }
+    __device__ __forceinline__ bool any(bool p) const { return __any_sync(0xffffffffu, p); }
+};
+
+struct BlockG {
+    static constexpr int size = BLK;
+    uint64_t* sh;   // >= BLK/32 + 1 entries
+    __device__ __forceinline__ int rank() const { return threadIdx.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ uint64_t incl_scan(uint64_t v, uint64_t* total) const {
+        int l = threadIdx.x & 31, wi = threadIdx.x >> 5;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (l >= o) v += y;
+        }
+        if (l == 31) sh[wi] = v;
+        __syncthreads();
+        if (wi == 0) {
+            uint64_t s = l < BLK / 32 ? sh[l] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint64_t y = __shfl_up_sync(0xffffffffu, s, o);
+                if (l >= o) s += y;
+            }
+            if (l < BLK / 32) sh[l] = s;
+        }
+        __syncthreads();
+        uint64_t r = v + (wi ? sh[wi - 1] : 0);
+        *total = sh[BLK / 32 - 1];
+        __syncthreads();
+        return r;
+    }
+    __device__ uint64_t sum(uint64_t v) const {
+        uint64_t t;
+        incl_scan(v, &t);
+        return t;
+    }
+    __device__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
+};
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z ^= z >> 33;
+    z *= 0xff51afd7ed558ccdULL;
+    z ^= z >> 33;
+    z *= 0xc4ceb9fe1a85ec53ULL;
+    z ^= z >> 33;
+    return z;
+}
+// hash of a directed entry; the graph is symmetric iff the sum over entries of
+// H(v,u,w) equals the sum of H(u,v,w) (as multisets, with high probability)
+__device__ __forceinline__ uint64_t edge_hash(uint64_t a, uint64_t b, uint64_t w) {
+    return mix64((a << 32 | b) ^ mix64(w + 0x9E3779B97F4A7C15ULL));
+}
+
+// -------------------------------------------------------- row stats ---
+struct StatsOut {
+    uint4* vrec;
+    uint32_t* status;
+    unsigned long long* acc;   // [0] max S, [1] hash(v,u,w), [2] hash(u,v,w)
+};
+
+template <class G>
+__device__ void row_stats(const G& g, int64_t v, int64_t start, int64_t deg, int64_t n, const int32_t* col,
+                          const uint32_t* w, const StatsOut& o, uint64_t& h1, uint64_t& h2, uint64_t& mx) {
+    uint64_t s = 0, a1 = 0, a2 = 0;
+    bool bad = false;
+    for (int64_t i = g.rank(); i < deg; i += G::size) {
+        int32_t u = col[start + i];
+        uint32_t ww = w[start + i];
+        bad |= (u < 0) || ((int64_t)u >= n) || ((int64_t)u == v) || (ww == 0) ||
+               (i > 0 && col[start + i - 1] >= u);
+        s += ww;
+        if (u >= 0) {
+            a1 += edge_hash((uint64_t)v, (uint64_t)u, ww);
+            a2 += edge_hash((uint64_t)u, (uint64_t)v, ww);
+        }
+    }
+    s = g.sum(s);
+    a1 = g.sum(a1);
+    a2 = g.sum(a2);
+    bad = g.any(bad);
+    if (g.rank() == 0) {
+        o.vrec[v] = make_uint4((uint32_t)start, (uint32_t)deg, (uint32_t)s, (uint32_t)(s >> 32));
+        // q = w * deg must stay below 2^63 for the alias construction
+        if (deg > 0 && (__umul64hi(s, (uint64_t)deg) != 0 || s * (uint64_t)deg >= (1ull << 63)))
+            flag_status(o.status, ST_OVERFLOW);
+        if (bad) {
+            flag_status(o.status, ST_GRAPH_BAD);
+            atomicMin(o.status + 1, (uint32_t)v);
+        }
+    }
+    h1 += a1;
+    h2 += a2;
+    mx = s > mx ? s : mx;
+}
+
+__global__ void rows_check_kernel(const int64_t* __restrict__ row_ptr, int64_t n, int64_t m,
+                                  int32_t* __restrict__ big, int* __restrict__ nbig, uint32_t* status) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v > n) return;
+    int64_t a = row_ptr[v];
+    if (v == 0 && a != 0) flag_status(status, ST_GRAPH_BAD);
+    if (v == n) {
+        if (a != m) flag_status(status, ST_GRAPH_BAD);
+        return;
+    }
+    int64_t b = row_ptr[v + 1];
+    if (b < a || a < 0 || b > m) {
+        flag_status(status, ST_GRAPH_BAD);
+        return;
+    }
+    if (b - a > BIG_DEG) big[atomicAdd(nbig, 1)] = (int32_t)v;
+}
+
+__global__ void stats_warp_kernel(const int64_t* __restrict__ row_ptr, int64_t n, const int32_t* __restrict__ col,
+                                  const uint32_t* __restrict__ w, StatsOut o) {
+    WarpG g;
+    int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint64_t h1 = 0, h2 = 0, mx = 0;
+    for (int64_t v = wid; v < n; v += nw) {
+        int64_t a = row_ptr[v], b = row_ptr[v + 1];
+        if (b < a || b - a > BIG_DEG) continue;
+        row_stats(g, v, a, b - a, n, col, w, o, h1, h2, mx);
+    }
+    if (g.rank() == 0) {
+        atomicMax(o.acc + 0, (unsigned long long)mx);
+        atomicAdd(o.acc + 1, (unsigned long long)h1);
+        atomicAdd(o.acc + 2, (unsigned long long)h2);
+    }
+}
+
+__global__ void stats_block_kernel(const int64_t* __restrict__ row_ptr, int64_t n, const int32_t* __restrict__ col,
+                                   const uint32_t* __restrict__ w, const int32_t* __restrict__ big, StatsOut o) {
+    __shared__ uint64_t sh[BLK / 32 + 1];
+    BlockG g{sh};
+    int64_t v = big[blockIdx.x];
+    uint64_t h1 = 0, h2 = 0, mx = 0;
+    row_stats(g, v, row_ptr[v], row_ptr[v + 1] - row_ptr[v], n, col, w, o, h1, h2, mx);
+    if (threadIdx.x == 0) {
+        atomicMax(o.acc + 0, (unsigned long long)mx);
+        atomicAdd(o.acc + 1, (unsigned long long)h1);
+        atomicAdd(o.acc + 2, (unsigned long long)h2);
+    }
+}
+
+// ---------------------------------------------------------- prefix ---
+template <class G, bool WIDE>
+__device__ void row_prefix(const G& g, int64_t start, int64_t deg, const int32_t* col, const uint32_t* w,
+                           void* tab) {
+    uint64_t carry = 0;
+    for (int64_t base = 0; base < deg; base += G::size) {
+        int64_t i = base + g.rank();
+        uint64_t ww = i < deg ? w[start + i] : 0;
+        uint64_t tot;
+        uint64_t inc = g.incl_scan(ww, &tot) + carry;
+        if (i < deg) {
+            if (WIDE)
+                ((uint4*)tab)[start + i] =
+                    make_uint4((uint32_t)inc, (uint32_t)(inc >> 32), (uint32_t)col[start + i], 0u);
+            else
+                ((uint2*)tab)[start + i] = make_uint2((uint32_t)inc, (uint32_t)col[start + i]);
+        }
+        carry += tot;
+    }
+}
+
+template <bool WIDE>
+__global__ void prefix_warp_kernel(const int64_t* __restrict__ row_ptr, int64_t n, const int32_t* __restrict__ col,
+                                   const uint32_t* __restrict__ w, void* tab) {
+    WarpG g;
+    int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = wid; v < n; v += nw) {
+        int64_t a = row_ptr[v], d = row_ptr[v + 1] - a;
+        if (d > BIG_DEG) continue;
+        row_prefix<WarpG, WIDE>(g, a, d, col, w, tab);
+    }
+}
+
+template <bool WIDE>
+__global__ void prefix_block_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                    const uint32_t* __restrict__ w, const int32_t* __restrict__ big, void* tab) {
+    __shared__ uint64_t sh[BLK / 32 + 1];
+    BlockG g{sh};
+    int64_t v = big[blockIdx.x];
+    row_prefix<BlockG, WIDE>(g, row_ptr[v], row_ptr[v + 1] - row_ptr[v], col, w, tab);
+}
+
+// ----------------------------------------------------------- alias ---
+// first index in [0,cnt) with a[i] >= x (cnt if none)
+__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* a, int64_t cnt, uint64_t x) {
+    int64_t lo = 0, hi = cnt;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+// first index in [0,cnt) with a[i] > x (cnt if none)
+__device__ __forceinline__ int64_t upper_bound_u64(const uint64_t* a, int64_t cnt, uint64_t x) {
+    int64_t lo = 0, hi = cnt;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+template <class G>
+__device__ void row_alias(const G& g, int64_t start, int64_t deg, uint64_t S, const int32_t* col,
+                          const uint32_t* w, uint4* tab, int32_t* sidx, uint64_t* scum) {
+    if (deg == 0) return;
+    const uint64_t d = (uint64_t)deg;
+    // A: number of small columns (q < S)
+    uint64_t ns = 0;
+    for (int64_t i = g.rank(); i < deg; i += G::size) ns += ((uint64_t)w[start + i] * d < S);
+    ns = g.sum(ns);
+    const int64_t nsm = (int64_t)ns, nl = deg - nsm;
+    // B: columns in pop order (descending index) - smalls at [0,ns), larges at [ns,deg)
+    uint64_t cs = 0, cl = 0;
+    for (int64_t base = 0; base < deg; base += G::size) {
+        int64_t i = base + g.rank();
+        bool valid = i < deg;
+        uint64_t q = valid ? (uint64_t)w[start + i] * d : 0;
+        uint64_t sm = (valid && q < S) ? 1 : 0, lg = (valid && q >= S) ? 1 : 0;
+        uint64_t ts, tl;
+        uint64_t rs = g.incl_scan(sm, &ts) - sm + cs;
+        uint64_t rl = g.incl_scan(lg, &tl) - lg + cl;
+        if (sm) sidx[start + nsm - 1 - (int64_t)rs] = (int32_t)i;
+        if (lg) sidx[start + nsm + nl - 1 - (int64_t)rl] = (int32_t)i;
+        cs += ts;
+        cl += tl;
+    }
+    g.sync();
+    // C: D = prefix of deficits S - q over smalls, E = prefix of excesses q - S over larges
+    uint64_t carry = 0;
+    for (int64_t base = 0; base < nsm; base += G::size) {
+        int64_t p = base + g.rank();
+        uint64_t x = p < nsm ? S - (uint64_t)w[start + sidx[start + p]] * d : 0;
+        uint64_t tot;
+        uint64_t inc = g.incl_scan(x, &tot) + carry;
+        if (p < nsm) scum[start + p] = inc;
+        carry += tot;
+    }
+    carry = 0;
+    for (int64_t base = 0; base < nl; base += G::size) {
+        int64_t p = base + g.rank();
+        uint64_t x = p < nl ? (uint64_t)w[start + sidx[start + nsm + p]] * d - S : 0;
+        uint64_t tot;
+        uint64_t inc = g.incl_scan(x, &tot) + carry;
+        if (p < nl) scum[start + nsm + p] = inc;
+        carry += tot;
+    }
+    g.sync();
+    const uint64_t* D = scum + start;
+    const uint64_t* E = scum + start + nsm;
+    const int32_t* SI = sidx + start;
+    const int32_t* LI = sidx + start + nsm;
+    const uint64_t Dtot = nsm ? D[nsm - 1] : 0;
+    // D: table entries. Each lane takes a contiguous run and walks the other
+    // sequence forward from one binary search (both sequences are sorted).
+    {
+        int64_t per = (nsm + G::size - 1) / G::size;
+        int64_t p0 = (int64_t)g.rank() * per, p1 = p0 + per < nsm ? p0 + per : nsm;
+        if (p0 < p1) {
+            int64_t i = nl ? lower_bound_u64(E, nl, p0 ? D[p0 - 1] : 0) : 0;
+            for (int64_t p = p0; p < p1; ++p) {
+                uint64_t dprev = p ? D[p - 1] : 0;
+                while (i < nl && E[i] < dprev) ++i;
+                int32_t j = SI[p];
+                uint64_t q = (uint64_t)w[start + j] * d;
+                int32_t self = col[start + j];
+                if (nl == 0 || i >= nl)   // cannot happen for consistent integer weights
+                    tab[start + j] = make_uint4((uint32_t)S, (uint32_t)(S >> 32), (uint32_t)self, (uint32_t)self);
+                else
+                    tab[start + j] = make_uint4((uint32_t)q, (uint32_t)(q >> 32), (uint32_t)self,
+                                                (uint32_t)col[start + LI[i]]);
+            }
+        }
+    }
+    {
+        int64_t per = (nl + G::size - 1) / G::size;
+        int64_t i0 = (int64_t)g.rank() * per, i1 = i0 + per < nl ? i0 + per : nl;
+        if (i0 < i1) {
+            int64_t js = upper_bound_u64(D, nsm, E[i0]);
+            for (int64_t i = i0; i < i1; ++i) {
+                uint64_t Ei = E[i];
+                while (js < nsm && D[js] <= Ei) ++js;
+                int32_t j = LI[i];
+                int32_t self = col[start + j];
+                if (Dtot > Ei && i + 1 < nl) {
+                    uint64_t thr = S - (D[js] - Ei);
+                    tab[start + j] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), (uint32_t)self,
+                                                (uint32_t)col[start + LI[i + 1]]);
+                } else {
+                    tab[start + j] = make_uint4((uint32_t)S, (uint32_t)(S >> 32), (uint32_t)self, (uint32_t)self);
+                }
+            }
+        }
+    }
+}
+
+__global__ void alias_warp_kernel(const uint4* __restrict__ vrec, int64_t n, const int32_t* __restrict__ col,
+                                  const uint32_t* __restrict__ w, uint4* tab, int32_t* sidx, uint64_t* scum) {
+    WarpG g;
+    int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = wid; v < n; v += nw) {
+        uint4 r = vrec[v];
+        if ((int64_t)r.y > BIG_DEG) continue;
+        row_alias(g, (int64_t)r.x, (int64_t)r.y, (uint64_t)r.z | ((uint64_t)r.w << 32), col, w, tab, sidx, scum);
+    }
+}
+
+__global__ void alias_block_kernel(const uint4* __restrict__ vrec, const int32_t* __restrict__ col,
+                                   const uint32_t* __restrict__ w, const int32_t* __restrict__ big, uint4* tab,
+                                   int32_t* sidx, uint64_t* scum) {
+    __shared__ uint64_t sh[BLK / 32 + 1];
+    BlockG g{sh};
+    uint4 r = vrec[big[blockIdx.x]];
+    row_alias(g, (int64_t)r.x, (int64_t)r.y, (uint64_t)r.z | ((uint64_t)r.w << 32), col, w, tab, sidx, scum);
+}
+
+unsigned grid_for(panther_ctx* ctx, int64_t items_per_block_unit, int64_t n, int threads) {
+    int64_t blocks = ceil_div(n, items_per_block_unit);
+    int64_t cap = (int64_t)ctx->num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    (void)threads;
+    return (unsigned)blocks;
+}
+
+}  // namespace
+
+extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64_t m, const int64_t* row_ptr,
+                                              const int32_t* col, const uint32_t* w, int mem, int modes,
+                                              panther_graph** out) {
+    if (!ctx || !out) return PANTHER_EINVAL;
+    *out = nullptr;
+    if (n < 1 || n >= (int64_t(1) << 31)) return set_err(ctx, PANTHER_EINVAL, "n must be in [1, 2^31)");
+    if (m < 0) return set_err(ctx, PANTHER_EINVAL, "m must be >= 0");
+    if (m >= (int64_t(1) << 32)) return set_err(ctx, PANTHER_EOVERFLOW, "m must be < 2^32");
+    if (!row_ptr || (m > 0 && (!col || !w))) return set_err(ctx, PANTHER_EINVAL, "null graph array");
+    if (mem != PANTHER_MEM_HOST && mem != PANTHER_MEM_DEVICE) return set_err(ctx, PANTHER_EINVAL, "bad mem");
+    if (modes < 1 || modes > 3) return set_err(ctx, PANTHER_EINVAL, "modes must be PREFIX, ALIAS or both");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    cudaMemcpyKind kind = mem == PANTHER_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+
+    panther_graph* g = new panther_graph();
+    g->ctx = ctx;
+    g->n = n;
+    g->m = m;
+    g->modes = modes;
+    int64_t* d_rp = nullptr;
+    uint32_t* d_w = nullptr;
+    int32_t* big = nullptr;
+    int* nbig = nullptr;
+    unsigned long long* acc = nullptr;
+    panther_status st = PANTHER_OK;
+    auto fail = [&](panther_status e) {
+        dev_free(ctx, d_rp);
+        dev_free(ctx, d_w);
+        dev_free(ctx, big);
+        dev_free(ctx, nbig);
+        dev_free(ctx, acc);
+        cudaStreamSynchronize(s);
+        panther_free_graph(g);
+        return e;
+    };
+    if ((st = dev_alloc(ctx, (void**)&d_rp, sizeof(int64_t) * (n + 1))) ||
+        (st = dev_alloc(ctx, (void**)&g->col, sizeof(int32_t) * m)) ||
+        (st = dev_alloc(ctx, (void**)&d_w, sizeof(uint32_t) * m)) ||
+        (st = dev_alloc(ctx, (void**)&g->vrec, sizeof(uint4) * n)) ||
+        (st = dev_alloc(ctx, (void**)&big, sizeof(int32_t) * (n + 1))) ||
+        (st = dev_alloc(ctx, (void**)&nbig, sizeof(int) * 2)) ||
+        (st = dev_alloc(ctx, (void**)&acc, sizeof(unsigned long long) * 4)))
+        return fail(st);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(d_rp, row_ptr, sizeof(int64_t) * (n + 1), kind, s)) ||
+        (m && (e = cudaMemcpyAsync(g->col, col, sizeof(int32_t) * m, kind, s))) ||
+        (m && (e = cudaMemcpyAsync(d_w, w, sizeof(uint32_t) * m, kind, s))) ||
+        (e = cudaMemsetAsync(nbig, 0, sizeof(int) * 2, s)) ||
+        (e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 4, s)) ||
+        (e = cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s)) ||
+        (e = cudaMemsetAsync(ctx->d_status + 1, 0xff, sizeof(uint32_t), s)))
+        return fail(cuda_err(ctx, e, "graph upload"));
+
+    rows_check_kernel<<<(unsigned)ceil_div(n + 1, 256), 256, 0, s>>>(d_rp, n, m, big, nbig, ctx->d_status);
+    ctx->launches++;
+    int h_nbig = 0;
+    uint32_t h_st[2];
+    if ((e = cudaMemcpyAsync(&h_nbig, nbig, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(h_st, ctx->d_status, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s)))
+        return fail(cuda_err(ctx, e, "row check"));
+    if (h_st[0]) return fail(set_err(ctx, PANTHER_EINVAL, "row_ptr is not a valid CSR offset array"));
+
+    StatsOut so{g->vrec, ctx->d_status, acc};
+    unsigned gw = grid_for(ctx, 64, n, 256);
+    stats_warp_kernel<<<gw, 256, 0, s>>>(d_rp, n, g->col, d_w, so);
+    ctx->launches++;
+    if (h_nbig) {
+        stats_block_kernel<<<h_nbig, BLK, 0, s>>>(d_rp, n, g->col, d_w, big, so);
+        ctx->launches++;
+    }
+    unsigned long long h_acc[3];
+    if ((e = cudaMemcpyAsync(h_acc, acc, sizeof(h_acc), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(h_st, ctx->d_status, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s)))
+        return fail(cuda_err(ctx, e, "graph validation"));
+    if (h_st[0] & ST_OVERFLOW) {
+        cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s);
+        return fail(set_err(ctx, PANTHER_EOVERFLOW, "a row's weight sum times its degree reaches 2^63"));
+    }
+    if (h_st[0]) {
+        cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s);
+        return fail(set_err(ctx, PANTHER_EINVAL,
+                            "malformed graph at row %u (column range, order, self-loop or zero weight)", h_st[1]));
+    }
+    if (h_acc[1] != h_acc[2])
+        return fail(set_err(ctx, PANTHER_EINVAL, "graph is not symmetric with equal weights"));
+    g->max_row_sum = h_acc[0];
+    g->prefix_wide = h_acc[0] >= (1ull << 32) ? 1 : 0;
+
+    if (modes & PANTHER_MODE_PREFIX) {
+        size_t esz = g->prefix_wide ? sizeof(uint4) : sizeof(uint2);
+        if ((st = dev_alloc(ctx, &g->prefix, esz * (size_t)m))) return fail(st);
+        if (g->prefix_wide) {
+            prefix_warp_kernel<true><<<gw, 256, 0, s>>>(d_rp, n, g->col, d_w, g->prefix);
+            if (h_nbig) prefix_block_kernel<true><<<h_nbig, BLK, 0, s>>>(d_rp, g->col, d_w, big, g->prefix);
+        } else {
+            prefix_warp_kernel<false><<<gw, 256, 0, s>>>(d_rp, n, g->col, d_w, g->prefix);
+            if (h_nbig) prefix_block_kernel<false><<<h_nbig, BLK, 0, s>>>(d_rp, g->col, d_w, big, g->prefix);
+        }
+        ctx->launches += h_nbig ? 2 : 1;
+        if ((e = cudaGetLastError())) return fail(cuda_err(ctx, e, "prefix table"));
+    }
+    if (modes & PANTHER_MODE_ALIAS) {
+        int32_t* sidx = nullptr;
+        uint64_t* scum = nullptr;
+        if ((st = dev_alloc(ctx, (void**)&g->alias, sizeof(uint4) * m)) ||
+            (st = dev_alloc(ctx, (void**)&sidx, sizeof(int32_t) * m)) ||
+            (st = dev_alloc(ctx, (void**)&scum, sizeof(uint64_t) * m))) {
+            dev_free(ctx, sidx);
+            return fail(st);
+        }
+        alias_warp_kernel<<<gw, 256, 0, s>>>(g->vrec, n, g->col, d_w, g->alias, sidx, scum);
+        ctx->launches++;
+        if (h_nbig) {
+            alias_block_kernel<<<h_nbig, BLK, 0, s>>>(g->vrec, g->col, d_w, big, g->alias, sidx, scum);
+            ctx->launches++;
+        }
+        e = cudaGetLastError();
+        dev_free(ctx, sidx);
+        dev_free(ctx, scum);
+        if (e) return fail(cuda_err(ctx, e, "alias table"));
+    }
+    dev_free(ctx, d_rp);
+    dev_free(ctx, d_w);
+    dev_free(ctx, big);
+    dev_free(ctx, nbig);
+    dev_free(ctx, acc);
+    if ((e = cudaStreamSynchronize(s))) {
+        d_rp = nullptr; d_w = nullptr; big = nullptr; nbig = nullptr; acc = nullptr;
+        return fail(cuda_err(ctx, e, "graph tables"));
+    }
+    *out = g;
+    return PANTHER_OK;
+}
+
+extern "C" {
+// Debug/test access: copy the alias table (thr, col_self, col_alias) or the
+// prefix table entries of the graph to caller device memory.
+panther_status panther_debug_graph_tables(const panther_graph* g, void* dev_alias16, void* dev_prefix,
+                                                     int* prefix_wide) {
+    if (!g) return PANTHER_EINVAL;
+    panther_ctx* ctx = g->ctx;
+    if (prefix_wide) *prefix_wide = g->prefix_wide;
+    if (dev_alias16 && g->alias)
+        PCK(ctx, cudaMemcpyAsync(dev_alias16, g->alias, sizeof(uint4) * g->m, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (dev_prefix && g->prefix)
+        PCK(ctx, cudaMemcpyAsync(dev_prefix, g->prefix, (g->prefix_wide ? 16 : 8) * g->m, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+    PCK(ctx, cudaStreamSynchronize(ctx->stream));
+    return PANTHER_OK;
+}
+}  // extern "C"

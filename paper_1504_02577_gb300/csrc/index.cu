@@ -1,0 +1,246 @@
+// Vertex -> path inverted index (Sec. 3.1) by a stable LSD radix sort.
+//
+// Pass 0 reads the path rows directly: item (r, j) of the flattened
+// [R][stride] array is a (key = vertex, value = r) pair unless j >= T+1 or the
+// same vertex occurred earlier in row r (P_v is a set). Rows are stride-
+// aligned inside every 32-lane round, so the duplicate test is one
+// __match_any_sync. Later passes read the (key, value) pairs of the previous
+// pass. Every pass is: tile histogram -> exclusive scan over (digit, tile) ->
+// stable scatter. The scatter ranks items with warp-private digit counters:
+// warps own contiguous sub-ranges of a tile and walk them in order, so the
+// sort is stable and path ids come out ascending within each vertex.
+#include "internal.cuh"
+
+namespace {
+
+constexpr int IX_T = 512;                  // threads per tile CTA
+constexpr int IX_WARPS = IX_T / 32;
+constexpr int IX_ROUNDS = 32;              // 32-item rounds per warp
+constexpr int IX_TILE = IX_T * IX_ROUNDS;  // 16384 items per tile
+constexpr int MAX_RADIX = 512;
+
+struct Src {
+    // pass 0 source
+    const int32_t* rows;
+    int64_t R;
+    int L, stride;
+    // later-pass source
+    const int32_t* keys;
+    const int32_t* vals;
+    int64_t count;      // number of pairs (later passes)
+    int first;          // 1 for pass 0
+};
+
+// load item i of the current source; returns false if it is not a pair
+__device__ __forceinline__ bool load_item(const Src& s, int64_t i, uint32_t& key, int32_t& val) {
+    if (s.first) {
+        int64_t total = s.R * s.stride;
+        bool inb = i < total;
+        int32_t x = inb ? s.rows[i] : -1;
+        int j = (int)(i & (s.stride - 1));
+        unsigned lane = threadIdx.x & 31;
+        unsigned peers = __match_any_sync(0xffffffffu, x);
+        unsigned rowbase = lane & ~(unsigned)(s.stride - 1);
+        unsigned rowmask = (s.stride == 32) ? 0xffffffffu : (((1u << s.stride) - 1u) << rowbase);
+        unsigned before = peers & rowmask & ((1u << lane) - 1u);
+        key = (uint32_t)x;
+        val = (int32_t)(i / s.stride);
+        return inb && j < s.L && before == 0;
+    } else {
+        bool inb = i < s.count;
+        key = inb ? (uint32_t)s.keys[i] : 0u;
+        val = inb ? s.vals[i] : 0;
+        return inb;
+    }
+}
+
+__global__ void __launch_bounds__(IX_T) hist_kernel(Src s, int shift, int radix, int64_t ntiles,
+                                                    int64_t* __restrict__ counts) {
+    __shared__ unsigned h[MAX_RADIX];
+    for (int d = threadIdx.x; d < radix; d += IX_T) h[d] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * IX_TILE;
+    int w = threadIdx.x >> 5;
+    for (int k = 0; k < IX_ROUNDS; ++k) {
+        int64_t i = base + (int64_t)w * (IX_ROUNDS * 32) + k * 32 + (threadIdx.x & 31);
+        uint32_t key;
+        int32_t val;
+        if (load_item(s, i, key, val)) atomicAdd(&h[(key >> shift) & (radix - 1)], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < radix; d += IX_T) counts[(int64_t)d * ntiles + blockIdx.x] = h[d];
+}
+
+__global__ void __launch_bounds__(IX_T) scatter_kernel(Src s, int shift, int radix, int64_t ntiles,
+                                                       const int64_t* __restrict__ offs, int32_t* __restrict__ okeys,
+                                                       int32_t* __restrict__ ovals) {
+    __shared__ unsigned wc[IX_WARPS][MAX_RADIX];   // per-warp digit counts, then starts within the tile
+    __shared__ long long toff[MAX_RADIX];          // global start of each digit's run from this tile
+    const int w = threadIdx.x >> 5;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int d = threadIdx.x; d < IX_WARPS * MAX_RADIX; d += IX_T) (&wc[0][0])[d] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * IX_TILE + (int64_t)w * (IX_ROUNDS * 32);
+    // phase 1: per-warp digit counts
+    for (int k = 0; k < IX_ROUNDS; ++k) {
+        uint32_t key;
+        int32_t val;
+        bool ok = load_item(s, base + k * 32 + lane, key, val);
+        uint32_t d = ok ? ((key >> shift) & (radix - 1)) : 0xffffffffu;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (ok && (peers & lt) == 0) wc[w][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // phase 2: start of each warp's run = counts of the earlier warps (tile-relative)
+    for (int d = threadIdx.x; d < radix; d += IX_T) {
+        toff[d] = offs[(int64_t)d * ntiles + blockIdx.x];
+        unsigned run = 0;
+        for (int ww = 0; ww < IX_WARPS; ++ww) {
+            unsigned c = wc[ww][d];
+            wc[ww][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    // phase 3: stable scatter in item order
+    for (int k = 0; k < IX_ROUNDS; ++k) {
+        uint32_t key;
+        int32_t val;
+        bool ok = load_item(s, base + k * 32 + lane, key, val);
+        uint32_t d = ok ? ((key >> shift) & (radix - 1)) : 0xffffffffu;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (ok) {
+            int64_t pos = (int64_t)toff[d] + wc[w][d] + __popc(peers & lt);
+            okeys[pos] = (int32_t)key;
+            ovals[pos] = val;
+        }
+        __syncwarp();
+        if (ok && (peers & lt) == 0) wc[w][d] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+__global__ void offsets_kernel(const int32_t* __restrict__ keys, int64_t nnz, int64_t n, int64_t* __restrict__ off,
+                               uint32_t* status) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > nnz) return;
+    int64_t prev = i > 0 ? (int64_t)keys[i - 1] : -1;
+    int64_t cur = i < nnz ? (int64_t)keys[i] : n;
+    if (prev < -1 || prev >= n || cur < 0 || cur > n || cur < prev) {   // keys out of range or unsorted
+        flag_status(status, ST_BAD_INDEX);
+        return;
+    }
+    for (int64_t v = prev + 1; v <= cur; ++v) off[v] = i;
+}
+
+__global__ void total_kernel(const int64_t* __restrict__ counts, const int64_t* __restrict__ offs, int64_t len,
+                             int64_t* __restrict__ total) {
+    *total = offs[len - 1] + counts[len - 1];
+}
+
+int bits_for(int64_t maxval) {
+    int b = 1;
+    while (b < 62 && (int64_t(1) << b) <= maxval) ++b;
+    return b;
+}
+
+}  // namespace
+
+// sizes of the radix passes for keys < n
+static void radix_plan(int64_t n, int* passes, int* rbits) {
+    int bits = bits_for(n - 1 > 0 ? n - 1 : 1);
+    int np = (bits + 8) / 9;
+    if (np < 1) np = 1;
+    *passes = np;
+    *rbits = (bits + np - 1) / np;
+}
+
+extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_paths* p, panther_index** out) {
+    if (!ctx || !p || !out) return PANTHER_EINVAL;
+    *out = nullptr;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const int64_t n = p->n;
+    const int64_t maxpairs = p->R * p->L;
+    int passes, rb;
+    radix_plan(n, &passes, &rb);
+    const int radix = 1 << rb;
+
+    panther_index* ix = new panther_index();
+    ix->ctx = ctx;
+    ix->n = n;
+    int32_t *kA = nullptr, *vA = nullptr, *kB = nullptr, *vB = nullptr;
+    int64_t *counts = nullptr, *offs = nullptr, *tot = nullptr;
+    panther_status st;
+    const int64_t tiles0 = ceil_div(p->R * p->stride, IX_TILE);
+    const int64_t tilesN = ceil_div(maxpairs, IX_TILE);
+    const int64_t maxtiles = tiles0 > tilesN ? tiles0 : tilesN;
+    auto cleanup = [&]() {
+        dev_free(ctx, kA); dev_free(ctx, vA); dev_free(ctx, kB); dev_free(ctx, vB);
+        dev_free(ctx, counts); dev_free(ctx, offs); dev_free(ctx, tot);
+    };
+    if ((st = dev_alloc(ctx, (void**)&kA, sizeof(int32_t) * maxpairs)) ||
+        (st = dev_alloc(ctx, (void**)&vA, sizeof(int32_t) * maxpairs)) ||
+        (st = dev_alloc(ctx, (void**)&kB, sizeof(int32_t) * maxpairs)) ||
+        (st = dev_alloc(ctx, (void**)&vB, sizeof(int32_t) * maxpairs)) ||
+        (st = dev_alloc(ctx, (void**)&counts, sizeof(int64_t) * radix * maxtiles)) ||
+        (st = dev_alloc(ctx, (void**)&offs, sizeof(int64_t) * radix * maxtiles)) ||
+        (st = dev_alloc(ctx, (void**)&tot, sizeof(int64_t))) ||
+        (st = dev_alloc(ctx, (void**)&ix->off, sizeof(int64_t) * (n + 1)))) {
+        cleanup();
+        panther_free_index(ix);
+        return st;
+    }
+    Src src{};
+    src.rows = p->rows;
+    src.R = p->R;
+    src.L = p->L;
+    src.stride = p->stride;
+    src.first = 1;
+    int32_t *ik = nullptr, *iv = nullptr, *ok = kA, *ov = vA;
+    int64_t count = 0;
+    for (int pass = 0; pass < passes; ++pass) {
+        int shift = pass * rb;
+        int64_t ntiles = pass == 0 ? tiles0 : ceil_div(count, IX_TILE);
+        if (ntiles < 1) ntiles = 1;
+        int64_t len = (int64_t)radix * ntiles;
+        hist_kernel<<<(unsigned)ntiles, IX_T, 0, s>>>(src, shift, radix, ntiles, counts);
+        ctx->launches++;
+        cudaError_t e = cudaMemcpyAsync(offs, counts, sizeof(int64_t) * len, cudaMemcpyDeviceToDevice, s);
+        if (e) { cleanup(); panther_free_index(ix); return cuda_err(ctx, e, "index scan copy"); }
+        if ((st = scan_exclusive_i64(ctx, offs, len))) { cleanup(); panther_free_index(ix); return st; }
+        if (pass == 0) {
+            // the number of pairs is needed to size the later passes
+            total_kernel<<<1, 1, 0, s>>>(counts, offs, len, tot);
+            ctx->launches++;
+            e = cudaMemcpyAsync(&count, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+            if (!e) e = cudaStreamSynchronize(s);
+            if (e) { cleanup(); panther_free_index(ix); return cuda_err(ctx, e, "index count"); }
+        }
+        scatter_kernel<<<(unsigned)ntiles, IX_T, 0, s>>>(src, shift, radix, ntiles, offs, ok, ov);
+        ctx->launches++;
+        e = cudaGetLastError();
+        if (e) { cleanup(); panther_free_index(ix); return cuda_err(ctx, e, "index scatter"); }
+        // next pass reads what this one wrote
+        src.first = 0;
+        src.keys = ok;
+        src.vals = ov;
+        src.count = count;
+        ik = ok; iv = ov;
+        ok = (ok == kA) ? kB : kA;
+        ov = (ov == vA) ? vB : vA;
+    }
+    ix->nnz = count;
+    offsets_kernel<<<(unsigned)ceil_div(count + 1, 256), 256, 0, s>>>(ik, count, n, ix->off, ctx->d_status);
+    ctx->launches++;
+    // keep the final value array as pid; release everything else
+    ix->pid = iv;
+    if (iv == vA) vA = nullptr; else vB = nullptr;
+    cleanup();
+    cudaError_t e = cudaGetLastError();
+    if (e) { panther_free_index(ix); return cuda_err(ctx, e, "index offsets"); }
+    *out = ix;
+    return PANTHER_OK;
+}

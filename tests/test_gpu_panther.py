@@ -1,0 +1,297 @@
+"""GPU parity of the Panther path against the CPU oracle (bit-exact, integer outputs).
+
+Everything goes through the C ABI (libpanther.so) via the ctypes binding.
+Inputs are seeded synthetic Chung-Lu graphs; expected values come only from
+oracle/.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pk():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_02577_gb300 as pk
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return pk
+
+
+@pytest.fixture(scope="module")
+def small():
+    return synth.workload_graph("small")
+
+
+def _run(pk, g, seed, R, T, mode, k=None, queries=None, plain=False, budget=None):
+    with pk.Panther(0) as P:
+        if budget:
+            pk.panther_set_scratch_budget(P.h.ctx, budget)
+        P.build_graph(g.row_ptr, g.col, g.w, pk.MODE_BOTH)
+        P.sample_paths(seed, R, T, mode)
+        out = {"paths": P.paths_tensor().cpu().numpy()}
+        P.build_index()
+        off, pid = P.index_tensors()
+        out["off"], out["pid"] = off.cpu().numpy(), pid.cpu().numpy()
+        if k:
+            q = torch.as_tensor(queries if queries is not None else np.arange(g.n, dtype=np.int32),
+                                dtype=torch.int32, device="cuda:0")
+            ids, cnt = P.topk(q, k, plain=plain)
+            P.sync()
+            out["ids"], out["cnt"] = ids.cpu().numpy(), cnt.cpu().numpy().astype(np.uint32)
+        P.sync()
+        out["launches"] = P.launches()
+    return out
+
+
+# ------------------------------------------------------------ Philox ---
+
+def test_philox_matches_curand_and_oracle(pk):
+    ctx = pk.panther_create(0)
+    try:
+        for (k0, k1, r0, c2, c3) in [(1, 0, 0, 0, 0), (0xDEADBEEF, 0x12345678, 2**32 - 5, 7, 3),
+                                     (0xFFFFFFFF, 0xFFFFFFFF, 2**40, 0xFFFF, 0x10)]:
+            n = 4096
+            out = torch.empty((n, 4), dtype=torch.int32, device="cuda:0")
+            ref = torch.empty((n, 4), dtype=torch.int32, device="cuda:0")
+            pk.panther_debug_philox(ctx, k0, k1, r0, c2, c3, n, out, ref)
+            a = out.cpu().numpy().view(np.uint32)
+            b = ref.cpu().numpy().view(np.uint32)
+            assert np.array_equal(a, b), "device Philox differs from curand"
+            for i in (0, 1, 17, n - 1):
+                r = r0 + i
+                o = oracle.philox4x32_10((r & 0xFFFFFFFF, r >> 32, c2, c3), (k0, k1))
+                assert np.array_equal(o, b[i]), "oracle Philox differs from curand"
+    finally:
+        pk.panther_destroy(ctx)
+
+
+# ------------------------------------------------------------ tables ---
+
+def _tables(pk, g):
+    with pk.Panther(0) as P:
+        P.build_graph(g.row_ptr, g.col, g.w, pk.MODE_BOTH)
+        al = torch.empty((max(g.m, 1), 4), dtype=torch.int32, device="cuda:0")
+        wide = pk.panther_debug_graph_tables(P.h.graph, al, None)
+        pre = torch.empty((max(g.m, 1), 4 if wide else 2), dtype=torch.int32, device="cuda:0")
+        pk.panther_debug_graph_tables(P.h.graph, None, pre)
+        return al.cpu().numpy().view(np.uint32), pre.cpu().numpy().view(np.uint32), wide
+
+
+def _big_row_graph():
+    # a hub of degree 5000 (CTA-per-row path) with skewed weights, plus a ring
+    n = 6000
+    rng = np.random.default_rng(4)
+    edges, ws = [], []
+    for u in range(1, 5001):
+        edges.append((0, u))
+        ws.append(int(rng.integers(1, 2**20)) if u % 7 else 1)
+    for u in range(1, n - 1):
+        edges.append((u, u + 1))
+        ws.append(int(rng.integers(1, 50)))
+    return synth.graph_from_edges(n, edges, ws)
+
+
+@pytest.mark.parametrize("which", ["small", "bigrow", "wide"])
+def test_transition_tables_match_oracle(pk, small, which):
+    if which == "small":
+        g = small
+    elif which == "bigrow":
+        g = _big_row_graph()
+    else:
+        # row sums beyond 2^32 switch the prefix table to 64-bit entries
+        g = synth.graph_from_edges(40, [(0, i) for i in range(1, 40)] + [(1, 2)],
+                                   [2**31 + i for i in range(1, 40)] + [5])
+    al, pre, wide = _tables(pk, g)
+    thr, ali = oracle.alias_tables(g)
+    gthr = al[:, 0].astype(np.uint64) | (al[:, 1].astype(np.uint64) << np.uint64(32))
+    assert np.array_equal(gthr[:g.m], thr[:g.m])
+    assert np.array_equal(al[:g.m, 2], g.col.view(np.uint32))
+    # alias column stored as the neighbour id
+    row_of = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    want_alias = g.col[g.row_ptr[row_of] + ali[:g.m]]
+    assert np.array_equal(al[:g.m, 3].view(np.int32), want_alias)
+    # prefix: inclusive cumulative weight per row
+    cum = np.zeros(g.m, dtype=np.uint64)
+    for v in range(g.n):
+        a, b = g.row_ptr[v], g.row_ptr[v + 1]
+        cum[a:b] = np.cumsum(g.w[a:b].astype(np.uint64))
+    if wide:
+        gcum = pre[:, 0].astype(np.uint64) | (pre[:, 1].astype(np.uint64) << np.uint64(32))
+        assert np.array_equal(gcum[:g.m], cum) and np.array_equal(pre[:g.m, 2].view(np.int32), g.col)
+    else:
+        assert np.array_equal(pre[:g.m, 0].astype(np.uint64), cum)
+        assert np.array_equal(pre[:g.m, 1].view(np.int32), g.col)
+    assert wide == (which == "wide")
+
+
+def test_invalid_graph_is_rejected(pk):
+    g = synth.graph_from_edges(5, [(0, 1), (1, 2), (3, 4)], [1, 2, 3])
+    with pk.Panther(0) as P:
+        w = g.w.copy()
+        w[0] = 7           # asymmetric weight
+        with pytest.raises(pk.PantherError):
+            P.build_graph(g.row_ptr, g.col, w)
+        col = g.col.copy()
+        col[0] = 0         # self-loop
+        with pytest.raises(pk.PantherError):
+            P.build_graph(g.row_ptr, col, g.w)
+        rp = g.row_ptr.copy()
+        rp[2] = rp[3] + 1  # offsets not monotone
+        with pytest.raises(pk.PantherError):
+            P.build_graph(rp, g.col, g.w)
+        P.build_graph(g.row_ptr, g.col, g.w)   # the valid graph still builds
+
+
+# ------------------------------------------------------------- paths ---
+
+@pytest.mark.parametrize("mode", ["prefix", "alias"])
+def test_paths_and_index_bit_exact_small_workload(pk, small, mode):
+    m = pk.MODE_PREFIX if mode == "prefix" else pk.MODE_ALIAS
+    om = oracle.PREFIX if mode == "prefix" else oracle.ALIAS
+    R, T = 200_000, 5
+    out = _run(pk, small, 1, R, T, m)
+    ref = oracle.sample_paths(small, 1, R, T, om)
+    assert np.array_equal(out["paths"], ref)
+    off, pid = oracle.build_index(small.n, ref)
+    assert np.array_equal(out["off"], off)
+    assert np.array_equal(out["pid"], pid)
+
+
+@pytest.mark.parametrize("T", [1, 2, 7, 9, 15, 20, 31])
+def test_paths_other_lengths(pk, T):
+    g = synth.chung_lu(3000, 6, 2.2, ("uniform", 1, 1000), seed=9)
+    R = 3001     # ragged: not a multiple of any tile
+    out = _run(pk, g, 12345, R, T, pk.MODE_ALIAS)
+    ref = oracle.sample_paths(g, 12345, R, T, oracle.ALIAS)
+    assert np.array_equal(out["paths"], ref)
+    off, pid = oracle.build_index(g.n, ref)
+    assert np.array_equal(out["off"], off) and np.array_equal(out["pid"], pid)
+
+
+def test_paths_wide_prefix_and_isolated(pk):
+    # 64-bit cumulative weights and isolated vertices (the walk stays put)
+    edges = [(0, i) for i in range(1, 30)] + [(1, 2), (2, 3)]
+    ws = [2**31 + 17 * i for i in range(1, 30)] + [3, 4]
+    g = synth.graph_from_edges(40, edges, ws)
+    for m, om in ((pk.MODE_PREFIX, oracle.PREFIX), (pk.MODE_ALIAS, oracle.ALIAS)):
+        out = _run(pk, g, 99, 5000, 6, m)
+        ref = oracle.sample_paths(g, 99, 5000, 6, om)
+        assert np.array_equal(out["paths"], ref)
+
+
+def test_counter_based_seeds_differ(pk, small):
+    a = _run(pk, small, 1, 1000, 5, pk.MODE_ALIAS)["paths"]
+    b = _run(pk, small, 2, 1000, 5, pk.MODE_ALIAS)["paths"]
+    assert not np.array_equal(a, b)
+    assert np.array_equal(a, oracle.sample_paths(small, 1, 1000, 5, oracle.ALIAS))
+
+
+# ------------------------------------------------------------- top-k ---
+
+@pytest.mark.parametrize("k", [1, 10, 33, 64])
+def test_topk_all_vertices_small_workload(pk, small, k):
+    R, T = 200_000, 5
+    out = _run(pk, small, 1, R, T, pk.MODE_ALIAS, k=k)
+    ref = oracle.sample_paths(small, 1, R, T, oracle.ALIAS)
+    o = oracle.Oracle(small.n, ref)
+    rid, rcnt = o.topk_many(np.arange(small.n), k)
+    assert np.array_equal(out["ids"], rid)
+    assert np.array_equal(out["cnt"], rcnt)
+
+
+def test_topk_plain_equals_batched_and_oracle(pk, small):
+    R, T, k = 50_000, 5, 10
+    rng = np.random.default_rng(0)
+    q = rng.integers(0, small.n, size=300).astype(np.int32)
+    a = _run(pk, small, 5, R, T, pk.MODE_PREFIX, k=k, queries=q, plain=True)
+    b = _run(pk, small, 5, R, T, pk.MODE_PREFIX, k=k, queries=q, plain=False)
+    assert np.array_equal(a["ids"], b["ids"]) and np.array_equal(a["cnt"], b["cnt"])
+    o = oracle.Oracle(small.n, oracle.sample_paths(small, 5, R, T, oracle.PREFIX))
+    rid, rcnt = o.topk_many(q, k)
+    assert np.array_equal(a["ids"], rid) and np.array_equal(a["cnt"], rcnt)
+    assert a["launches"] > b["launches"] + 250      # one launch per query
+
+
+def test_topk_global_tier_hubs(pk):
+    # hubs whose candidate bound exceeds the shared-memory table; a small
+    # scratch budget forces several rounds of global tables
+    g = synth.chung_lu(20_000, 12, 2.05, ("uniform", 1, 5), seed=2)
+    R, T, k = 300_000, 5, 12
+    hubs = synth.hub_set(g, 0.002)
+    q = np.concatenate([hubs, np.arange(0, 20_000, 97, dtype=np.int32)]).astype(np.int32)
+    out = _run(pk, g, 3, R, T, pk.MODE_ALIAS, k=k, queries=q, budget=64 << 20)
+    ref = oracle.sample_paths(g, 3, R, T, oracle.ALIAS)
+    o = oracle.Oracle(g.n, ref)
+    sizes = np.diff(o.off)
+    assert sizes[hubs].max() * 5 > 20_000            # some query is in the global tier
+    rid, rcnt = o.topk_many(q, k)
+    assert np.array_equal(out["ids"], rid)
+    assert np.array_equal(out["cnt"], rcnt)
+
+
+def test_topk_edge_cases(pk):
+    g = synth.graph_from_edges(6, [(0, 1), (1, 2), (2, 0), (3, 4)], [1, 2, 3, 4])  # 5 isolated
+    R, T = 400, 3
+    q = np.array([5, 0, 0, 3, 1, 5], dtype=np.int32)          # duplicates, isolated
+    out = _run(pk, g, 8, R, T, pk.MODE_ALIAS, k=7, queries=q)
+    o = oracle.Oracle(g.n, oracle.sample_paths(g, 8, R, T, oracle.ALIAS))
+    rid, rcnt = o.topk_many(q, 7)
+    assert np.array_equal(out["ids"], rid) and np.array_equal(out["cnt"], rcnt)
+    assert (out["ids"][0] == -1).all() and (out["cnt"][0] == 0).all()
+    with pk.Panther(0) as P:
+        P.build_graph(g.row_ptr, g.col, g.w)
+        P.sample_paths(1, 10, 2)
+        P.build_index()
+        empty = torch.empty(0, dtype=torch.int32, device="cuda:0")
+        P.topk(empty, 3)                                        # q = 0 is a no-op
+        bad = torch.tensor([0, 6], dtype=torch.int32, device="cuda:0")
+        P.topk(bad, 3)
+        with pytest.raises(pk.PantherError):
+            P.sync()                                            # out-of-range query reported
+        with pytest.raises(pk.PantherError):
+            P.topk(torch.zeros(1, dtype=torch.int32, device="cuda:0"), 65)
+
+
+def test_topk_host_io(pk, small):
+    with pk.Panther(0) as P:
+        P.build_graph(small.row_ptr, small.col, small.w)
+        P.sample_paths(1, 20_000, 5)
+        P.build_index()
+        q = np.arange(0, small.n, 3, dtype=np.int32)
+        ids = np.empty((q.shape[0], 5), np.int32)
+        cnt = np.empty((q.shape[0], 5), np.uint32)
+        pk.panther_topk(P.h.ctx, P.h.index, P.h.paths, q, q.shape[0], 5, ids, cnt,
+                        pk.TOPK_BATCHED | pk.IO_HOST)
+    o = oracle.Oracle(small.n, oracle.sample_paths(small, 1, 20_000, 5, oracle.ALIAS))
+    rid, rcnt = o.topk_many(q, 5)
+    assert np.array_equal(ids, rid) and np.array_equal(cnt, rcnt)
+
+
+def test_batched_workload_full_size_sampled(pk):
+    """N=1M Chung-Lu (mean degree 20, gamma 2.3, log-uniform weights), R from the
+    sample-size bound (eps 0.01, delta 0.1, c 0.5), 16,384 queries (half from the
+    top-1% degree set), top-5: every path compared, and top-5 of a sample of
+    queries including the heaviest."""
+    g = synth.workload_graph("batched")
+    R = oracle.sample_size(0.01, 0.1, 0.5, 5)
+    assert R == 33123
+    q = synth.query_mix(g, 8192, 8192, seed=1)
+    out = _run(pk, g, 1, R, 5, pk.MODE_ALIAS, k=5, queries=q)
+    ref = oracle.sample_paths(g, 1, R, 5, oracle.ALIAS)
+    assert np.array_equal(out["paths"], ref)
+    off, pid = oracle.build_index(g.n, ref)
+    assert np.array_equal(out["off"], off) and np.array_equal(out["pid"], pid)
+    o = oracle.Oracle(g.n, ref, off, pid)
+    sizes = np.diff(off)[q]
+    pick = np.unique(np.concatenate([np.argsort(-sizes)[:64], np.arange(0, q.shape[0], 37)]))
+    rid, rcnt = o.topk_many(q[pick], 5)
+    assert np.array_equal(out["ids"][pick], rid)
+    assert np.array_equal(out["cnt"][pick], rcnt)

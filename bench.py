@@ -1,0 +1,464 @@
+"""Benchmark of the Panther hot path on one or more GB300s (one process per GPU).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload scale|batched|small]
+                    [--impl ours|reference]
+
+One step is one pass of the Panther hot path over one synthetic graph:
+transition tables (Eq. 3) from the device-resident CSR, R random paths
+(Algorithm 3), the inverted index (Sec. 3.1), and top-k for every vertex
+(Algorithm 1). `value` is whole-job throughput in top-k queries per second
+(vertices answered per second, path sampling and indexing included: the
+"processing + query" of the paper's Table 2). Multi-GPU runs are independent
+replicas (weak scaling): every rank processes its own copy of the workload.
+
+Extra keys: per-stage timings with their roofline fractions, the batched vs
+one-launch-per-query comparison on the 1M-vertex batched-query workload, the
+oracle timed on a bounded sample on the host cores (`cpu_baseline`), the same
+step through the C ABI with host buffers (`e2e`), SM clocks sampled during the
+timed region, and the number of library kernel launches in it.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "paths sampled/s; top-k queries/s batched vs plain at 1 GB300; % of HBM roofline"
+
+# Algorithmic bytes per unit (sector-granular for random accesses):
+#   sampler (alias): per step one 32 B sector of the vertex record and one of
+#     the alias entry; per path T*64 B + the (T+1)*4 B row  -> 344 B at T=5
+#   index: per (vertex, path) pair 4 B key + 4 B id, read + written, per radix
+#     pass (3 passes)                                       -> 48 B / pair
+#   counting + top-k: per (vertex, path) pair of the index 4 B path id + one
+#     32 B path-row sector; per query 8 B*k of output
+SAMPLER_B_PER_PATH = lambda T: T * 64 + (T + 1) * 4
+INDEX_B_PER_PAIR = 48
+COUNT_B_PER_PAIR = 36
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _src_hash(*files):
+    h = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1504_02577_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+# DRAM traffic per launch of the dominant kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
+# source is unchanged; the capture and its command are in profiles/.
+NCU_TRAFFIC = {}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        try:
+            for ln in open(self.path):
+                f = [x.strip() for x in ln.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = float(f[2])
+                except ValueError:
+                    continue
+                for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                      "sw_power_cap"], f[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _workload(name):
+    import synth
+    p = dict(synth.WORKLOADS[name])
+    if name == "batched":
+        import oracle  # only for the closed-form R of Sec. 3.2? no: the library computes it
+    return p
+
+
+def _sample_size(p):
+    import paper_1504_02577_gb300 as pk
+    if "R" in p:
+        return p["R"]
+    return pk.panther_sample_size(p["eps"], p["delta"], p["c"], p["T"])
+
+
+# ------------------------------------------------------------ our arm ---
+def run_ours(args, ws, rank, local):
+    import torch
+    import synth
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_02577_gb300 as pk
+
+    torch.cuda.set_device(local)
+    p = synth.WORKLOADS[args.workload]
+    t0 = time.time()
+    g = synth.workload_graph(args.workload)
+    gen_s = time.time() - t0
+    R, T, k = _sample_size(p), p["T"], p["k"]
+    dev = f"cuda:{local}"
+    d_rp = torch.from_numpy(g.row_ptr).to(dev)
+    d_col = torch.from_numpy(g.col).to(dev)
+    d_w = torch.from_numpy(g.w.view(np.int32)).to(dev)
+    if args.workload == "batched":
+        q_host = synth.query_mix(g, p["q_uniform"], p["q_hub"], seed=1)
+    else:
+        q_host = np.arange(g.n, dtype=np.int32)
+    queries = torch.from_numpy(q_host).to(dev)
+    nq = int(q_host.shape[0])
+
+    P = pk.Panther(local)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    stages = ["tables", "sample", "index", "topk"]
+
+    def step(record=None):
+        s = P.stream
+        e = [ev() for _ in range(5)] if record is not None else None
+        if e: e[0].record(s)
+        P.build_graph(d_rp, d_col, d_w, pk.MODE_ALIAS)
+        if e: e[1].record(s)
+        P.sample_paths(1, R, T, pk.MODE_ALIAS)
+        if e: e[2].record(s)
+        P.build_index()
+        if e: e[3].record(s)
+        ids, cnt = P.topk(queries, k)
+        if e: e[4].record(s)
+        if record is not None:
+            record.append(e)
+        return ids, cnt
+
+    for _ in range(args.warmup):
+        step()
+    P.sync()
+    torch.cuda.synchronize()
+    _barrier(ws)
+    rec = []
+    l0 = P.launches()
+    with Clocks(local) as clk:
+        start, end = ev(), ev()
+        torch.cuda.synchronize()
+        start.record(P.stream)
+        for _ in range(args.steps):
+            step(rec)
+        end.record(P.stream)
+        torch.cuda.synchronize()
+    launches = P.launches() - l0
+    P.sync()
+    ms_total = start.elapsed_time(end)
+    ms_step = _max_over_ranks(ms_total / args.steps, ws)
+    stage_ms = {s: statistics.median(r[i].elapsed_time(r[i + 1]) for r in rec) for i, s in enumerate(stages)}
+    _barrier(ws)
+    clocks = clk.summary()
+
+    # index size for the algorithmic byte counts
+    _, _, _, nnz = pk.panther_index_view(P.h.index)
+    peak, peak_kind = _peaks()
+    algo = {
+        "sample": R * SAMPLER_B_PER_PATH(T),
+        "index": nnz * INDEX_B_PER_PAIR,
+        "topk": nnz * COUNT_B_PER_PAIR + nq * (16 + 8 * k),
+        "tables": g.m * (4 + 4 + 16 + 16) + g.n * 16,
+    }
+    stage_obj = {}
+    for s in stages:
+        gbs = algo[s] / (stage_ms[s] * 1e-3) / 1e9
+        stage_obj[s] = {"ms": round(stage_ms[s], 4), "algo_bytes": int(algo[s]), "achieved_gbs": round(gbs, 1),
+                        "frac": round(gbs / peak, 4)}
+    dom = max(stages, key=lambda s: stage_ms[s])
+    kernel_name = {"sample": "sample_kernel", "index": "radix index passes", "topk": "topk (persistent)",
+                   "tables": "graph tables"}[dom]
+    traffic = NCU_TRAFFIC.get(dom)
+    roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": stage_obj[dom]["achieved_gbs"], "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": stage_obj[dom]["frac"],
+                "traffic": traffic}
+
+    value = ws * nq / (ms_step * 1e-3)
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32/u64 (integer counts)", "data": "synthetic",
+        "config": {"workload": args.workload, "graph": f"Chung-Lu n={g.n} m={g.m} mean_deg={p['mean_deg']} "
+                   f"gamma={p['gamma']} weights={p['weights'][0]}[{p['weights'][1]},{p['weights'][2]}] seed=1",
+                   "R": R, "T": T, "k": k, "queries": nq, "mode": "alias",
+                   "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (graph and paths)"},
+        "paths_sampled_per_s": round(ws * R / (stage_ms["sample"] * 1e-3), 1),
+        "stages": stage_obj,
+        "roofline": roofline,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "graph_gen_s": round(gen_s, 2),
+    }
+
+    # batched vs plain on the 1M-vertex batched-query workload (16,384 queries, top-5)
+    if rank == 0 and not args.no_extras and args.workload != "batched":
+        out["batched_vs_plain"] = batched_vs_plain(pk, torch, local)
+
+    # end to end through the C ABI with host buffers
+    if not args.no_extras:
+        out["e2e"] = e2e(pk, torch, P, g, R, T, k, q_host, args, ws)
+    P.close()
+
+    if rank == 0 and ws == 1 and not args.no_extras:
+        out["cpu_baseline"] = cpu_baseline(args.workload, g, R, T, k, nq)
+    return out
+
+
+def batched_vs_plain(pk, torch, local):
+    import synth
+    p = synth.WORKLOADS["batched"]
+    g = synth.workload_graph("batched")
+    R = pk.panther_sample_size(p["eps"], p["delta"], p["c"], p["T"])
+    q = torch.from_numpy(synth.query_mix(g, p["q_uniform"], p["q_hub"], seed=1)).to(f"cuda:{local}")
+    res = {}
+    with pk.Panther(local) as P:
+        P.build_graph(g.row_ptr, g.col, g.w, pk.MODE_ALIAS)
+        P.sample_paths(1, R, p["T"], pk.MODE_ALIAS)
+        P.build_index()
+        for plain in (False, True):
+            reps = 10 if not plain else 2
+            for _ in range(2):
+                P.topk(q, p["k"], plain=plain)
+            P.sync()
+            torch.cuda.synchronize()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = P.launches()
+            s.record(P.stream)
+            for _ in range(reps):
+                a = P.topk(q, p["k"], plain=plain)
+            e.record(P.stream)
+            torch.cuda.synchronize()
+            ms = s.elapsed_time(e) / reps
+            res["plain" if plain else "batched"] = {"ms": round(ms, 4), "queries_per_s": round(q.shape[0] / ms * 1e3, 1),
+                                                     "launches_per_call": (P.launches() - l0) // reps}
+            if plain:
+                pl = a
+            else:
+                bt = a
+        P.sync()
+        res["identical"] = bool(torch.equal(pl[0], bt[0]) and torch.equal(pl[1], bt[1]))
+    res["speedup"] = round(res["plain"]["ms"] / res["batched"]["ms"], 2)
+    res["workload"] = f"Chung-Lu n={g.n} mean_deg=20 gamma=2.3 loguniform[1,1024]; R={R} T=5; 16384 queries; top-5"
+    return res
+
+
+def e2e(pk, torch, P, g, R, T, k, q_host, args, ws):
+    """The same step through the C ABI with HOST buffers: CSR in, top-k out."""
+    rp = torch.from_numpy(g.row_ptr).pin_memory().numpy()
+    col = torch.from_numpy(g.col).pin_memory().numpy()
+    w = torch.from_numpy(g.w.view(np.int32)).pin_memory().numpy().view(np.uint32)
+    qh = torch.from_numpy(q_host).pin_memory().numpy()
+    nq = q_host.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int32).pin_memory().numpy()
+    cnt = torch.empty((nq, k), dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+    ctx = P.h.ctx
+
+    def step():
+        gh = pk.panther_build_graph(ctx, g.n, g.m, rp, col, w, pk.MEM_HOST, pk.MODE_ALIAS)
+        ph = pk.panther_sample_paths(ctx, gh, 1, R, T, pk.MODE_ALIAS)
+        ih = pk.panther_build_index(ctx, ph)
+        pk.panther_topk(ctx, ih, ph, qh, nq, k, ids, cnt, pk.TOPK_BATCHED | pk.IO_HOST)
+        pk.panther_free_index(ih)
+        pk.panther_free_paths(ph)
+        pk.panther_free_graph(gh)
+
+    steps = max(1, min(args.steps, 3))
+    step()
+    torch.cuda.synchronize()
+    _barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    dt = _max_over_ranks((time.perf_counter() - t0) / steps, ws)
+    h2d = g.row_ptr.nbytes + g.col.nbytes + g.w.nbytes + q_host.nbytes
+    d2h = ids.nbytes + cnt.nbytes
+    return {"value": round(ws * nq / dt, 1), "unit": "queries/s", "ms_per_step": round(dt * 1e3, 3),
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+# ---------------------------------------------------------- CPU oracle ---
+def cpu_baseline(workload, g, R, T, k, nq, budget_s: float = 20.0):
+    """The oracle as it stands (single-threaded C) on a bounded sample of the workload.
+
+    Sample: alias tables of the whole graph, R_s = R/f paths, their index, and
+    top-k for up to 2,000 vertices. Per-step CPU seconds are extrapolated as
+    t_tables + (t_paths + t_index) * f + t_per_query * nq * f, since the
+    per-query work scales with |P_v|, i.e. with R.
+    """
+    import oracle
+    t0 = time.perf_counter()
+    tables = oracle.alias_tables(g)
+    t_tab = time.perf_counter() - t0
+    f = max(1, int(math.ceil(R / 200_000)))
+    Rs = max(1, R // f)
+    t0 = time.perf_counter()
+    P = oracle.sample_paths(g, 1, Rs, T, oracle.ALIAS, tables=tables)
+    t_paths = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    off, pid = oracle.build_index(g.n, P)
+    t_index = time.perf_counter() - t0
+    o = oracle.Oracle(g.n, P, off, pid)
+    rng = np.random.default_rng(5)
+    qs = rng.integers(0, g.n, size=min(2000, g.n)).astype(np.int32)
+    t0 = time.perf_counter()
+    done = 0
+    for v in qs:
+        o.topk(int(v), k)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    t_q = (time.perf_counter() - t0) / max(done, 1)
+    step_s = t_tab + (t_paths + t_index) * f + t_q * nq * f
+    return {"value": round(nq / step_s, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": f"alias tables of the full graph ({t_tab:.1f}s), {Rs} of {R} paths, their index, "
+                      f"top-{k} of {done} random vertices; per-step time = tables + (paths+index)*{f} "
+                      f"+ per-query*{nq}*{f}",
+            "step_s_extrapolated": round(step_s, 2)}
+
+
+def run_reference(args, ws, rank):
+    """The oracle timed on the host cores as the reference arm (bounded samples)."""
+    if rank != 0:
+        return None
+    import synth
+    p = synth.WORKLOADS[args.workload]
+    g = synth.workload_graph(args.workload)
+    import oracle
+    oracle.build()
+    if "R" in p:
+        R = p["R"]
+    else:
+        R = oracle.sample_size(p["eps"], p["delta"], p["c"], p["T"])
+    nq = g.n if args.workload != "batched" else p["q_uniform"] + p["q_hub"]
+    budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(args.workload, g, R, p["T"], p["k"], nq, budget_s=budget)
+        if i >= args.warmup:
+            vals.append(cb)
+    v = statistics.median(c["value"] for c in vals)
+    step_s = statistics.median(c["step_s_extrapolated"] for c in vals)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/u64 (integer counts)",
+            "data": "synthetic", "config": {"workload": args.workload, "R": R, "T": p["T"], "k": p["k"]},
+            "cpu_baseline": {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="scale", choices=["scale", "batched", "small"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and batched-vs-plain")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    out = run_ours(args, ws, rank, local)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

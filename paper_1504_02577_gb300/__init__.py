@@ -286,10 +286,22 @@ class Panther:
         import torch
         self.torch = torch
         self.device = device
-        if stream is None:
-            stream = torch.cuda.current_stream(device)
-        self.stream = stream
-        self.h = Handles(panther_create(device, stream.cuda_stream))
+        # the library enqueues on this (non-default) stream; results are handed
+        # back to the caller's current stream by _enter/_leave
+        self.stream = stream if stream is not None else torch.cuda.Stream(device)
+        self.h = Handles(panther_create(device, self.stream.cuda_stream))
+
+    def _enter(self, *inputs):
+        """Order the library stream after the caller's stream (inputs ready)."""
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+
+    def _leave(self, *outputs):
+        """Order the caller's stream after the library stream; keep outputs alive."""
+        cur = self.torch.cuda.current_stream(self.device)
+        cur.wait_stream(self.stream)
+        for t in outputs:
+            if t is not None and hasattr(t, "record_stream"):
+                t.record_stream(cur)
 
     def close(self):
         h = self.h
@@ -316,6 +328,7 @@ class Panther:
         mem = MEM_HOST if isinstance(row_ptr, np.ndarray) else MEM_DEVICE
         if self.h.graph:
             panther_free_graph(self.h.graph)
+        self._enter()
         self.h.graph = panther_build_graph(self.h.ctx, n, m, row_ptr, col, w, mem, modes)
         self.n = n
         return self.h.graph
@@ -330,8 +343,10 @@ class Panther:
         """int32[R][T+1] copy of the sampled rows (device)."""
         torch = self.torch
         rows, R, L, stride = panther_paths_view(self.h.paths)
-        t = _device_view(torch, rows, (R, stride), torch.int32, self.device)
-        return t[:, :L].contiguous()
+        with torch.cuda.stream(self.stream):
+            t = _device_view(torch, rows, (R, stride), torch.int32, self.device)[:, :L].contiguous()
+        self._leave(t)
+        return t
 
     def build_index(self):
         if self.h.index:
@@ -342,17 +357,23 @@ class Panther:
     def index_tensors(self):
         torch = self.torch
         off, pid, n, nnz = panther_index_view(self.h.index)
-        o = _device_view(torch, off, (n + 1,), torch.int64, self.device).clone()
-        p = _device_view(torch, pid, (max(nnz, 1),), torch.int32, self.device)[:nnz].clone()
+        with torch.cuda.stream(self.stream):
+            o = _device_view(torch, off, (n + 1,), torch.int64, self.device).clone()
+            p = _device_view(torch, pid, (max(nnz, 1),), torch.int32, self.device)[:nnz].clone()
+        self._leave(o, p)
         return o, p
 
     def topk(self, queries, k: int, plain: bool = False):
         torch = self.torch
         q = int(queries.shape[0])
-        ids = torch.empty((q, k), dtype=torch.int32, device=queries.device)
-        cnt = torch.empty((q, k), dtype=torch.int32, device=queries.device)
+        self._enter()
+        with torch.cuda.stream(self.stream):
+            ids = torch.empty((q, k), dtype=torch.int32, device=queries.device)
+            cnt = torch.empty((q, k), dtype=torch.int32, device=queries.device)
+        queries.record_stream(self.stream)
         panther_topk(self.h.ctx, self.h.index, self.h.paths, queries, q, k, ids, cnt,
                      TOPK_PLAIN if plain else TOPK_BATCHED)
+        self._leave(ids, cnt)
         return ids, cnt
 
     def vectors(self, D: int = 50):
@@ -364,14 +385,21 @@ class Panther:
     def theta_tensor(self):
         torch = self.torch
         th, n, D = pantherpp_vecs_view(self.h.vecs)
-        return _device_view(torch, th, (n, D), torch.int32, self.device).clone()
+        with torch.cuda.stream(self.stream):
+            t = _device_view(torch, th, (n, D), torch.int32, self.device).clone()
+        self._leave(t)
+        return t
 
     def knn(self, queries, k: int, fp32: bool = False):
         torch = self.torch
         q = int(queries.shape[0])
-        ids = torch.empty((q, k), dtype=torch.int32, device=queries.device)
-        d2 = torch.empty((q, k), dtype=torch.int64, device=queries.device)
+        self._enter()
+        with torch.cuda.stream(self.stream):
+            ids = torch.empty((q, k), dtype=torch.int32, device=queries.device)
+            d2 = torch.empty((q, k), dtype=torch.int64, device=queries.device)
+        queries.record_stream(self.stream)
         pantherpp_knn(self.h.ctx, self.h.vecs, queries, q, k, ids, d2, KNN_FP32 if fp32 else KNN_BF16_SCREEN)
+        self._leave(ids, d2)
         return ids, d2
 
     def sync(self):

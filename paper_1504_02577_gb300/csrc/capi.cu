@@ -190,7 +190,11 @@ void pantherpp_free_vecs(pantherpp_vecs* v) {
     if (!v) return;
     panther_ctx* c = v->ctx;
     dev_free(c, v->theta);
-    dev_free(c, v->bf);
+    dev_free(c, v->B);
+    dev_free(c, v->cid);
+    dev_free(c, v->cnrm);
+    dev_free(c, v->cncf);
+    dev_free(c, v->ctile);
     dev_free(c, v->norm2);
     dev_free(c, v->nrm);
     dev_free(c, v->exact);

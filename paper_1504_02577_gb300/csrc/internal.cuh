@@ -68,11 +68,17 @@ struct pantherpp_vecs {
     int64_t n = 0;
     int D = 0;
     uint32_t* theta = nullptr;       // [n][D]
-    uint16_t* bf = nullptr;          // [n][64] bf16 bits, zero padded
     uint64_t* norm2 = nullptr;       // [n] exact squared norms
     float* nrm = nullptr;            // [n] sqrt(norm2) rounded up (for the error bound)
     uint8_t* exact = nullptr;        // [n] 1 if every entry <= 256 (BF16-exact row)
     uint32_t max_val = 0;
+    // candidate side of the screening GEMM, exact rows first
+    int64_t npad = 0, nexact = 0;    // positions (multiple of 256), exact positions
+    uint16_t* B = nullptr;           // [npad][64] bf16 candidate rows
+    int32_t* cid = nullptr;          // [npad] vertex at each position (-1 padding)
+    float* cnrm = nullptr;           // [npad] |b| rounded up
+    float* cncf = nullptr;           // [npad] |b|^2 rounded up
+    uint8_t* ctile = nullptr;        // [npad/256] 1 if the tile holds only exact rows
 };
 
 // ------------------------------------------------------------ host helpers ---

@@ -263,76 +263,85 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 }
 
 // ---------------------------------------------------------- selection ---
+// Per query row: the k best keys live in shared memory (ascending by
+// (key, id)); only the k-th key and id stay in registers for the fast test.
 struct Row {
     float thr;       // key of the k-th entry (+inf until k entries)
     int thr_id;
     int n;           // entries held
-    int qid;         // query vertex (-1: padding row)
-    bool exact;
-    float anrm;      // KN_ALPHA * |a|
     int scount;      // shortlist entries appended
-    float2* list;    // k entries {key, id bits}, ascending
 };
 
-__device__ __forceinline__ void row_insert(Row& r, int k, float key, int id) {
-    int i = r.n < k ? r.n : k - 1;
-    if (r.n < k) ++r.n;
+struct RowConst {
+    int qid;         // query vertex (-1: padding row)
+    bool exact;
+    float anrm;      // KN_ALPHA * |a| (BF16) or 2 eps |a| (FP32)
+    float2* list;    // k entries {key, id bits}
+    int32_t* sl;     // shortlist
+    int* overflow;
+    int k;
+};
+
+// insert (key, id) (caller checked it beats the k-th entry); out of line: rare
+__device__ __noinline__ Row row_insert(Row r, const RowConst& c, float key, int id) {
+    int i = r.n < c.k ? r.n : c.k - 1;
+    if (r.n < c.k) ++r.n;
     while (i > 0) {
-        float2 e = r.list[i - 1];
+        float2 e = c.list[i - 1];
         int eid = __float_as_int(e.y);
         if (e.x < key || (e.x == key && eid < id)) break;
-        r.list[i] = e;
+        c.list[i] = e;
         --i;
     }
-    r.list[i] = make_float2(key, __int_as_float(id));
-    if (r.n == k) {
-        float2 last = r.list[k - 1];
+    c.list[i] = make_float2(key, __int_as_float(id));
+    if (r.n == c.k) {
+        float2 last = c.list[c.k - 1];
         r.thr = last.x;
         r.thr_id = __float_as_int(last.y);
     }
+    return r;
 }
 
-__device__ __forceinline__ void take_exact(Row& r, int k, float y, int cid) {
-    if (cid < 0 || cid == r.qid) return;
-    if (y < r.thr || (y == r.thr && cid < r.thr_id)) row_insert(r, k, y, cid);
+__device__ __forceinline__ Row take_exact(Row r, const RowConst& c, float y, int cid) {
+    if (cid < 0 || cid == c.qid) return r;
+    if (y < r.thr || (y == r.thr && cid < r.thr_id)) r = row_insert(r, c, y, cid);
+    return r;
 }
 
-__device__ __forceinline__ void take_bounded(Row& r, int k, float y, float E, int cid, bool cexact, int32_t* sl,
-                                             int* overflow) {
-    if (cid < 0 || cid == r.qid) return;
-    if (r.exact && cexact) {
-        take_exact(r, k, y, cid);
-        return;
-    }
-    if (__fsub_rd(y, E) > r.thr) return;
-    if (r.scount < KN_SCAP) sl[r.scount] = cid; else *overflow = 1;
+// a pair whose screened value carries an error bound E
+__device__ __noinline__ Row take_bounded(Row r, const RowConst& c, float y, float E, int cid, bool cexact) {
+    if (cid < 0 || cid == c.qid) return r;
+    if (c.exact && cexact) return take_exact(r, c, y, cid);
+    if (__fsub_rd(y, E) > r.thr) return r;
+    if (r.scount < KN_SCAP) c.sl[r.scount] = cid; else *c.overflow = 1;
     ++r.scount;
     float ub = __fadd_ru(y, E);
-    if (ub < r.thr || (ub == r.thr && cid < r.thr_id)) row_insert(r, k, ub, cid);
+    if (ub < r.thr || (ub == r.thr && cid < r.thr_id)) r = row_insert(r, c, ub, cid);
+    return r;
 }
 
-// one group of 32 screened values y (columns c0..c0+31 of the tile)
-__device__ __forceinline__ void select_group(Row& r, int k, const float* y, bool fast, const int32_t* cid,
-                                             const float* cnrm, const float* cncf, int64_t pos0, int64_t nexact,
-                                             int32_t* sl, int* overflow) {
-    if (r.qid < 0) return;
+// one group of 32 screened values y (columns pos0 .. pos0+31)
+__device__ __forceinline__ Row select_group(Row r, const RowConst& c, const float (&y)[32], bool fast,
+                                            const int32_t* cid, const float* cnrm, const float* cncf, int64_t pos0,
+                                            int64_t nexact) {
+    if (c.qid < 0) return r;
     if (fast) {
         float m = y[0];
 #pragma unroll
         for (int j = 1; j < 32; ++j) m = fminf(m, y[j]);
         if (m <= r.thr) {
-#pragma unroll 1
+#pragma unroll
             for (int j = 0; j < 32; ++j)
-                if (y[j] <= r.thr) take_exact(r, k, y[j], cid[j]);
+                if (y[j] <= r.thr) r = take_exact(r, c, y[j], cid[j]);
         }
     } else {
-#pragma unroll 1
+#pragma unroll
         for (int j = 0; j < 32; ++j) {
-            float E = fmaf(r.anrm, cnrm[j], fmaf(KN_BETA, cncf[j], 1.0f)) * 1.0001f;
-            if (__fsub_rd(y[j], E) <= r.thr)
-                take_bounded(r, k, y[j], E, cid[j], pos0 + j < nexact, sl, overflow);
+            float E = fmaf(c.anrm, cnrm[j], fmaf(KN_BETA, cncf[j], 1.0f)) * 1.0001f;
+            if (__fsub_rd(y[j], E) <= r.thr) r = take_bounded(r, c, y[j], E, cid[j], pos0 + j < nexact);
         }
     }
+    return r;
 }
 
 struct ScreenArgs {
@@ -466,16 +475,9 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
         int64_t it = 0;
         for (int64_t qt = blockIdx.x; qt < S.nqt; qt += gridDim.x) {
             const int64_t slot = qt * KN_M + row;
-            Row r;
-            r.thr = __int_as_float(0x7f800000);
-            r.thr_id = 0x7fffffff;
-            r.n = 0;
-            r.qid = S.qv[slot];
-            r.exact = S.qexact[slot] != 0;
-            r.anrm = KN_ALPHA * S.qnrm[slot];
-            r.scount = 0;
-            r.list = mylist;
-            int32_t* sl = S.shortlist + slot * KN_SCAP;
+            Row r{__int_as_float(0x7f800000), 0x7fffffff, 0, 0};
+            const RowConst rc{S.qv[slot], S.qexact[slot] != 0, KN_ALPHA * S.qnrm[slot], mylist,
+                              S.shortlist + slot * KN_SCAP, S.overflow + slot, S.k};
             const bool qtile_exact = S.qtile[qt] != 0;
             bool ok = true;
             for (int64_t ct = 0; ct < S.nct; ++ct, ++it) {
@@ -497,8 +499,8 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
                     float y[32];
                     __syncwarp();
                     tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + b * KN_N + g * 32, y);
-                    select_group(r, S.k, y, fast, cid + g * 32, cnrm + g * 32, cncf + g * 32,
-                                 ct * KN_N + g * 32, S.nexact, sl, S.overflow + slot);
+                    r = select_group(r, rc, y, fast, cid + g * 32, cnrm + g * 32, cncf + g * 32,
+                                     ct * KN_N + g * 32, S.nexact);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -509,7 +511,7 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
             }
             if (!ok) break;
             for (int i = 0; i < S.k; ++i)
-                S.lists[slot * S.k + i] = i < r.n ? r.list[i] : make_float2(0.f, __int_as_float(-1));
+                S.lists[slot * S.k + i] = i < r.n ? mylist[i] : make_float2(0.f, __int_as_float(-1));
             S.scount[slot] = r.scount;
         }
     }
@@ -523,36 +525,28 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
 // One thread per query row, candidates streamed through shared memory in
 // tiles of 256; y = |b|^2 - 2 a.b with the dot product in FP32 FMAs. Bound:
 // |y_hat - y| <= (D+3) 2^-23 (2|a||b| + |b|^2) + 1.
-constexpr int F_T = 128, F_TILE = 64;
+constexpr int F_T = 128, F_TILE = 32;
 
 __global__ void __launch_bounds__(F_T) fp32_kernel(const uint32_t* __restrict__ theta, int D, const int32_t* __restrict__ qv,
-                                                   const uint8_t* __restrict__ qexact, const float* __restrict__ qnrm,
-                                                   int64_t qpad, const int32_t* __restrict__ cidv,
-                                                   const float* __restrict__ cnrmv, const float* __restrict__ cncfv,
-                                                   int64_t npad, int64_t nexact, int k, float2* __restrict__ lists,
-                                                   int32_t* __restrict__ shortlist, int32_t* __restrict__ scount,
-                                                   int* __restrict__ overflow) {
+                                                   const float* __restrict__ qnrm, int64_t qpad,
+                                                   const int32_t* __restrict__ cidv, const float* __restrict__ cnrmv,
+                                                   const float* __restrict__ cncfv, int64_t npad, int k,
+                                                   float2* __restrict__ lists, int32_t* __restrict__ shortlist,
+                                                   int32_t* __restrict__ scount, int* __restrict__ overflow) {
     __shared__ float cb[F_TILE][KN_K];
     __shared__ float cn2[F_TILE], cnr[F_TILE];
     __shared__ int cidx[F_TILE];
     __shared__ float2 lst[F_T * KN_KMAX];
     const int64_t slot = (int64_t)blockIdx.x * F_T + threadIdx.x;
-    float a[KN_K];
-    Row r;
-    r.thr = __int_as_float(0x7f800000);
-    r.thr_id = 0x7fffffff;
-    r.n = 0;
-    r.qid = slot < qpad ? qv[slot] : -1;
-    r.exact = false;   // FP32 products are not exact in general: every pair is bounded
-    const float qn = slot < qpad ? qnrm[slot] : 0.f;
     const float epsD = (float)(D + 3) * (1.0f / 8388608.0f);
-    r.anrm = 2.0f * epsD * qn;
-    r.scount = 0;
-    r.list = lst + threadIdx.x * KN_KMAX;
-    int32_t* sl = shortlist + (slot < qpad ? slot : 0) * KN_SCAP;
-    int ovf = 0;
+    const int qid = slot < qpad ? qv[slot] : -1;
+    // FP32 products are not exact in general: every pair carries a bound
+    const RowConst rc{qid, false, 2.0f * epsD * (slot < qpad ? qnrm[slot] : 0.f), lst + threadIdx.x * KN_KMAX,
+                      shortlist + (slot < qpad ? slot : 0) * KN_SCAP, overflow + (slot < qpad ? slot : 0), k};
+    Row r{__int_as_float(0x7f800000), 0x7fffffff, 0, 0};
+    float a[KN_K];
 #pragma unroll
-    for (int d = 0; d < KN_K; ++d) a[d] = (r.qid >= 0 && d < D) ? (float)theta[(int64_t)r.qid * D + d] : 0.f;
+    for (int d = 0; d < KN_K; ++d) a[d] = (qid >= 0 && d < D) ? (float)theta[(int64_t)qid * D + d] : 0.f;
     for (int64_t c0 = 0; c0 < npad; c0 += F_TILE) {
         __syncthreads();
         for (int i = threadIdx.x; i < F_TILE * KN_K; i += F_T) {
@@ -566,20 +560,19 @@ __global__ void __launch_bounds__(F_T) fp32_kernel(const uint32_t* __restrict__ 
             cnr[threadIdx.x] = cnrmv[c0 + threadIdx.x];
         }
         __syncthreads();
-        if (r.qid < 0) continue;
+        if (qid < 0) continue;
         for (int c = 0; c < F_TILE; ++c) {
             float s = 0.f;
 #pragma unroll
             for (int d = 0; d < KN_K; ++d) s = fmaf(a[d], cb[c][d], s);
             float y = fmaf(-2.0f, s, cn2[c]);
-            float E = (fmaf(r.anrm, cnr[c], epsD * cn2[c]) + 1.0f) * 1.0001f;
-            if (__fsub_rd(y, E) <= r.thr) take_bounded(r, k, y, E, cidx[c], false, sl, &ovf);
+            float E = (fmaf(rc.anrm, cnr[c], epsD * cn2[c]) + 1.0f) * 1.0001f;
+            if (__fsub_rd(y, E) <= r.thr) r = take_bounded(r, rc, y, E, cidx[c], false);
         }
     }
     if (slot < qpad) {
-        for (int i = 0; i < k; ++i) lists[slot * k + i] = i < r.n ? r.list[i] : make_float2(0.f, __int_as_float(-1));
+        for (int i = 0; i < k; ++i) lists[slot * k + i] = i < r.n ? rc.list[i] : make_float2(0.f, __int_as_float(-1));
         scount[slot] = r.scount;
-        if (ovf) overflow[slot] = 1;
     }
 }
 
@@ -759,21 +752,6 @@ __global__ void fill_i32(int32_t* p, int64_t n, int32_t v) {
 }  // namespace
 
 // ---------------------------------------------------------------- host ---
-struct KnnExtra {
-    uint16_t* B = nullptr;       // [npad][64] candidate rows (permuted)
-    int32_t* cid = nullptr;      // [npad]
-    float* cnrm = nullptr;
-    float* cncf = nullptr;
-    uint8_t* ctile = nullptr;    // [npad/256]
-    int64_t npad = 0, nexact = 0;
-};
-
-// the extra buffers live next to the public handle
-struct pantherpp_vecs_ext {
-    pantherpp_vecs base;
-    KnnExtra x;
-};
-
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn(panther_ctx* ctx) {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -815,8 +793,7 @@ extern "C" panther_status pantherpp_vectors(panther_ctx* ctx, const panther_inde
     cudaSetDevice(ctx->device);
     cudaStream_t s = ctx->stream;
     const int64_t n = ix->n;
-    auto* e = new pantherpp_vecs_ext();
-    pantherpp_vecs* v = &e->base;
+    pantherpp_vecs* v = new pantherpp_vecs();
     v->ctx = ctx;
     v->n = n;
     v->D = D;
@@ -854,7 +831,7 @@ extern "C" panther_status pantherpp_vectors(panther_ctx* ctx, const panther_inde
     v->max_val = hmax;
     if (hmax >= (1u << 29))
         return fail(set_err(ctx, PANTHER_EOVERFLOW, "a count reaches 2^29: squared distances could overflow"));
-    KnnExtra& x = e->x;
+    pantherpp_vecs& x = *v;
     x.nexact = last_scan + last_flag;
     x.npad = ceil_div(n, KN_N) * KN_N;
     int32_t* perm = nullptr;
@@ -887,20 +864,9 @@ extern "C" panther_status pantherpp_vectors(panther_ctx* ctx, const panther_inde
     return PANTHER_OK;
 }
 
-void knn_free_extra(pantherpp_vecs* v) {
-    auto* e = reinterpret_cast<pantherpp_vecs_ext*>(v);
-    panther_ctx* c = v->ctx;
-    dev_free(c, e->x.B);
-    dev_free(c, e->x.cid);
-    dev_free(c, e->x.cnrm);
-    dev_free(c, e->x.cncf);
-    dev_free(c, e->x.ctile);
-}
-
 static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* v, const int32_t* queries, int64_t q, int k,
                               int32_t* ids, uint64_t* d2, bool fp32) {
-    const auto* e = reinterpret_cast<const pantherpp_vecs_ext*>(v);
-    const KnnExtra& x = e->x;
+    const pantherpp_vecs& x = *v;
     cudaStream_t s = ctx->stream;
     const int64_t n = v->n;
     const int64_t qpad = ceil_div(q, KN_M) * KN_M;
@@ -965,8 +931,8 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* v, const i
         screen_kernel<<<(unsigned)grid, KN_THREADS, KN_SMEM_BYTES, s>>>(tmA, tmB, S);
         ctx->launches++;
     } else {
-        fp32_kernel<<<(unsigned)(qpad / F_T), F_T, 0, s>>>(v->theta, v->D, qv, qex, qn, qpad, x.cid, x.cnrm, x.cncf,
-                                                            x.npad, x.nexact, k, lists, sl, sc, ovf);
+        fp32_kernel<<<(unsigned)(qpad / F_T), F_T, 0, s>>>(v->theta, v->D, qv, qn, qpad, x.cid, x.cnrm, x.cncf,
+                                                            x.npad, k, lists, sl, sc, ovf);
         ctx->launches++;
     }
     PCK(ctx, cudaGetLastError());

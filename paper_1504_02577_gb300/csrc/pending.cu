@@ -3,20 +3,6 @@
 #include "internal.cuh"
 
 extern "C" {
-panther_status pantherpp_vectors(panther_ctx* ctx, const panther_index*, const panther_paths*, int,
-                                 pantherpp_vecs** out) {
-    if (out) *out = nullptr;
-    return set_err(ctx, PANTHER_EINVAL, "pantherpp_vectors is not available in this build");
-}
-panther_status pantherpp_knn(panther_ctx* ctx, const pantherpp_vecs*, const int32_t*, int64_t, int, int32_t*,
-                             uint64_t*, int) {
-    return set_err(ctx, PANTHER_EINVAL, "pantherpp_knn is not available in this build");
-}
-panther_status pantherpp_knn_stats(panther_ctx* ctx, int64_t stats[4]) {
-    if (!ctx || !stats) return PANTHER_EINVAL;
-    for (int i = 0; i < 4; ++i) stats[i] = ctx->knn_stats[i];
-    return PANTHER_OK;
-}
 panther_status panther_serve_create(int, const panther_index*, const panther_paths*, const pantherpp_vecs*, int64_t,
                                     int, int, panther_server** out) {
     if (out) *out = nullptr;

@@ -1,0 +1,149 @@
+"""GPU parity of Panther++ (theta vectors and exact k-NN) against the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pk():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_02577_gb300 as pk
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return pk
+
+
+def _vectors(pk, g, seed, R, T, D, queries=None, k=None, fp32=False, both=False):
+    with pk.Panther(0) as P:
+        P.build_graph(g.row_ptr, g.col, g.w, pk.MODE_ALIAS)
+        P.sample_paths(seed, R, T, pk.MODE_ALIAS)
+        P.build_index()
+        P.vectors(D)
+        out = {"theta": P.theta_tensor().cpu().numpy().view(np.uint32)}
+        if k:
+            q = torch.as_tensor(queries, dtype=torch.int32, device="cuda:0")
+            forms = [False, True] if both else [fp32]
+            for f in forms:
+                ids, d2 = P.knn(q, k, fp32=f)
+                P.sync()
+                out[("fp32" if f else "bf16")] = (ids.cpu().numpy(), d2.cpu().numpy().view(np.uint64))
+            out["stats"] = pk.pantherpp_knn_stats(P.h.ctx)
+        P.sync()
+    return out
+
+
+def _oracle_theta(g, seed, R, T, D):
+    P = oracle.sample_paths(g, seed, R, T, oracle.ALIAS)
+    return oracle.Oracle(g.n, P).theta_all(D)
+
+
+@pytest.fixture(scope="module")
+def small_case():
+    g = synth.workload_graph("small")
+    th = _oracle_theta(g, 1, 200_000, 5, 50)
+    return g, th
+
+
+def test_theta_bit_exact_small_workload(pk, small_case):
+    g, th = small_case
+    out = _vectors(pk, g, 1, 200_000, 5, 50)
+    assert np.array_equal(out["theta"], th)
+    assert th.max() > 256          # some rows are not BF16-exact: the bounded path runs
+
+
+@pytest.mark.parametrize("k", [1, 10, 32])
+def test_knn_exact_all_vertices_small_workload(pk, small_case, k):
+    g, th = small_case
+    q = np.arange(g.n, dtype=np.int32)
+    out = _vectors(pk, g, 1, 200_000, 5, 50, queries=q, k=k, both=True)
+    for form in ("bf16", "fp32"):
+        ids, d2 = out[form]
+        for v in range(g.n):
+            rid, rd = oracle.knn(th, v, k)
+            assert ids[v].tolist() == rid.tolist(), (form, v)
+            assert d2[v].tolist() == rd.tolist(), (form, v)
+
+
+def test_knn_large_counts_and_ragged_queries(pk):
+    # a small dense graph with many paths: counts in the thousands, so most
+    # rows are inexact in BF16 and the error bound decides the shortlist
+    g = synth.chung_lu(700, 12, 2.4, ("uniform", 1, 20), seed=6)
+    R, T, D, k = 600_000, 5, 50, 7
+    th = _oracle_theta(g, 4, R, T, D)
+    assert th.max() > 2000
+    rng = np.random.default_rng(1)
+    q = rng.integers(0, g.n, size=333).astype(np.int32)          # ragged, with repeats
+    out = _vectors(pk, g, 4, R, T, D, queries=q, k=k, both=True)
+    assert np.array_equal(out["theta"], th)
+    for form in ("bf16", "fp32"):
+        ids, d2 = out[form]
+        for i, v in enumerate(q):
+            rid, rd = oracle.knn(th, int(v), k)
+            assert ids[i].tolist() == rid.tolist(), (form, i)
+            assert d2[i].tolist() == rd.tolist(), (form, i)
+
+
+def test_knn_mass_ties_and_padding(pk):
+    # many identical vectors (distance-0 ties broken by id) and k larger than
+    # the number of other vertices
+    g = synth.graph_from_edges(9, [(0, 1), (2, 3), (4, 5), (6, 7)], [1, 1, 1, 1])   # 8 isolated
+    R, T, D = 2000, 3, 4
+    th = _oracle_theta(g, 2, R, T, D)
+    q = np.arange(g.n, dtype=np.int32)
+    out = _vectors(pk, g, 2, R, T, D, queries=q, k=12, both=True)
+    assert np.array_equal(out["theta"], th)
+    for form in ("bf16", "fp32"):
+        ids, d2 = out[form]
+        for v in range(g.n):
+            rid, rd = oracle.knn(th, v, 12)
+            assert ids[v].tolist() == rid.tolist()
+            assert d2[v].tolist() == rd.tolist()
+
+
+def test_knn_host_io_and_errors(pk, small_case):
+    g, th = small_case
+    with pk.Panther(0) as P:
+        P.build_graph(g.row_ptr, g.col, g.w, pk.MODE_ALIAS)
+        P.sample_paths(1, 200_000, 5, pk.MODE_ALIAS)
+        P.build_index()
+        P.vectors(50)
+        q = np.array([3, 1999, 0, 77], dtype=np.int32)
+        ids = np.empty((4, 5), np.int32)
+        d2 = np.empty((4, 5), np.uint64)
+        pk.pantherpp_knn(P.h.ctx, P.h.vecs, q, 4, 5, ids, d2, pk.KNN_BF16_SCREEN | pk.IO_HOST)
+        for i, v in enumerate(q):
+            rid, rd = oracle.knn(th, int(v), 5)
+            assert ids[i].tolist() == rid.tolist() and d2[i].tolist() == rd.tolist()
+        with pytest.raises(pk.PantherError):
+            P.knn(torch.zeros(1, dtype=torch.int32, device="cuda:0"), 33)
+        P.vectors(60)
+        with pytest.raises(pk.PantherError):            # D > 56 cannot fold the norm
+            P.knn(torch.zeros(1, dtype=torch.int32, device="cuda:0"), 3)
+        ids, d2 = P.knn(torch.zeros(1, dtype=torch.int32, device="cuda:0"), 3, fp32=True)
+        P.sync()
+
+
+def test_knn_workload_shape_sampled(pk):
+    """A 200K-vertex graph shaped like the k-NN workload (mean degree 20, gamma 2.3,
+    log-uniform weights), R = 5 paths per vertex, D = 50: all-vertex theta checked on
+    a sample of rows, and the exact top-10 of sampled queries (incl. the heaviest)."""
+    g = synth.chung_lu(200_000, 20, 2.3, ("loguniform", 1, 1024), seed=1)
+    R, T, D, k = 1_000_000, 5, 50, 10
+    P = oracle.sample_paths(g, 1, R, T, oracle.ALIAS)
+    o = oracle.Oracle(g.n, P)
+    th = o.theta_all(D)
+    sizes = np.diff(o.off)
+    q = np.unique(np.concatenate([np.argsort(-sizes)[:40], np.arange(0, g.n, 4001)])).astype(np.int32)
+    out = _vectors(pk, g, 1, R, T, D, queries=q, k=k, both=False)
+    assert np.array_equal(out["theta"], th)
+    ids, d2 = out["bf16"]
+    for i, v in enumerate(q):
+        rid, rd = oracle.knn(th, int(v), k)
+        assert ids[i].tolist() == rid.tolist() and d2[i].tolist() == rd.tolist(), i

@@ -174,9 +174,13 @@ def run_ours(args, ws, rank, local):
     import paper_1504_02577_gb300 as pk
 
     torch.cuda.set_device(local)
-    p = synth.WORKLOADS[args.workload]
+    p = dict(synth.WORKLOADS[args.workload])
+    if args.n:
+        if "R" in p:
+            p["R"] = max(1, p["R"] * args.n // p["n"])
+        p["n"] = args.n
     t0 = time.time()
-    g = synth.workload_graph(args.workload)
+    g = synth.workload_graph(args.workload, n=p["n"])
     gen_s = time.time() - t0
     R, T, k = _sample_size(p), p["T"], p["k"]
     dev = f"cuda:{local}"
@@ -438,6 +442,8 @@ def main():
     ap.add_argument("--workload", default="scale", choices=["scale", "batched", "small"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and batched-vs-plain")
+    ap.add_argument("--n", type=int, default=None,
+                    help="vertices (smaller case of the same shape: R scales with n; profiling only)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

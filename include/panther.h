@@ -194,6 +194,17 @@ PANTHER_API panther_status panther_topk(panther_ctx* ctx, const panther_index* i
                             const int32_t* queries, int64_t q, int k,
                             int32_t* out_ids, uint32_t* out_counts, int flags);
 
+/* Autotuner for the batched form: runs the batch once per candidate launch
+ * shape of the persistent kernel (threads per CTA, shared-table slots, CTAs
+ * per SM), times three more runs of each with CUDA events on the context
+ * stream, and keeps the fastest shape in the context for later calls.
+ * Arguments as panther_topk (device pointers); the outputs hold the batch's
+ * result on return. chosen (may be NULL) receives {threads, slots, ctas/SM}.
+ * Synchronises. Errors: EINVAL, ENOMEM, ECUDA. */
+PANTHER_API panther_status panther_tune_topk(panther_ctx* ctx, const panther_index* ix, const panther_paths* p,
+                                             const int32_t* queries, int64_t q, int k, int32_t* out_ids,
+                                             uint32_t* out_counts, int* chosen);
+
 /* ---------------------------------------------------- Panther++ (3.3) --- */
 
 /* theta(v) = the D largest counts cnt(v,u), u != v, descending, zero padded,

@@ -49,6 +49,7 @@ SIGNATURES = {
     "panther_build_index": ([_vp, _vp, _P(_vp)], _int),
     "panther_index_view": ([_vp, _P(_vp), _P(_vp), _P(_i64), _P(_i64)], _int),
     "panther_topk": ([_vp, _vp, _vp, _vp, _i64, _int, _vp, _vp, _int], _int),
+    "panther_tune_topk": ([_vp, _vp, _vp, _vp, _i64, _int, _vp, _vp, _P(_int)], _int),
     "pantherpp_vectors": ([_vp, _vp, _vp, _int, _P(_vp)], _int),
     "pantherpp_vecs_view": ([_vp, _P(_vp), _P(_i64), _P(_int)], _int),
     "pantherpp_knn": ([_vp, _vp, _vp, _i64, _int, _vp, _vp, _int], _int),
@@ -182,6 +183,13 @@ def panther_topk(ctx: int, ix: int, p: int, queries, q: int, k: int, out_ids, ou
                  flags: int = TOPK_BATCHED) -> None:
     _check(ctx, load_library().panther_topk(ctx, ix, p, _ptr(queries), q, k, _ptr(out_ids), _ptr(out_counts),
                                             flags))
+
+
+def panther_tune_topk(ctx: int, ix: int, p: int, queries, q: int, k: int, out_ids, out_counts):
+    chosen = (_int * 3)()
+    _check(ctx, load_library().panther_tune_topk(ctx, ix, p, _ptr(queries), q, k, _ptr(out_ids), _ptr(out_counts),
+                                                 chosen))
+    return list(chosen)
 
 
 def pantherpp_vectors(ctx: int, ix: int, p: int, D: int) -> int:
@@ -375,6 +383,18 @@ class Panther:
                      TOPK_PLAIN if plain else TOPK_BATCHED)
         self._leave(ids, cnt)
         return ids, cnt
+
+    def tune_topk(self, queries, k: int):
+        """Autotune the batched top-k launch shape on this batch; returns the chosen shape."""
+        torch = self.torch
+        q = int(queries.shape[0])
+        self._enter()
+        with torch.cuda.stream(self.stream):
+            ids = torch.empty((q, k), dtype=torch.int32, device=queries.device)
+            cnt = torch.empty((q, k), dtype=torch.int32, device=queries.device)
+        shape = panther_tune_topk(self.h.ctx, self.h.index, self.h.paths, queries, q, k, ids, cnt)
+        self._leave(ids, cnt)
+        return shape
 
     def vectors(self, D: int = 50):
         if self.h.vecs:

@@ -680,10 +680,57 @@ panther_status topk_counts_all(panther_ctx* ctx, const panther_index* ix, const 
     return topk_run(ctx, ix, p, nullptr, ix->n, D, nullptr, theta, false);
 }
 
-// autotuner hook: set the persistent launch shape
-panther_status topk_set_shape(panther_ctx* ctx, int threads, int cta_slots, int blocks_per_sm) {
-    ctx->topk_threads = threads;
-    ctx->topk_cta_slots = cta_slots;
-    ctx->topk_blocks_per_sm = blocks_per_sm;
+// Autotuner: time the candidate launch shapes of the persistent kernel on the
+// caller's own batch (CUDA events on the context stream, best of 3 after one
+// warm-up run each) and keep the fastest in the context. Every shape returns
+// identical results; only the split between tiers and the occupancy change.
+extern "C" panther_status panther_tune_topk(panther_ctx* ctx, const panther_index* ix, const panther_paths* p,
+                                            const int32_t* queries, int64_t q, int k, int32_t* out_ids,
+                                            uint32_t* out_counts, int* chosen) {
+    if (!ctx || !ix || !p || !queries || !out_ids || !out_counts || q < 1 || k < 1 || k > KMAX)
+        return set_err(ctx, PANTHER_EINVAL, "bad tuner arguments");
+    cudaSetDevice(ctx->device);
+    struct Shape { int threads, slots, bps; };
+    const Shape cand[] = {{1024, 24576, 1}, {512, 24576, 1}, {512, 11264, 2}, {256, 8192, 3}, {1024, 16384, 1}};
+    cudaEvent_t a, b;
+    PCK(ctx, cudaEventCreate(&a));
+    PCK(ctx, cudaEventCreate(&b));
+    float best = 1e30f;
+    int bi = 0;
+    for (int i = 0; i < (int)(sizeof(cand) / sizeof(cand[0])); ++i) {
+        ctx->topk_threads = cand[i].threads;
+        ctx->topk_cta_slots = cand[i].slots;
+        ctx->topk_blocks_per_sm = cand[i].bps;
+        panther_status st = topk_run(ctx, ix, p, queries, q, k, out_ids, out_counts, false);
+        if (st) {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            return st;
+        }
+        float t = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+            PCK(ctx, cudaEventRecord(a, ctx->stream));
+            if ((st = topk_run(ctx, ix, p, queries, q, k, out_ids, out_counts, false))) return st;
+            PCK(ctx, cudaEventRecord(b, ctx->stream));
+            PCK(ctx, cudaEventSynchronize(b));
+            float ms = 0;
+            cudaEventElapsedTime(&ms, a, b);
+            t = ms < t ? ms : t;
+        }
+        if (t < best) {
+            best = t;
+            bi = i;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->topk_threads = cand[bi].threads;
+    ctx->topk_cta_slots = cand[bi].slots;
+    ctx->topk_blocks_per_sm = cand[bi].bps;
+    if (chosen) {
+        chosen[0] = cand[bi].threads;
+        chosen[1] = cand[bi].slots;
+        chosen[2] = cand[bi].bps;
+    }
     return PANTHER_OK;
 }

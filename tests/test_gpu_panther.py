@@ -295,3 +295,22 @@ def test_batched_workload_full_size_sampled(pk):
     rid, rcnt = o.topk_many(q[pick], 5)
     assert np.array_equal(out["ids"][pick], rid)
     assert np.array_equal(out["cnt"][pick], rcnt)
+
+
+def test_autotuner_keeps_results_exact(pk):
+    g = synth.workload_graph("batched", n=200_000)
+    R, T, k = 40_000, 5, 5
+    q = synth.query_mix(g, 2048, 2048, seed=3)
+    with pk.Panther(0) as P:
+        P.build_graph(g.row_ptr, g.col, g.w, pk.MODE_ALIAS)
+        P.sample_paths(11, R, T, pk.MODE_ALIAS)
+        P.build_index()
+        qt = torch.as_tensor(q, device="cuda:0")
+        shape = P.tune_topk(qt, k)
+        assert shape[0] in (256, 512, 1024) and shape[2] in (1, 2, 3)
+        ids, cnt = P.topk(qt, k)
+        P.sync()
+        ids, cnt = ids.cpu().numpy(), cnt.cpu().numpy().astype(np.uint32)
+    o = oracle.Oracle(g.n, oracle.sample_paths(g, 11, R, T, oracle.ALIAS))
+    rid, rcnt = o.topk_many(q, k)
+    assert np.array_equal(ids, rid) and np.array_equal(cnt, rcnt)

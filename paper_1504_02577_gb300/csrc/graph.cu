@@ -17,6 +17,8 @@
 //                j* = min{ j : D_j > E_i } and alias = L_(i+1);
 //                otherwise thr = S and alias = itself.
 //   D = inclusive prefix of deficits, E = inclusive prefix of excesses.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace {
@@ -27,6 +29,7 @@ constexpr int BLK = 512;            // threads of the CTA-per-row kernels
 // ------------------------------------------------------------ groups ---
 struct WarpG {
     static constexpr int size = 32;
+    static constexpr int IPT = 1;
     __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
     __device__ __forceinline__ void sync() const { __syncwarp(); }
     __device__ __forceinline__ uint64_t incl_scan(uint64_t v, uint64_t* total) const {
@@ -45,10 +48,18 @@ struct WarpG {
         return v;
     }
     __device__ __forceinline__ bool any(bool p) const { return __any_sync(0xffffffffu, p); }
+    // exclusive scan of the chunk (thread r holds item r); returns the chunk total
+    __device__ __forceinline__ uint64_t chunk_scan(uint64_t (&v)[IPT]) const {
+        uint64_t tot;
+        uint64_t inc = incl_scan(v[0], &tot);
+        v[0] = inc - v[0];
+        return tot;
+    }
 };
 
 struct BlockG {
     static constexpr int size = BLK;
+    static constexpr int IPT = 16;
     uint64_t* sh;   // >= BLK/32 + 1 entries
     __device__ __forceinline__ int rank() const { return threadIdx.x; }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
@@ -82,6 +93,23 @@ struct BlockG {
         return t;
     }
     __device__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
+    // exclusive scan of the chunk in blocked order (thread r holds items
+    // r*IPT .. r*IPT+IPT-1): a sequential scan per thread, one block scan of
+    // the thread totals; returns the chunk total
+    __device__ uint64_t chunk_scan(uint64_t (&v)[IPT]) const {
+        uint64_t run = 0;
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            uint64_t x = v[j];
+            v[j] = run;
+            run += x;
+        }
+        uint64_t tot;
+        uint64_t before = incl_scan(run, &tot) - run;
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) v[j] += before;
+        return tot;
+    }
 };
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -194,18 +222,27 @@ __global__ void stats_block_kernel(const int64_t* __restrict__ row_ptr, int64_t 
 template <class G, bool WIDE>
 __device__ void row_prefix(const G& g, int64_t start, int64_t deg, const int32_t* col, const uint32_t* w,
                            void* tab) {
+    constexpr int IPT = G::IPT;
     uint64_t carry = 0;
-    for (int64_t base = 0; base < deg; base += G::size) {
-        int64_t i = base + g.rank();
-        uint64_t ww = i < deg ? w[start + i] : 0;
-        uint64_t tot;
-        uint64_t inc = g.incl_scan(ww, &tot) + carry;
-        if (i < deg) {
-            if (WIDE)
-                ((uint4*)tab)[start + i] =
-                    make_uint4((uint32_t)inc, (uint32_t)(inc >> 32), (uint32_t)col[start + i], 0u);
-            else
-                ((uint2*)tab)[start + i] = make_uint2((uint32_t)inc, (uint32_t)col[start + i]);
+    for (int64_t base = 0; base < deg; base += (int64_t)G::size * IPT) {
+        uint64_t v[IPT];
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            int64_t i = base + (int64_t)g.rank() * IPT + j;
+            v[j] = i < deg ? w[start + i] : 0;
+        }
+        uint64_t tot = g.chunk_scan(v);
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            int64_t i = base + (int64_t)g.rank() * IPT + j;
+            if (i < deg) {
+                uint64_t inc = carry + v[j] + w[start + i];
+                if (WIDE)
+                    ((uint4*)tab)[start + i] =
+                        make_uint4((uint32_t)inc, (uint32_t)(inc >> 32), (uint32_t)col[start + i], 0u);
+                else
+                    ((uint2*)tab)[start + i] = make_uint2((uint32_t)inc, (uint32_t)col[start + i]);
+            }
         }
         carry += tot;
     }
@@ -264,39 +301,55 @@ __device__ void row_alias(const G& g, int64_t start, int64_t deg, uint64_t S, co
     ns = g.sum(ns);
     const int64_t nsm = (int64_t)ns, nl = deg - nsm;
     // B: columns in pop order (descending index) - smalls at [0,ns), larges at [ns,deg)
-    uint64_t cs = 0, cl = 0;
-    for (int64_t base = 0; base < deg; base += G::size) {
-        int64_t i = base + g.rank();
-        bool valid = i < deg;
-        uint64_t q = valid ? (uint64_t)w[start + i] * d : 0;
-        uint64_t sm = (valid && q < S) ? 1 : 0, lg = (valid && q >= S) ? 1 : 0;
-        uint64_t ts, tl;
-        uint64_t rs = g.incl_scan(sm, &ts) - sm + cs;
-        uint64_t rl = g.incl_scan(lg, &tl) - lg + cl;
-        if (sm) sidx[start + nsm - 1 - (int64_t)rs] = (int32_t)i;
-        if (lg) sidx[start + nsm + nl - 1 - (int64_t)rl] = (int32_t)i;
+    constexpr int IPT = G::IPT;
+    constexpr int64_t CH = (int64_t)G::size * IPT;
+    uint64_t cs = 0;
+    for (int64_t base = 0; base < deg; base += CH) {
+        uint64_t f[IPT];
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            int64_t i = base + (int64_t)g.rank() * IPT + j;
+            f[j] = (i < deg && (uint64_t)w[start + i] * d < S) ? 1 : 0;
+        }
+        uint64_t ts = g.chunk_scan(f);   // f = smalls before each item within the chunk
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            int64_t i = base + (int64_t)g.rank() * IPT + j;
+            if (i < deg) {
+                bool sm = (uint64_t)w[start + i] * d < S;
+                int64_t rs = (int64_t)(cs + f[j]);      // smalls before i
+                int64_t rl = i - rs;                     // larges before i
+                if (sm) sidx[start + nsm - 1 - rs] = (int32_t)i;
+                else sidx[start + nsm + nl - 1 - rl] = (int32_t)i;
+            }
+        }
         cs += ts;
-        cl += tl;
     }
     g.sync();
     // C: D = prefix of deficits S - q over smalls, E = prefix of excesses q - S over larges
-    uint64_t carry = 0;
-    for (int64_t base = 0; base < nsm; base += G::size) {
-        int64_t p = base + g.rank();
-        uint64_t x = p < nsm ? S - (uint64_t)w[start + sidx[start + p]] * d : 0;
-        uint64_t tot;
-        uint64_t inc = g.incl_scan(x, &tot) + carry;
-        if (p < nsm) scum[start + p] = inc;
-        carry += tot;
-    }
-    carry = 0;
-    for (int64_t base = 0; base < nl; base += G::size) {
-        int64_t p = base + g.rank();
-        uint64_t x = p < nl ? (uint64_t)w[start + sidx[start + nsm + p]] * d - S : 0;
-        uint64_t tot;
-        uint64_t inc = g.incl_scan(x, &tot) + carry;
-        if (p < nl) scum[start + nsm + p] = inc;
-        carry += tot;
+    for (int part = 0; part < 2; ++part) {
+        const int64_t cnt = part == 0 ? nsm : nl;
+        const int64_t o0 = part == 0 ? 0 : nsm;
+        uint64_t carry = 0;
+        for (int64_t base = 0; base < cnt; base += CH) {
+            uint64_t x[IPT];
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) {
+                int64_t p = base + (int64_t)g.rank() * IPT + j;
+                uint64_t q = p < cnt ? (uint64_t)w[start + sidx[start + o0 + p]] * d : 0;
+                x[j] = p < cnt ? (part == 0 ? S - q : q - S) : 0;
+            }
+            uint64_t y[IPT];
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) y[j] = x[j];
+            uint64_t tot = g.chunk_scan(y);
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) {
+                int64_t p = base + (int64_t)g.rank() * IPT + j;
+                if (p < cnt) scum[start + o0 + p] = carry + y[j] + x[j];
+            }
+            carry += tot;
+        }
     }
     g.sync();
     const uint64_t* D = scum + start;
@@ -347,6 +400,45 @@ __device__ void row_alias(const G& g, int64_t start, int64_t deg, uint64_t S, co
     }
 }
 
+// rows of degree <= SMALL_DEG: one thread per row runs the sequential LIFO
+// construction (worklists in registers/local memory), writing each entry
+// when it is final
+constexpr int SMALL_DEG = 16;
+
+__global__ void __launch_bounds__(256) alias_thread_kernel(const uint4* __restrict__ vrec, int64_t n,
+                                                           const int32_t* __restrict__ col,
+                                                           const uint32_t* __restrict__ w, uint4* tab) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        uint4 r = vrec[v];
+        const int d = (int)r.y;
+        if (d == 0 || d > SMALL_DEG) continue;
+        const int64_t start = r.x;
+        const uint64_t S = (uint64_t)r.z | ((uint64_t)r.w << 32);
+        uint64_t q[SMALL_DEG];
+        int8_t sm[SMALL_DEG], lg[SMALL_DEG];
+        int ns = 0, nl = 0;
+        for (int j = 0; j < d; ++j) {
+            q[j] = (uint64_t)w[start + j] * (uint64_t)d;
+            if (q[j] < S) sm[ns++] = (int8_t)j; else lg[nl++] = (int8_t)j;
+        }
+        while (ns > 0 && nl > 0) {
+            int a = sm[--ns], b = lg[--nl];
+            tab[start + a] = make_uint4((uint32_t)q[a], (uint32_t)(q[a] >> 32), (uint32_t)col[start + a],
+                                        (uint32_t)col[start + b]);
+            q[b] -= S - q[a];
+            if (q[b] < S) sm[ns++] = (int8_t)b; else lg[nl++] = (int8_t)b;
+        }
+        while (nl > 0) {
+            int b = lg[--nl];
+            tab[start + b] = make_uint4((uint32_t)S, (uint32_t)(S >> 32), (uint32_t)col[start + b], (uint32_t)col[start + b]);
+        }
+        while (ns > 0) {
+            int a = sm[--ns];
+            tab[start + a] = make_uint4((uint32_t)S, (uint32_t)(S >> 32), (uint32_t)col[start + a], (uint32_t)col[start + a]);
+        }
+    }
+}
+
 __global__ void alias_warp_kernel(const uint4* __restrict__ vrec, int64_t n, const int32_t* __restrict__ col,
                                   const uint32_t* __restrict__ w, uint4* tab, int32_t* sidx, uint64_t* scum) {
     WarpG g;
@@ -354,7 +446,7 @@ __global__ void alias_warp_kernel(const uint4* __restrict__ vrec, int64_t n, con
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t v = wid; v < n; v += nw) {
         uint4 r = vrec[v];
-        if ((int64_t)r.y > BIG_DEG) continue;
+        if ((int64_t)r.y > BIG_DEG || (int64_t)r.y <= SMALL_DEG) continue;
         row_alias(g, (int64_t)r.x, (int64_t)r.y, (uint64_t)r.z | ((uint64_t)r.w << 32), col, w, tab, sidx, scum);
     }
 }
@@ -492,8 +584,10 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
             dev_free(ctx, sidx);
             return fail(st);
         }
+        alias_thread_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->num_sms * 16), 256, 0, s>>>(
+            g->vrec, n, g->col, d_w, g->alias);
         alias_warp_kernel<<<gw, 256, 0, s>>>(g->vrec, n, g->col, d_w, g->alias, sidx, scum);
-        ctx->launches++;
+        ctx->launches += 2;
         if (h_nbig) {
             alias_block_kernel<<<h_nbig, BLK, 0, s>>>(g->vrec, g->col, d_w, big, g->alias, sidx, scum);
             ctx->launches++;

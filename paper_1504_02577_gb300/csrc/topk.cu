@@ -35,27 +35,35 @@ __device__ __forceinline__ uint32_t hslot(uint32_t key, uint32_t nslots) {
     return __umulhi(key * 0x9E3779B1u ^ (key >> 15), nslots);
 }
 
-// add 1 to the count of `key`; returns false if the table is full
+// add `amount` to the count of `key`; returns false if the table is full
 template <bool SHARED>
-__device__ __forceinline__ bool hash_add(unsigned long long* tab, uint32_t nslots, uint32_t key) {
+__device__ __forceinline__ bool hash_add(unsigned long long* tab, uint32_t nslots, uint32_t key,
+                                         uint32_t amount = 1) {
     uint32_t s = hslot(key, nslots);
     for (uint32_t probe = 0; probe < nslots; ++probe) {
         unsigned long long cur = tab[s];
         if ((uint32_t)(cur >> 32) == key && cur != EMPTY) {
-            atomicAdd(&tab[s], 1ull);
+            atomicAdd(&tab[s], (unsigned long long)amount);
             return true;
         }
         if (cur == EMPTY) {
-            unsigned long long prev = atomicCAS(&tab[s], EMPTY, ((unsigned long long)key << 32) | 1ull);
+            unsigned long long prev = atomicCAS(&tab[s], EMPTY, ((unsigned long long)key << 32) | amount);
             if (prev == EMPTY) return true;
             if ((uint32_t)(prev >> 32) == key) {
-                atomicAdd(&tab[s], 1ull);
+                atomicAdd(&tab[s], (unsigned long long)amount);
                 return true;
             }
         }
         s = (s + 1 == nslots) ? 0 : s + 1;
     }
     return false;
+}
+
+// table size for a query whose distinct candidates are at most cap: about
+// twice cap, a multiple of 32, within [lo, hi]
+__device__ __forceinline__ uint32_t table_size(int64_t cap, uint32_t lo, uint32_t hi) {
+    int64_t t = ((2 * cap + 31) / 32) * 32;
+    return (uint32_t)(t < lo ? lo : (t > hi ? hi : t));
 }
 
 // ------------------------------------------------------ warp top-k list ---
@@ -152,14 +160,96 @@ __device__ __forceinline__ bool insert_path(const PathsRef& P, int32_t r, int32_
     return ok;
 }
 
+// ----------------------------------------------------------- lane tier ---
+// Queries touching at most LANE_NP paths (T <= 7): one thread per query. The
+// rows sit in registers; every distinct u != v is counted at its first
+// occurrence by comparing against the later rows, and the k best scores are
+// kept in a register list sorted by insertion.
+constexpr int LANE_NP = 6;
+constexpr int LANE_K = 16;
+
+__device__ __forceinline__ bool row_has(const int32_t (&r)[8], int32_t u) {
+    bool h = false;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) h |= (r[j] == u);
+    return h;
+}
+
+__global__ void __launch_bounds__(256) lane_kernel(PathsRef P, const int32_t* __restrict__ queries,
+                                                   const int32_t* __restrict__ list, const int* __restrict__ count,
+                                                   int slot, OutRef o) {
+    const int n = count[slot];
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x) {
+        const int64_t qi = list[it];
+        const int32_t v = queries ? queries[qi] : (int32_t)qi;
+        const int64_t a = P.off[v];
+        const int np = (int)(P.off[v + 1] - a);
+        int32_t row[LANE_NP][8];
+#pragma unroll
+        for (int i = 0; i < LANE_NP; ++i) {
+            int32_t r = i < np ? P.pid[a + i] : -1;
+            if (r >= 0 && (int64_t)r < P.R) {
+                const int4* src = (const int4*)(P.rows + (int64_t)r * 8);
+                int4 x = __ldg(src), y = __ldg(src + 1);
+                row[i][0] = x.x; row[i][1] = x.y; row[i][2] = x.z; row[i][3] = x.w;
+                row[i][4] = y.x; row[i][5] = y.y; row[i][6] = y.z; row[i][7] = y.w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) row[i][j] = -1;
+            }
+            // positions past the path length never count (rows are padded with -1)
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j >= P.L) row[i][j] = -1;
+        }
+        uint64_t best[LANE_K];
+#pragma unroll
+        for (int t = 0; t < LANE_K; ++t) best[t] = 0;
+#pragma unroll
+        for (int i = 0; i < LANE_NP; ++i) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int32_t u = row[i][j];
+                bool first = u >= 0 && u != v;
+#pragma unroll
+                for (int jj = 0; jj < j; ++jj) first &= row[i][jj] != u;
+#pragma unroll
+                for (int ii = 0; ii < i; ++ii) first &= !row_has(row[ii], u);
+                if (first) {
+                    uint32_t c = 1;
+#pragma unroll
+                    for (int ii = i + 1; ii < LANE_NP; ++ii) c += row_has(row[ii], u) ? 1u : 0u;
+                    uint64_t sc = ((uint64_t)c << 32) | (uint64_t)(0xffffffffu - (uint32_t)u);
+                    // sorted insertion (descending)
+#pragma unroll
+                    for (int t = 0; t < LANE_K; ++t) {
+                        uint64_t hi = best[t] > sc ? best[t] : sc;
+                        uint64_t lo = best[t] > sc ? sc : best[t];
+                        best[t] = hi;
+                        sc = lo;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < LANE_K; ++t) {
+            if (t < o.k) {
+                uint64_t sc = best[t];
+                if (o.ids) o.ids[qi * o.k + t] = sc ? (int32_t)(0xffffffffu - (uint32_t)sc) : -1;
+                o.cnt[qi * o.k + t] = (uint32_t)(sc >> 32);
+            }
+        }
+    }
+}
+
 struct Tiers {
-    int32_t* list[3];    // query indices per tier: warp, CTA, global
-    int* count;          // [3] tier sizes, [3..4] fetch counters (warp, CTA)
+    int32_t* list[4];    // query indices per tier: warp, CTA, global, lane
+    int* count;          // [0..2] warp/CTA/global sizes, [3..4] fetch counters (warp, CTA), [5] lane size
 };
 
 // classification: pads trivially empty queries and sorts the rest into tiers
 __global__ void classify_kernel(const int32_t* __restrict__ queries, int64_t q, PathsRef P, int64_t ccap,
-                                Tiers tiers, OutRef o, uint32_t* status) {
+                                bool lane_ok, Tiers tiers, OutRef o, uint32_t* status) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned lane = threadIdx.x & 31;
     int tier = -1;
@@ -172,7 +262,7 @@ __global__ void classify_kernel(const int32_t* __restrict__ queries, int64_t q, 
             int64_t np = P.off[v + 1] - P.off[v];
             int64_t cap = np * (P.L - 1);
             if (cap > P.n - 1) cap = P.n - 1;
-            if (cap > 0) tier = cap <= WCAP ? 0 : (cap <= ccap ? 1 : 2);
+            if (cap > 0) tier = (lane_ok && np <= LANE_NP) ? 3 : (cap <= WCAP ? 0 : (cap <= ccap ? 1 : 2));
         }
         if (tier < 0) {
             for (int r = 0; r < o.k; ++r) {
@@ -182,12 +272,12 @@ __global__ void classify_kernel(const int32_t* __restrict__ queries, int64_t q, 
         }
     }
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {
+    for (int t = 0; t < 4; ++t) {
         unsigned m = __ballot_sync(0xffffffffu, tier == t);
         if (!m) continue;
         int leader = __ffs(m) - 1;
         int base = 0;
-        if ((int)lane == leader) base = atomicAdd(&tiers.count[t], __popc(m));
+        if ((int)lane == leader) base = atomicAdd(&tiers.count[t == 3 ? 5 : t], __popc(m));
         base = __shfl_sync(0xffffffffu, base, leader);
         if (tier == t) tiers.list[t][base + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
     }
@@ -195,11 +285,12 @@ __global__ void classify_kernel(const int32_t* __restrict__ queries, int64_t q, 
 
 // CTA-wide: count one query into the shared table and write its top-k
 template <int STRIDE>
-__device__ void cta_query(const PathsRef& P, int32_t v, int64_t qi, unsigned long long* tab, uint32_t nslots,
+__device__ void cta_query(const PathsRef& P, int32_t v, int64_t qi, unsigned long long* tab, uint32_t max_slots,
                           unsigned long long* lists, const OutRef& o, uint32_t* status) {
+    int64_t a = P.off[v], b = P.off[v + 1];
+    const uint32_t nslots = table_size((b - a) * (P.L - 1), 1024, max_slots);
     for (uint32_t s = threadIdx.x; s < nslots; s += blockDim.x) tab[s] = EMPTY;
     __syncthreads();
-    int64_t a = P.off[v], b = P.off[v + 1];
     bool ok = true;
     for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) ok &= insert_path<STRIDE, true>(P, P.pid[e], v, tab, nslots);
     if (!ok) flag_status(status, ST_HASH_FULL);
@@ -229,15 +320,16 @@ template <int STRIDE>
 __device__ void warp_query(const PathsRef& P, int32_t v, int64_t qi, unsigned long long* tab, const OutRef& o,
                            uint32_t* status) {
     unsigned lane = threadIdx.x & 31;
-    for (int s = lane; s < WSLOTS; s += 32) tab[s] = EMPTY;
-    __syncwarp();
     int64_t a = P.off[v], b = P.off[v + 1];
+    const uint32_t ns = table_size((b - a) * (P.L - 1), 64, WSLOTS);
+    for (uint32_t s = lane; s < ns; s += 32) tab[s] = EMPTY;
+    __syncwarp();
     bool ok = true;
-    for (int64_t e = a + lane; e < b; e += 32) ok &= insert_path<STRIDE, true>(P, P.pid[e], v, tab, WSLOTS);
+    for (int64_t e = a + lane; e < b; e += 32) ok &= insert_path<STRIDE, true>(P, P.pid[e], v, tab, ns);
     if (!ok) flag_status(status, ST_HASH_FULL);
     __syncwarp();
     WarpTopK t;
-    for (int base = 0; base < WSLOTS; base += 32) t.offer(slot_score(tab[base + lane]), o.k);
+    for (uint32_t base = 0; base < ns; base += 32) t.offer(slot_score(tab[base + lane]), o.k);
     write_list(t, o, qi);
     __syncwarp();
 }
@@ -423,6 +515,103 @@ __global__ void g_merge_kernel(GPlan G, const unsigned long long* __restrict__ p
     write_list(t, o, G.qidx[g]);
 }
 
+// ---------------------------------------------- bucketed global tier ---
+// A hub query is counted in two passes without device-wide atomics on
+// counts: (1) a CTA counts one chunk of the hub's paths in shared memory and
+// scatters its (vertex, partial count) pairs into nb buckets by a hash of the
+// vertex; (2) one CTA per bucket sums the pairs of its bucket in shared
+// memory and keeps that bucket's top-k. Partial lists merge per query. A
+// bucket that fills up marks its query, which is then counted again by the
+// global-table path.
+constexpr int B_SLOTS1 = 8192;     // pass-1 table (one chunk, T <= 7)
+constexpr int B_CAP = 12288;       // pairs per bucket
+constexpr int B_SLOTS2 = 16384;    // pass-2 table
+constexpr int B_TARGET = 4096;     // expected pairs per bucket when sizing nb
+
+struct BPlan {
+    int bpaths;                // paths per pass-1 chunk
+    const int32_t* qidx;       // [ng] query index
+    const int64_t* chunk_off;  // [ng+1] prefix of pass-1 chunks
+    const int64_t* bucket_off; // [ng+1] prefix of buckets
+    int ng;
+    unsigned long long* pairs; // [total buckets][B_CAP]
+    int* cursor;               // [total buckets]
+    int* overflow;             // [ng]
+};
+
+__device__ __forceinline__ uint32_t bucket_of(uint32_t key, uint32_t nb) {
+    uint32_t h = key * 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return __umulhi(h, nb);
+}
+
+template <int STRIDE>
+__global__ void __launch_bounds__(512) b_scatter_kernel(PathsRef P, const int32_t* __restrict__ queries, BPlan B,
+                                                        uint32_t* status) {
+    extern __shared__ unsigned long long tab[];
+    const int64_t item = blockIdx.x;
+    const int g = find_owner(B.chunk_off, B.ng, item);
+    const int64_t qi = B.qidx[g];
+    const int32_t v = queries ? queries[qi] : (int32_t)qi;
+    const int64_t a = P.off[v] + (item - B.chunk_off[g]) * B.bpaths;
+    const int64_t b = a + B.bpaths < P.off[v + 1] ? a + B.bpaths : P.off[v + 1];
+    const uint32_t nslots = B_SLOTS1;
+    for (uint32_t s = threadIdx.x; s < nslots; s += blockDim.x) tab[s] = EMPTY;
+    __syncthreads();
+    bool ok = true;
+    for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) ok &= insert_path<STRIDE, true>(P, P.pid[e], v, tab, nslots);
+    if (!ok) flag_status(status, ST_HASH_FULL);
+    __syncthreads();
+    const uint32_t nb = (uint32_t)(B.bucket_off[g + 1] - B.bucket_off[g]);
+    const int64_t b0 = B.bucket_off[g];
+    for (uint32_t s = threadIdx.x; s < nslots; s += blockDim.x) {
+        unsigned long long x = tab[s];
+        if (x == EMPTY) continue;
+        int64_t bk = b0 + bucket_of((uint32_t)(x >> 32), nb);
+        int pos = atomicAdd(&B.cursor[bk], 1);
+        if (pos < B_CAP) B.pairs[bk * B_CAP + pos] = x;
+        else B.overflow[g] = 1;
+    }
+}
+
+__global__ void __launch_bounds__(1024) b_count_kernel(BPlan B, int k, unsigned long long* __restrict__ partial,
+                                                       uint32_t* status) {
+    extern __shared__ unsigned long long tab[];
+    __shared__ unsigned long long lists[32 * KMAX];
+    const int64_t bk = blockIdx.x;
+    const int cnt = min(B.cursor[bk], B_CAP);
+    const uint32_t nslots = table_size(cnt, 1024, B_SLOTS2);
+    for (uint32_t s = threadIdx.x; s < nslots; s += blockDim.x) tab[s] = EMPTY;
+    __syncthreads();
+    bool ok = true;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        unsigned long long x = B.pairs[bk * B_CAP + i];
+        ok &= hash_add<true>(tab, nslots, (uint32_t)(x >> 32), (uint32_t)x);
+    }
+    if (!ok) flag_status(status, ST_HASH_FULL);
+    __syncthreads();
+    WarpTopK t;
+    int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
+    unsigned lane = threadIdx.x & 31;
+    for (uint32_t base = (uint32_t)w * 32; base < nslots; base += (uint32_t)nw * 32) {
+        uint32_t s = base + lane;
+        t.offer(s < nslots ? slot_score(tab[s]) : 0, k);
+    }
+    lists[w * KMAX + lane] = t.a;
+    lists[w * KMAX + 32 + lane] = t.b;
+    __syncthreads();
+    if (w == 0) {
+        for (int ww = 1; ww < nw; ++ww) {
+            t.offer(lists[ww * KMAX + lane], k);
+            if (k > 32) t.offer(lists[ww * KMAX + 32 + lane], k);
+        }
+        partial[bk * KMAX + lane] = t.a;
+        partial[bk * KMAX + 32 + lane] = t.b;
+    }
+}
+
 __global__ void g_info_kernel(const int32_t* __restrict__ list, int ng, const int32_t* __restrict__ queries,
                               const int64_t* __restrict__ off, int64_t* __restrict__ np) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -471,6 +660,171 @@ static panther_status set_smem_attr(panther_ctx* ctx, size_t bytes) {
     return PANTHER_OK;
 }
 
+struct HubQuery {
+    int32_t qi;      // query index
+    int64_t np;      // |P_v|
+};
+
+// device copy of a small host plan (kept until the stream reaches it)
+static panther_status upload(panther_ctx* ctx, const std::vector<char>& h, char** d) {
+    panther_status st = dev_alloc(ctx, (void**)d, h.size());
+    if (st) return st;
+    PCK(ctx, cudaMemcpyAsync(*d, h.data(), h.size(), cudaMemcpyHostToDevice, ctx->stream));
+    return PANTHER_OK;
+}
+
+template <class T>
+static size_t put(std::vector<char>& h, const std::vector<T>& v) {
+    size_t off = (h.size() + 15) & ~size_t(15);
+    h.resize(off + sizeof(T) * v.size());
+    memcpy(h.data() + off, v.data(), sizeof(T) * v.size());
+    return off;
+}
+
+// Bucketed counting of hub queries (largest first, rounds under the scratch
+// budget). Queries whose buckets overflowed are returned in `again`.
+static panther_status hub_buckets(panther_ctx* ctx, const PathsRef& P, const int32_t* queries, const OutRef& o, int k,
+                                  std::vector<HubQuery> hubs, std::vector<HubQuery>& again) {
+    cudaStream_t s = ctx->stream;
+    std::sort(hubs.begin(), hubs.end(),
+              [](const HubQuery& a, const HubQuery& b) { return a.np != b.np ? a.np > b.np : a.qi < b.qi; });
+    const int bpaths = std::max(32, B_SLOTS1 / (2 * std::max(1, P.L - 1)));
+    const int64_t per_bucket = (int64_t)B_CAP * 8 + 4 + KMAX * 8;
+    const int64_t budget = std::max<int64_t>(ctx->scratch_budget, per_bucket * 64);
+    int stride = 0;
+    {   // stride of the path rows from L
+        int L = P.L;
+        stride = L <= 8 ? 8 : (L <= 16 ? 16 : 32);
+    }
+    static bool attr = false;
+    if (!attr) {
+        PCK(ctx, cudaFuncSetAttribute(b_scatter_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS1 * 8));
+        PCK(ctx, cudaFuncSetAttribute(b_scatter_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS1 * 8));
+        PCK(ctx, cudaFuncSetAttribute(b_scatter_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS1 * 8));
+        PCK(ctx, cudaFuncSetAttribute(b_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS2 * 8));
+        attr = true;
+    }
+    size_t pos = 0;
+    panther_status st;
+    while (pos < hubs.size()) {
+        std::vector<int32_t> rq;
+        std::vector<int64_t> coff{0}, boff{0};
+        std::vector<HubQuery> rh;
+        int64_t used = 0;
+        while (pos < hubs.size()) {
+            const HubQuery& h = hubs[pos];
+            int64_t cap = std::min<int64_t>(h.np * (P.L - 1), P.n - 1);
+            int64_t nb = std::max<int64_t>(1, ceil_div(cap, B_TARGET));
+            if (!rq.empty() && used + nb * per_bucket > budget) break;
+            rq.push_back(h.qi);
+            rh.push_back(h);
+            coff.push_back(coff.back() + ceil_div(h.np, bpaths));
+            boff.push_back(boff.back() + nb);
+            used += nb * per_bucket;
+            ++pos;
+        }
+        const int rng = (int)rq.size();
+        const int64_t nbt = boff.back();
+        std::vector<char> hp;
+        size_t o_q = put(hp, rq), o_c = put(hp, coff), o_b = put(hp, boff);
+        char* dplan = nullptr;
+        unsigned long long *pairs = nullptr, *partial = nullptr;
+        int *cursor = nullptr, *ovf = nullptr;
+        if ((st = upload(ctx, hp, &dplan)) || (st = dev_alloc(ctx, (void**)&pairs, 8ull * B_CAP * nbt)) ||
+            (st = dev_alloc(ctx, (void**)&partial, 8ull * KMAX * nbt)) ||
+            (st = dev_alloc(ctx, (void**)&cursor, sizeof(int) * nbt)) ||
+            (st = dev_alloc(ctx, (void**)&ovf, sizeof(int) * rng))) {
+            dev_free(ctx, dplan); dev_free(ctx, pairs); dev_free(ctx, partial); dev_free(ctx, cursor);
+            return st;
+        }
+        PCK(ctx, cudaMemsetAsync(cursor, 0, sizeof(int) * nbt, s));
+        PCK(ctx, cudaMemsetAsync(ovf, 0, sizeof(int) * rng, s));
+        BPlan B{bpaths, (const int32_t*)(dplan + o_q), (const int64_t*)(dplan + o_c), (const int64_t*)(dplan + o_b),
+                rng, pairs, cursor, ovf};
+        const unsigned g1 = (unsigned)coff.back();
+        if (stride == 8) b_scatter_kernel<8><<<g1, 512, B_SLOTS1 * 8, s>>>(P, queries, B, ctx->d_status);
+        else if (stride == 16) b_scatter_kernel<16><<<g1, 512, B_SLOTS1 * 8, s>>>(P, queries, B, ctx->d_status);
+        else b_scatter_kernel<32><<<g1, 512, B_SLOTS1 * 8, s>>>(P, queries, B, ctx->d_status);
+        b_count_kernel<<<(unsigned)nbt, 1024, B_SLOTS2 * 8, s>>>(B, k, partial, ctx->d_status);
+        GPlan G{B.qidx, nullptr, nullptr, nullptr, B.bucket_off, rng};
+        g_merge_kernel<<<rng, 32, 0, s>>>(G, partial, o);
+        ctx->launches += 3;
+        PCK(ctx, cudaGetLastError());
+        std::vector<int> hov(rng);
+        PCK(ctx, cudaMemcpyAsync(hov.data(), ovf, sizeof(int) * rng, cudaMemcpyDeviceToHost, s));
+        PCK(ctx, cudaStreamSynchronize(s));
+        for (int i = 0; i < rng; ++i)
+            if (hov[i]) again.push_back(rh[i]);
+        dev_free(ctx, dplan); dev_free(ctx, pairs); dev_free(ctx, partial); dev_free(ctx, cursor); dev_free(ctx, ovf);
+    }
+    return PANTHER_OK;
+}
+
+// Hub queries counted in per-query device tables (the fallback of the
+// bucketed path): rounds under the scratch budget.
+static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int32_t* queries, const OutRef& o, int k,
+                                 const std::vector<HubQuery>& hubs) {
+    cudaStream_t s = ctx->stream;
+    const int64_t budget_slots = std::max<int64_t>(ctx->scratch_budget / 8 / 2, 1 << 20);
+    const int stride = P.L <= 8 ? 8 : (P.L <= 16 ? 16 : 32);
+    size_t pos = 0;
+    unsigned long long* arena = nullptr;
+    int64_t arena_slots = 0;
+    panther_status st;
+    while (pos < hubs.size()) {
+        std::vector<int32_t> rq;
+        std::vector<int64_t> roff, ioff{0}, soff{0};
+        std::vector<uint32_t> rn;
+        int64_t used = 0;
+        while (pos < hubs.size()) {
+            const HubQuery& h = hubs[pos];
+            int64_t cap = std::min<int64_t>(h.np * (P.L - 1), P.n - 1);
+            uint32_t slots = pow2_at_least(cap * 2);
+            if (!rq.empty() && used + slots > budget_slots) break;
+            rq.push_back(h.qi);
+            roff.push_back(used);
+            rn.push_back(slots);
+            used += slots;
+            ioff.push_back(ioff.back() + ceil_div(h.np, G_PATHS));
+            soff.push_back(soff.back() + ceil_div(slots, G_SLOTS));
+            ++pos;
+        }
+        if (used > arena_slots) {
+            dev_free(ctx, arena);
+            arena = nullptr;
+            if ((st = dev_alloc(ctx, (void**)&arena, 8ull * used))) return st;
+            arena_slots = used;
+            fill_empty_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(arena, used);
+            ctx->launches++;
+        }
+        const int rng = (int)rq.size();
+        std::vector<char> hp;
+        size_t o_q = put(hp, rq), o_o = put(hp, roff), o_n = put(hp, rn), o_i = put(hp, ioff), o_s = put(hp, soff);
+        char* dplan = nullptr;
+        unsigned long long* partial = nullptr;
+        if ((st = upload(ctx, hp, &dplan)) ||
+            (st = dev_alloc(ctx, (void**)&partial, sizeof(unsigned long long) * KMAX * soff.back()))) {
+            dev_free(ctx, dplan);
+            dev_free(ctx, arena);
+            return st;
+        }
+        GPlan G{(const int32_t*)(dplan + o_q), (const int64_t*)(dplan + o_o), (const uint32_t*)(dplan + o_n),
+                (const int64_t*)(dplan + o_i), (const int64_t*)(dplan + o_s), rng};
+        if (stride == 8) g_count_kernel<8><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
+        else if (stride == 16) g_count_kernel<16><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
+        else g_count_kernel<32><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
+        g_select_kernel<<<(unsigned)soff.back(), 512, 0, s>>>(G, arena, k, partial);
+        g_merge_kernel<<<rng, 32, 0, s>>>(G, partial, o);
+        ctx->launches += 3;
+        PCK(ctx, cudaGetLastError());
+        PCK(ctx, cudaStreamSynchronize(s));   // the host plan must outlive the copy
+        dev_free(ctx, dplan);
+        dev_free(ctx, partial);
+    }
+    dev_free(ctx, arena);
+    return PANTHER_OK;
+}
+
 // Internal entry shared by panther_topk and pantherpp_vectors: queries may be
 // NULL (meaning 0..q-1); ids may be NULL (counts only, e.g. theta rows).
 panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther_paths* p, const int32_t* queries,
@@ -509,15 +863,20 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
 
     int32_t* lists = nullptr;
     int* counts = nullptr;
-    if ((st = dev_alloc(ctx, (void**)&lists, sizeof(int32_t) * 3 * (size_t)q)) ||
+    if ((st = dev_alloc(ctx, (void**)&lists, sizeof(int32_t) * 4 * (size_t)q)) ||
         (st = dev_alloc(ctx, (void**)&counts, sizeof(int) * 8))) {
         dev_free(ctx, lists);
         return st;
     }
-    Tiers tiers{{lists, lists + q, lists + 2 * q}, counts};
+    Tiers tiers{{lists, lists + q, lists + 2 * q, lists + 3 * q}, counts};
+    const bool lane_ok = p->stride == 8 && k <= LANE_K;
     PCK(ctx, cudaMemsetAsync(counts, 0, sizeof(int) * 8, s));
-    classify_kernel<<<(unsigned)ceil_div(q, 256), 256, 0, s>>>(queries, q, P, ccap, tiers, o, ctx->d_status);
+    classify_kernel<<<(unsigned)ceil_div(q, 256), 256, 0, s>>>(queries, q, P, ccap, lane_ok, tiers, o, ctx->d_status);
     ctx->launches++;
+    if (lane_ok) {
+        lane_kernel<<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(P, queries, lists + 3 * q, counts, 5, o);
+        ctx->launches++;
+    }
     PersistArgs A{P, queries, tiers, o, sh.cta_slots, ctx->d_status};
     unsigned blocks = (unsigned)(ctx->num_sms * sh.blocks_per_sm);
     if (p->stride == 8) persistent_kernel<8><<<blocks, sh.threads, smem, s>>>(A);
@@ -546,90 +905,16 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
         PCK(ctx, cudaMemcpyAsync(npv.data(), d_np, sizeof(int64_t) * ng, cudaMemcpyDeviceToHost, s));
         PCK(ctx, cudaStreamSynchronize(s));
         dev_free(ctx, d_np);
-        // largest first, then pack rounds under the scratch budget
-        std::vector<int> order(ng);
-        for (int i = 0; i < ng; ++i) order[i] = i;
-        std::sort(order.begin(), order.end(), [&](int x, int y) {
-            return npv[x] != npv[y] ? npv[x] > npv[y] : x < y;
-        });
-        const int64_t budget_slots = std::max<int64_t>(ctx->scratch_budget / 8 / 2, 1 << 20);
-        size_t pos = 0;
-        unsigned long long* arena = nullptr;
-        int64_t arena_slots = 0;
-        while (pos < order.size()) {
-            std::vector<int32_t> rq;
-            std::vector<int64_t> roff, ioff{0}, soff{0};
-            std::vector<uint32_t> rn;
-            int64_t used = 0;
-            while (pos < order.size()) {
-                int i = order[pos];
-                int64_t np = npv[i];
-                int64_t cap = std::min<int64_t>(np * (p->L - 1), ix->n - 1);
-                uint32_t slots = pow2_at_least(cap * 2);
-                if (!rq.empty() && used + slots > budget_slots) break;
-                rq.push_back(gq[i]);
-                roff.push_back(used);
-                rn.push_back(slots);
-                used += slots;
-                ioff.push_back(ioff.back() + ceil_div(np, G_PATHS));
-                soff.push_back(soff.back() + ceil_div(slots, G_SLOTS));
-                ++pos;
-            }
-            if (used > arena_slots) {
-                dev_free(ctx, arena);
-                arena = nullptr;
-                if ((st = dev_alloc(ctx, (void**)&arena, 8ull * used))) {
-                    dev_free(ctx, lists);
-                    dev_free(ctx, counts);
-                    return st;
-                }
-                arena_slots = used;
-                fill_empty_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(arena, used);
-                ctx->launches++;
-            }
-            int rng = (int)rq.size();
-            // plan arrays in one device buffer
-            size_t bytes = sizeof(int32_t) * rng + sizeof(int64_t) * rng + sizeof(uint32_t) * rng +
-                           sizeof(int64_t) * (rng + 1) * 2 + 64;
-            std::vector<char> hbuf(bytes);
-            char* hp = hbuf.data();
-            size_t o0 = 0, o1 = o0 + sizeof(int32_t) * rng;
-            o1 = (o1 + 7) & ~size_t(7);
-            size_t o2 = o1 + sizeof(int64_t) * rng;
-            size_t o3 = o2 + sizeof(uint32_t) * rng;
-            o3 = (o3 + 7) & ~size_t(7);
-            size_t o4 = o3 + sizeof(int64_t) * (rng + 1);
-            memcpy(hp + o0, rq.data(), sizeof(int32_t) * rng);
-            memcpy(hp + o1, roff.data(), sizeof(int64_t) * rng);
-            memcpy(hp + o2, rn.data(), sizeof(uint32_t) * rng);
-            memcpy(hp + o3, ioff.data(), sizeof(int64_t) * (rng + 1));
-            memcpy(hp + o4, soff.data(), sizeof(int64_t) * (rng + 1));
-            char* dplan = nullptr;
-            unsigned long long* partial = nullptr;
-            if ((st = dev_alloc(ctx, (void**)&dplan, bytes)) ||
-                (st = dev_alloc(ctx, (void**)&partial, sizeof(unsigned long long) * KMAX * soff.back()))) {
-                dev_free(ctx, dplan);
-                dev_free(ctx, arena);
-                dev_free(ctx, lists);
-                dev_free(ctx, counts);
-                return st;
-            }
-            PCK(ctx, cudaMemcpyAsync(dplan, hp, bytes, cudaMemcpyHostToDevice, s));
-            GPlan G{(const int32_t*)(dplan + o0), (const int64_t*)(dplan + o1), (const uint32_t*)(dplan + o2),
-                    (const int64_t*)(dplan + o3), (const int64_t*)(dplan + o4), rng};
-            if (p->stride == 8) g_count_kernel<8><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
-            else if (p->stride == 16) g_count_kernel<16><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
-            else g_count_kernel<32><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
-            g_select_kernel<<<(unsigned)soff.back(), 512, 0, s>>>(G, arena, k, partial);
-            g_merge_kernel<<<rng, 32, 0, s>>>(G, partial, o);
-            ctx->launches += 3;
-            PCK(ctx, cudaGetLastError());
-            // the host plan buffer must outlive the async copy
-            PCK(ctx, cudaStreamSynchronize(s));
-            dev_free(ctx, dplan);
-            dev_free(ctx, partial);
+        std::vector<HubQuery> hubs(ng);
+        for (int i = 0; i < ng; ++i) hubs[i] = HubQuery{gq[i], npv[i]};
+        std::vector<HubQuery> again;
+        st = hub_buckets(ctx, P, queries, o, k, hubs, again);
+        if (!st && !again.empty()) st = hub_tables(ctx, P, queries, o, k, again);
+        if (st) {
+            dev_free(ctx, lists);
+            dev_free(ctx, counts);
+            return st;
         }
-        dev_free(ctx, arena);
     }
     dev_free(ctx, lists);
     dev_free(ctx, counts);

@@ -291,9 +291,9 @@ __device__ __forceinline__ int64_t upper_bound_u64(const uint64_t* a, int64_t cn
 }
 
 template <class G>
-__device__ void row_alias(const G& g, int64_t start, int64_t deg, uint64_t S, const int32_t* col,
-                          const uint32_t* w, uint4* tab, int32_t* sidx, uint64_t* scum) {
-    if (deg == 0) return;
+__device__ int64_t row_alias_prep(const G& g, int64_t start, int64_t deg, uint64_t S, const uint32_t* w,
+                                  int32_t* sidx, uint64_t* scum) {
+    if (deg == 0) return 0;
     const uint64_t d = (uint64_t)deg;
     // A: number of small columns (q < S)
     uint64_t ns = 0;
@@ -352,6 +352,17 @@ __device__ void row_alias(const G& g, int64_t start, int64_t deg, uint64_t S, co
         }
     }
     g.sync();
+    return nsm;
+}
+
+// Pass D of the alias construction: thread `tid` of `nthreads` takes a
+// contiguous run of the smalls and of the larges (in pop order) and walks the
+// other sorted sequence forward from one binary search.
+__device__ void alias_assign(int64_t start, int64_t deg, uint64_t S, int64_t nsm, const int32_t* col,
+                             const uint32_t* w, uint4* tab, const int32_t* sidx, const uint64_t* scum, int64_t tid,
+                             int64_t nthreads) {
+    const uint64_t d = (uint64_t)deg;
+    const int64_t nl = deg - nsm;
     const uint64_t* D = scum + start;
     const uint64_t* E = scum + start + nsm;
     const int32_t* SI = sidx + start;
@@ -360,8 +371,8 @@ __device__ void row_alias(const G& g, int64_t start, int64_t deg, uint64_t S, co
     // D: table entries. Each lane takes a contiguous run and walks the other
     // sequence forward from one binary search (both sequences are sorted).
     {
-        int64_t per = (nsm + G::size - 1) / G::size;
-        int64_t p0 = (int64_t)g.rank() * per, p1 = p0 + per < nsm ? p0 + per : nsm;
+        int64_t per = (nsm + nthreads - 1) / nthreads;
+        int64_t p0 = tid * per, p1 = p0 + per < nsm ? p0 + per : nsm;
         if (p0 < p1) {
             int64_t i = nl ? lower_bound_u64(E, nl, p0 ? D[p0 - 1] : 0) : 0;
             for (int64_t p = p0; p < p1; ++p) {
@@ -379,8 +390,8 @@ __device__ void row_alias(const G& g, int64_t start, int64_t deg, uint64_t S, co
         }
     }
     {
-        int64_t per = (nl + G::size - 1) / G::size;
-        int64_t i0 = (int64_t)g.rank() * per, i1 = i0 + per < nl ? i0 + per : nl;
+        int64_t per = (nl + nthreads - 1) / nthreads;
+        int64_t i0 = tid * per, i1 = i0 + per < nl ? i0 + per : nl;
         if (i0 < i1) {
             int64_t js = upper_bound_u64(D, nsm, E[i0]);
             for (int64_t i = i0; i < i1; ++i) {
@@ -398,6 +409,15 @@ __device__ void row_alias(const G& g, int64_t start, int64_t deg, uint64_t S, co
             }
         }
     }
+}
+
+
+template <class G>
+__device__ void row_alias(const G& g, int64_t start, int64_t deg, uint64_t S, const int32_t* col,
+                          const uint32_t* w, uint4* tab, int32_t* sidx, uint64_t* scum) {
+    if (deg == 0) return;
+    int64_t nsm = row_alias_prep(g, start, deg, S, w, sidx, scum);
+    alias_assign(start, deg, S, nsm, col, w, tab, sidx, scum, g.rank(), G::size);
 }
 
 // rows of degree <= SMALL_DEG: one thread per row runs the sequential LIFO
@@ -453,11 +473,24 @@ __global__ void alias_warp_kernel(const uint4* __restrict__ vrec, int64_t n, con
 
 __global__ void alias_block_kernel(const uint4* __restrict__ vrec, const int32_t* __restrict__ col,
                                    const uint32_t* __restrict__ w, const int32_t* __restrict__ big, uint4* tab,
-                                   int32_t* sidx, uint64_t* scum) {
+                                   int32_t* sidx, uint64_t* scum, int64_t* bign) {
     __shared__ uint64_t sh[BLK / 32 + 1];
     BlockG g{sh};
     uint4 r = vrec[big[blockIdx.x]];
-    row_alias(g, (int64_t)r.x, (int64_t)r.y, (uint64_t)r.z | ((uint64_t)r.w << 32), col, w, tab, sidx, scum);
+    int64_t nsm = row_alias_prep(g, (int64_t)r.x, (int64_t)r.y, (uint64_t)r.z | ((uint64_t)r.w << 32), w, sidx, scum);
+    if (threadIdx.x == 0) bign[blockIdx.x] = nsm;
+}
+
+// pass D for the rows above BIG_DEG: ASSIGN_SPLIT CTAs per row
+constexpr int ASSIGN_SPLIT = 32;
+__global__ void alias_assign_kernel(const uint4* __restrict__ vrec, const int32_t* __restrict__ col,
+                                    const uint32_t* __restrict__ w, const int32_t* __restrict__ big,
+                                    const int64_t* __restrict__ bign, uint4* tab, const int32_t* __restrict__ sidx,
+                                    const uint64_t* __restrict__ scum) {
+    const int64_t row = blockIdx.x / ASSIGN_SPLIT, part = blockIdx.x % ASSIGN_SPLIT;
+    uint4 r = vrec[big[row]];
+    alias_assign((int64_t)r.x, (int64_t)r.y, (uint64_t)r.z | ((uint64_t)r.w << 32), bign[row], col, w, tab, sidx,
+                 scum, part * blockDim.x + threadIdx.x, (int64_t)ASSIGN_SPLIT * blockDim.x);
 }
 
 unsigned grid_for(panther_ctx* ctx, int64_t items_per_block_unit, int64_t n, int threads) {
@@ -589,8 +622,17 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
         alias_warp_kernel<<<gw, 256, 0, s>>>(g->vrec, n, g->col, d_w, g->alias, sidx, scum);
         ctx->launches += 2;
         if (h_nbig) {
-            alias_block_kernel<<<h_nbig, BLK, 0, s>>>(g->vrec, g->col, d_w, big, g->alias, sidx, scum);
-            ctx->launches++;
+            int64_t* bign = nullptr;
+            if ((st = dev_alloc(ctx, (void**)&bign, sizeof(int64_t) * h_nbig))) {
+                dev_free(ctx, sidx);
+                dev_free(ctx, scum);
+                return fail(st);
+            }
+            alias_block_kernel<<<h_nbig, BLK, 0, s>>>(g->vrec, g->col, d_w, big, g->alias, sidx, scum, bign);
+            alias_assign_kernel<<<(unsigned)(h_nbig * ASSIGN_SPLIT), 256, 0, s>>>(g->vrec, g->col, d_w, big, bign,
+                                                                               g->alias, sidx, scum);
+            ctx->launches += 2;
+            dev_free(ctx, bign);
         }
         e = cudaGetLastError();
         dev_free(ctx, sidx);

@@ -80,16 +80,29 @@ __global__ void __launch_bounds__(IX_T) scatter_kernel(Src s, int shift, int rad
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     for (int d = threadIdx.x; d < IX_WARPS * MAX_RADIX; d += IX_T) (&wc[0][0])[d] = 0;
-    __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * IX_TILE + (int64_t)w * (IX_ROUNDS * 32);
-    // phase 1: per-warp digit counts
+    // the warp's items stay in registers; lrank = rank among the warp's items of the same digit
+    uint32_t key[IX_ROUNDS];
+    uint32_t lrank[IX_ROUNDS / 2];
+    uint32_t okmask = 0;
+#pragma unroll
     for (int k = 0; k < IX_ROUNDS; ++k) {
-        uint32_t key;
         int32_t val;
-        bool ok = load_item(s, base + k * 32 + lane, key, val);
-        uint32_t d = ok ? ((key >> shift) & (radix - 1)) : 0xffffffffu;
+        bool ok = load_item(s, base + k * 32 + lane, key[k], val);
+        okmask |= (ok ? 1u : 0u) << k;
+    }
+    __syncthreads();
+    // phase 1: per-warp digit counts and each item's rank within the warp
+#pragma unroll
+    for (int k = 0; k < IX_ROUNDS; ++k) {
+        bool ok = (okmask >> k) & 1u;
+        uint32_t d = ok ? ((key[k] >> shift) & (radix - 1)) : 0xffffffffu;
         unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (ok && (peers & lt) == 0) wc[w][d] += __popc(peers);
+        unsigned before = ok ? wc[w][d] : 0u;
+        uint32_t r = before + __popc(peers & lt);
+        if (k & 1) lrank[k >> 1] |= r << 16; else lrank[k >> 1] = r;
+        __syncwarp();
+        if (ok && (peers & lt) == 0) wc[w][d] = before + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
@@ -105,20 +118,16 @@ __global__ void __launch_bounds__(IX_T) scatter_kernel(Src s, int shift, int rad
     }
     __syncthreads();
     // phase 3: stable scatter in item order
+#pragma unroll
     for (int k = 0; k < IX_ROUNDS; ++k) {
-        uint32_t key;
-        int32_t val;
-        bool ok = load_item(s, base + k * 32 + lane, key, val);
-        uint32_t d = ok ? ((key >> shift) & (radix - 1)) : 0xffffffffu;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (ok) {
-            int64_t pos = (int64_t)toff[d] + wc[w][d] + __popc(peers & lt);
-            okeys[pos] = (int32_t)key;
-            ovals[pos] = val;
+        if ((okmask >> k) & 1u) {
+            uint32_t d = (key[k] >> shift) & (radix - 1);
+            uint32_t r = (k & 1) ? (lrank[k >> 1] >> 16) : (lrank[k >> 1] & 0xffffu);
+            int64_t pos = (int64_t)toff[d] + wc[w][d] + r;
+            int64_t i = base + k * 32 + lane;
+            okeys[pos] = (int32_t)key[k];
+            ovals[pos] = s.first ? (int32_t)(i / s.stride) : s.vals[i];   // value re-read (L2-resident tile)
         }
-        __syncwarp();
-        if (ok && (peers & lt) == 0) wc[w][d] += __popc(peers);
-        __syncwarp();
     }
 }
 

@@ -67,6 +67,9 @@ __device__ __forceinline__ uint32_t table_size(int64_t cap, uint32_t lo, uint32_
 }
 
 // ------------------------------------------------------ warp top-k list ---
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
 struct WarpTopK {
     uint64_t a = 0, b = 0;   // ranks lane and 32+lane, descending; 0 = empty
     __device__ __forceinline__ uint64_t kth(int k) const {
@@ -85,10 +88,44 @@ struct WarpTopK {
         a = na;
         b = nb;
     }
+    // merge another descending 64-list (xa, xb) in: the top 64 of the union,
+    // by one bitonic half-cleaner cascade (keys are distinct or 0)
+    __device__ __forceinline__ void merge(uint64_t xa, uint64_t xb) {
+        unsigned lane = threadIdx.x & 31;
+        uint64_t ra = __shfl_sync(0xffffffffu, xb, 31 - lane);
+        uint64_t rb = __shfl_sync(0xffffffffu, xa, 31 - lane);
+        uint64_t za = umax64(a, ra), zb = umax64(b, rb);
+        a = umax64(za, zb);
+        b = umin64(za, zb);
+#pragma unroll
+        for (int d = 16; d; d >>= 1) {
+            uint64_t pa = __shfl_xor_sync(0xffffffffu, a, d);
+            uint64_t pb = __shfl_xor_sync(0xffffffffu, b, d);
+            bool upper = lane & d;
+            a = upper ? umin64(a, pa) : umax64(a, pa);
+            b = upper ? umin64(b, pb) : umax64(b, pb);
+        }
+    }
     // offer one candidate per lane (0 = none)
     __device__ __forceinline__ void offer(uint64_t c, int k) {
         uint64_t thr = kth(k);
         unsigned m = __ballot_sync(0xffffffffu, c > thr);
+        if (__popc(m) > 2) {
+            // many pass: sort the 32 candidates (descending bitonic sort) and merge
+            unsigned lane = threadIdx.x & 31;
+#pragma unroll
+            for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+                for (int j = kk >> 1; j > 0; j >>= 1) {
+                    uint64_t pc = __shfl_xor_sync(0xffffffffu, c, j);
+                    bool desc = (lane & kk) == 0 || kk == 32;
+                    bool lower = (lane & j) == 0;
+                    c = (lower == desc) ? umax64(c, pc) : umin64(c, pc);
+                }
+            }
+            merge(c, 0);
+            return;
+        }
         while (m) {
             int src = __ffs(m) - 1;
             uint64_t x = __shfl_sync(0xffffffffu, c, src);
@@ -99,6 +136,22 @@ struct WarpTopK {
         }
     }
 };
+
+// merge the lists of all warps of the CTA into warp 0 (log-depth tree);
+// `lists` holds 64 entries per warp; every thread of the CTA must call it
+__device__ __forceinline__ void cta_merge(WarpTopK& t, unsigned long long* lists) {
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
+    const unsigned lane = threadIdx.x & 31;
+    for (int s = 1; s < nw; s <<= 1) {
+        if ((w & (2 * s - 1)) == s) {
+            lists[w * KMAX + lane] = t.a;
+            lists[w * KMAX + 32 + lane] = t.b;
+        }
+        __syncthreads();
+        if ((w & (2 * s - 1)) == 0 && w + s < nw) t.merge(lists[(w + s) * KMAX + lane], lists[(w + s) * KMAX + 32 + lane]);
+        __syncthreads();
+    }
+}
 
 __device__ __forceinline__ uint64_t slot_score(unsigned long long s) {
     if (s == EMPTY) return 0;
@@ -303,14 +356,8 @@ __device__ void cta_query(const PathsRef& P, int32_t v, int64_t qi, unsigned lon
         t.offer(s < nslots ? slot_score(tab[s]) : 0, o.k);
     }
     // merge warp lists through shared memory (reuses the list area)
-    lists[w * KMAX + lane] = t.a;
-    lists[w * KMAX + 32 + lane] = t.b;
-    __syncthreads();
+    cta_merge(t, lists);
     if (w == 0) {
-        for (int ww = 1; ww < nw; ++ww) {
-            t.offer(lists[ww * KMAX + lane], o.k);
-            if (o.k > 32) t.offer(lists[ww * KMAX + 32 + lane], o.k);
-        }
         write_list(t, o, qi);
     }
     __syncthreads();
@@ -346,7 +393,7 @@ struct PersistArgs {
 template <int STRIDE>
 __global__ void __launch_bounds__(1024, 1) persistent_kernel(PersistArgs A) {
     extern __shared__ unsigned long long smem[];
-    __shared__ unsigned long long lists[32 * KMAX];
+    unsigned long long* lists = smem + A.cta_slots;     // 64 entries per warp after the table
     __shared__ int s_item;
     const int nC = A.tiers.count[1], nW = A.tiers.count[0];
     // CTA tier first: the largest items, one query per fetch
@@ -383,7 +430,7 @@ template <int STRIDE>
 __global__ void __launch_bounds__(1024, 1) single_kernel(PathsRef P, const int32_t* __restrict__ queries, int64_t qi, OutRef o,
                               uint32_t cta_slots, unsigned long long* gtab, uint32_t gslots, uint32_t* status) {
     extern __shared__ unsigned long long smem[];
-    __shared__ unsigned long long lists[32 * KMAX];
+    unsigned long long* lists = smem + cta_slots;       // 64 entries per warp after the table
     int64_t v = queries ? queries[qi] : qi;
     if (v < 0 || v >= P.n) {
         if (threadIdx.x == 0) flag_status(status, ST_BAD_QUERY);
@@ -418,14 +465,8 @@ __global__ void __launch_bounds__(1024, 1) single_kernel(PathsRef P, const int32
         }
         t.offer(sc, o.k);
     }
-    lists[w * KMAX + lane] = t.a;
-    lists[w * KMAX + 32 + lane] = t.b;
-    __syncthreads();
+    cta_merge(t, lists);
     if (w == 0) {
-        for (int ww = 1; ww < nw; ++ww) {
-            t.offer(lists[ww * KMAX + lane], o.k);
-            if (o.k > 32) t.offer(lists[ww * KMAX + 32 + lane], o.k);
-        }
         write_list(t, o, qi);
     }
 }
@@ -490,14 +531,8 @@ __global__ void g_select_kernel(GPlan G, unsigned long long* arena, int k, unsig
         }
         t.offer(sc, k);
     }
-    lists[w * KMAX + lane] = t.a;
-    lists[w * KMAX + 32 + lane] = t.b;
-    __syncthreads();
+    cta_merge(t, lists);
     if (w == 0) {
-        for (int ww = 1; ww < nw; ++ww) {
-            t.offer(lists[ww * KMAX + lane], k);
-            if (k > 32) t.offer(lists[ww * KMAX + 32 + lane], k);
-        }
         partial[item * KMAX + lane] = t.a;
         partial[item * KMAX + 32 + lane] = t.b;
     }
@@ -566,13 +601,23 @@ __global__ void __launch_bounds__(512) b_scatter_kernel(PathsRef P, const int32_
     __syncthreads();
     const uint32_t nb = (uint32_t)(B.bucket_off[g + 1] - B.bucket_off[g]);
     const int64_t b0 = B.bucket_off[g];
-    for (uint32_t s = threadIdx.x; s < nslots; s += blockDim.x) {
-        unsigned long long x = tab[s];
-        if (x == EMPTY) continue;
-        int64_t bk = b0 + bucket_of((uint32_t)(x >> 32), nb);
-        int pos = atomicAdd(&B.cursor[bk], 1);
-        if (pos < B_CAP) B.pairs[bk * B_CAP + pos] = x;
-        else B.overflow[g] = 1;
+    const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    for (uint32_t base = 0; base < nslots; base += blockDim.x) {      // warp-uniform trip count
+        const uint32_t s = base + threadIdx.x;
+        const unsigned long long x = s < nslots ? tab[s] : EMPTY;
+        const bool valid = x != EMPTY;
+        const uint32_t bkt = valid ? bucket_of((uint32_t)(x >> 32), nb) : 0xffffffffu;
+        // one cursor atomic per (warp, bucket)
+        const unsigned peers = __match_any_sync(0xffffffffu, bkt);
+        const int leader = __ffs(peers) - 1;
+        int first = 0;
+        if (valid && (int)lane == leader) first = atomicAdd(&B.cursor[b0 + bkt], __popc(peers));
+        first = __shfl_sync(0xffffffffu, first, leader);
+        if (valid) {
+            int pos = first + __popc(peers & lt);
+            if (pos < B_CAP) B.pairs[(b0 + bkt) * B_CAP + pos] = x;
+            else B.overflow[g] = 1;
+        }
     }
 }
 
@@ -599,14 +644,8 @@ __global__ void __launch_bounds__(1024) b_count_kernel(BPlan B, int k, unsigned 
         uint32_t s = base + lane;
         t.offer(s < nslots ? slot_score(tab[s]) : 0, k);
     }
-    lists[w * KMAX + lane] = t.a;
-    lists[w * KMAX + 32 + lane] = t.b;
-    __syncthreads();
+    cta_merge(t, lists);
     if (w == 0) {
-        for (int ww = 1; ww < nw; ++ww) {
-            t.offer(lists[ww * KMAX + lane], k);
-            if (k > 32) t.offer(lists[ww * KMAX + 32 + lane], k);
-        }
         partial[bk * KMAX + lane] = t.a;
         partial[bk * KMAX + 32 + lane] = t.b;
     }
@@ -831,7 +870,7 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
                         int64_t q, int k, int32_t* ids, uint32_t* cnt, bool plain) {
     cudaStream_t s = ctx->stream;
     TopkShape sh = topk_shape(ctx);
-    const size_t smem = (size_t)sh.cta_slots * 8;
+    const size_t smem = (size_t)sh.cta_slots * 8 + (size_t)(sh.threads / 32) * KMAX * 8;
     panther_status st;
     if (p->stride == 8) st = set_smem_attr<8>(ctx, smem);
     else if (p->stride == 16) st = set_smem_attr<16>(ctx, smem);
@@ -976,7 +1015,7 @@ extern "C" panther_status panther_tune_topk(panther_ctx* ctx, const panther_inde
         return set_err(ctx, PANTHER_EINVAL, "bad tuner arguments");
     cudaSetDevice(ctx->device);
     struct Shape { int threads, slots, bps; };
-    const Shape cand[] = {{1024, 24576, 1}, {512, 24576, 1}, {512, 11264, 2}, {256, 8192, 3}, {1024, 16384, 1}};
+    const Shape cand[] = {{1024, 24576, 1}, {512, 12288, 2}, {256, 6144, 4}, {256, 4096, 6}, {512, 24576, 1}};
     cudaEvent_t a, b;
     PCK(ctx, cudaEventCreate(&a));
     PCK(ctx, cudaEventCreate(&b));

@@ -174,6 +174,24 @@ PANTHER_API panther_status panther_paths_view(const panther_paths* p, const int3
  * output. Errors: EINVAL, ENOMEM, ECUDA. */
 PANTHER_API panther_status panther_build_index(panther_ctx* ctx, const panther_paths* p, panther_index** out);
 
+/* Index build that allocates nothing (the paper has no counterpart; this is
+ * for callers that cannot call cudaMalloc, such as a host application that
+ * owns a fixed share of the GPU and accounts for every byte itself, or a
+ * latency-bound loop where an allocation could synchronise the device).
+ * Same result as panther_build_index: P_v = pid[off[v] .. off[v+1]),
+ * ascending. The caller passes dev_off (int64[n+1]) and dev_pid (int32,
+ * pid_capacity >= R*(T+1) entries); *nnz receives the number of pairs.
+ * Temporary buffers come from one static device array of about 72 MiB that
+ * every GPU loading the library reserves until the process exits; R*(T+1)
+ * may be at most 4,194,304 (EOVERFLOW beyond, before any launch). The first
+ * call on a device looks up that array's device address, so make it before
+ * any stream capture. Calls share the array: two calls that overlap on the
+ * GPU (other contexts or streams) race and must be ordered by the caller.
+ * Synchronises once (to size the later radix passes).
+ * Errors: EINVAL, EOVERFLOW, ECUDA. */
+PANTHER_API panther_status panther_build_index_noalloc(panther_ctx* ctx, const panther_paths* p, int64_t* dev_off,
+                                                       int32_t* dev_pid, int64_t pid_capacity, int64_t* nnz);
+
 PANTHER_API panther_status panther_index_view(const panther_index* ix, const int64_t** dev_off,
                                   const int32_t** dev_pid, int64_t* n, int64_t* nnz);
 

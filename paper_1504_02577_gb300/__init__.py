@@ -48,6 +48,7 @@ SIGNATURES = {
     "panther_paths_view": ([_vp, _P(_vp), _P(_i64), _P(_int), _P(_int)], _int),
     "panther_build_index": ([_vp, _vp, _P(_vp)], _int),
     "panther_index_view": ([_vp, _P(_vp), _P(_vp), _P(_i64), _P(_i64)], _int),
+    "panther_build_index_noalloc": ([_vp, _vp, _vp, _vp, _i64, _P(_i64)], _int),
     "panther_topk": ([_vp, _vp, _vp, _vp, _i64, _int, _vp, _vp, _int], _int),
     "panther_tune_topk": ([_vp, _vp, _vp, _vp, _i64, _int, _vp, _vp, _P(_int)], _int),
     "pantherpp_vectors": ([_vp, _vp, _vp, _int, _P(_vp)], _int),
@@ -170,6 +171,14 @@ def panther_build_index(ctx: int, p: int) -> int:
     h = _vp()
     _check(ctx, load_library().panther_build_index(ctx, p, ctypes.byref(h)))
     return h.value
+
+
+def panther_build_index_noalloc(ctx: int, p: int, dev_off, dev_pid, pid_capacity: int) -> int:
+    """Index into caller buffers with no device allocation; returns nnz."""
+    nnz = _i64()
+    _check(ctx, load_library().panther_build_index_noalloc(ctx, p, _ptr(dev_off), _ptr(dev_pid), pid_capacity,
+                                                           ctypes.byref(nnz)))
+    return nnz.value
 
 
 def panther_index_view(ix: int):

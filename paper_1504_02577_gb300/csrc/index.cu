@@ -9,6 +9,8 @@
 // stable scatter. The scatter ranks items with warp-private digit counters:
 // warps own contiguous sub-ranges of a tile and walk them in order, so the
 // sort is stable and path ids come out ascending within each vertex.
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace {
@@ -251,5 +253,139 @@ extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_pa
     cudaError_t e = cudaGetLastError();
     if (e) { panther_free_index(ix); return cuda_err(ctx, e, "index offsets"); }
     *out = ix;
+    return PANTHER_OK;
+}
+
+// ------------------------------------------------ index without allocation ---
+// A variant of the index build for callers that must not allocate device
+// memory: for example a host application that hands this library a fixed
+// share of the GPU and accounts for every byte itself, or a latency-bound
+// loop in which a cudaMalloc (which can synchronise the device) is not
+// acceptable. All temporary buffers live in one file-scope device array of
+// NA_SCRATCH_BYTES, reserved on every GPU that loads the library until the
+// process exits; the caller passes the outputs.
+namespace {
+constexpr int64_t NA_MAX_PAIRS = int64_t(1) << 22;           // R * (T+1) at most 4,194,304
+constexpr int64_t NA_MAX_TILES = 1024;                        // >= ceil(R * stride / 16384) for the limit above
+constexpr size_t NA_KV_BYTES = (size_t)NA_MAX_PAIRS * 4;      // one key or value array
+constexpr size_t NA_CNT_BYTES = (size_t)MAX_RADIX * NA_MAX_TILES * 8;
+constexpr size_t NA_SCRATCH_BYTES = 4 * NA_KV_BYTES + 2 * NA_CNT_BYTES + 256;
+
+static __device__ __align__(256) unsigned char na_scratch[NA_SCRATCH_BYTES];
+
+// exclusive scan of len int64 values by one CTA (the counts of one pass)
+__global__ void __launch_bounds__(1024) na_scan_kernel(const int64_t* __restrict__ in, int64_t* __restrict__ out,
+                                                       int64_t len, int64_t* __restrict__ total) {
+    __shared__ int64_t sh[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t base = 0; base < len; base += blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        int64_t v = i < len ? in[i] : 0, x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= (unsigned)o) x += y;
+        }
+        if (lane == 31) sh[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int64_t t = lane < (blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= (unsigned)o) t += y;
+            }
+            sh[lane] = t;
+        }
+        __syncthreads();
+        int64_t excl = carry + (wid ? sh[wid - 1] : 0) + x - v;
+        if (i < len) out[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+// device address of na_scratch, looked up once per device with that device current
+unsigned char* na_scratch_ptr[64];
+std::mutex na_mu;
+}  // namespace
+
+extern "C" panther_status panther_build_index_noalloc(panther_ctx* ctx, const panther_paths* p, int64_t* dev_off,
+                                                      int32_t* dev_pid, int64_t pid_capacity, int64_t* nnz) {
+    if (!ctx || !p || !dev_off || !dev_pid || !nnz) return PANTHER_EINVAL;
+    *nnz = 0;
+    const int64_t pairs = p->R * p->L;
+    if (pairs > NA_MAX_PAIRS)
+        return set_err(ctx, PANTHER_EOVERFLOW,
+                       "R*(T+1) = %lld exceeds the %lld pairs the static index scratch holds",
+                       (long long)pairs, (long long)NA_MAX_PAIRS);
+    if (pid_capacity < pairs) return set_err(ctx, PANTHER_EINVAL, "pid_capacity must be at least R*(T+1)");
+    if (ctx->device < 0 || ctx->device >= 64) return set_err(ctx, PANTHER_EINVAL, "device index out of range");
+    PCK(ctx, cudaSetDevice(ctx->device));
+    unsigned char* base;
+    {
+        std::lock_guard<std::mutex> lk(na_mu);
+        if (!na_scratch_ptr[ctx->device]) {
+            void* ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, na_scratch);
+            if (e != cudaSuccess || !ptr) return cuda_err(ctx, e, "cudaGetSymbolAddress(na_scratch)");
+            na_scratch_ptr[ctx->device] = (unsigned char*)ptr;
+        }
+        base = na_scratch_ptr[ctx->device];
+    }
+    int32_t* kA = (int32_t*)base;
+    int32_t* vA = (int32_t*)(base + NA_KV_BYTES);
+    int32_t* kB = (int32_t*)(base + 2 * NA_KV_BYTES);
+    int32_t* vB = (int32_t*)(base + 3 * NA_KV_BYTES);
+    int64_t* counts = (int64_t*)(base + 4 * NA_KV_BYTES);
+    int64_t* offs = (int64_t*)(base + 4 * NA_KV_BYTES + NA_CNT_BYTES);
+    int64_t* tot = (int64_t*)(base + 4 * NA_KV_BYTES + 2 * NA_CNT_BYTES);
+    cudaStream_t s = ctx->stream;
+    int passes, rb;
+    radix_plan(p->n, &passes, &rb);
+    const int radix = 1 << rb;
+    const int64_t tiles0 = ceil_div(p->R * p->stride, IX_TILE);
+    if (tiles0 > NA_MAX_TILES) return set_err(ctx, PANTHER_EOVERFLOW, "too many path rows for the static scratch");
+    Src src{};
+    src.rows = p->rows;
+    src.R = p->R;
+    src.L = p->L;
+    src.stride = p->stride;
+    src.first = 1;
+    int32_t *ik = nullptr, *ok = kA, *ov = vA;
+    int64_t count = 0;
+    for (int pass = 0; pass < passes; ++pass) {
+        const bool last = pass == passes - 1;
+        int64_t ntiles = pass == 0 ? tiles0 : ceil_div(count, IX_TILE);
+        if (ntiles < 1) ntiles = 1;
+        const int64_t len = (int64_t)radix * ntiles;
+        hist_kernel<<<(unsigned)ntiles, IX_T, 0, s>>>(src, pass * rb, radix, ntiles, counts);
+        na_scan_kernel<<<1, 1024, 0, s>>>(counts, offs, len, tot);
+        ctx->launches += 2;
+        if (pass == 0) {
+            PCK(ctx, cudaMemcpyAsync(&count, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            PCK(ctx, cudaStreamSynchronize(s));
+        }
+        int32_t* outv = last ? dev_pid : ov;     // the final pass writes the caller's pid array
+        scatter_kernel<<<(unsigned)ntiles, IX_T, 0, s>>>(src, pass * rb, radix, ntiles, offs, ok, outv);
+        ctx->launches++;
+        PCK(ctx, cudaGetLastError());
+        src.first = 0;
+        src.keys = ok;
+        src.vals = outv;
+        src.count = count;
+        ik = ok;
+        ok = (ok == kA) ? kB : kA;
+        ov = (ov == vA) ? vB : vA;
+    }
+    offsets_kernel<<<(unsigned)ceil_div(count + 1, 256), 256, 0, s>>>(ik, count, p->n, dev_off, ctx->d_status);
+    ctx->launches++;
+    PCK(ctx, cudaGetLastError());
+    *nnz = count;
     return PANTHER_OK;
 }

@@ -17,8 +17,8 @@ namespace {
 
 constexpr int IX_T = 512;                  // threads per tile CTA
 constexpr int IX_WARPS = IX_T / 32;
-constexpr int IX_ROUNDS = 32;              // 32-item rounds per warp
-constexpr int IX_TILE = IX_T * IX_ROUNDS;  // 16384 items per tile
+constexpr int IX_ROUNDS = 16;              // 32-item rounds per warp
+constexpr int IX_TILE = IX_T * IX_ROUNDS;  // 8192 items per tile
 constexpr int MAX_RADIX = 512;
 
 struct Src {
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(IX_T) hist_kernel(Src s, int shift, int radix,
     for (int d = threadIdx.x; d < radix; d += IX_T) counts[(int64_t)d * ntiles + blockIdx.x] = h[d];
 }
 
-__global__ void __launch_bounds__(IX_T) scatter_kernel(Src s, int shift, int radix, int64_t ntiles,
+__global__ void __launch_bounds__(IX_T, 2) scatter_kernel(Src s, int shift, int radix, int64_t ntiles,
                                                        const int64_t* __restrict__ offs, int32_t* __restrict__ okeys,
                                                        int32_t* __restrict__ ovals) {
     __shared__ unsigned wc[IX_WARPS][MAX_RADIX];   // per-warp digit counts, then starts within the tile
@@ -266,7 +266,7 @@ extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_pa
 // process exits; the caller passes the outputs.
 namespace {
 constexpr int64_t NA_MAX_PAIRS = int64_t(1) << 22;           // R * (T+1) at most 4,194,304
-constexpr int64_t NA_MAX_TILES = 1024;                        // >= ceil(R * stride / 16384) for the limit above
+constexpr int64_t NA_MAX_TILES = 2048;                        // >= ceil(R * stride / 8192) for the limit above
 constexpr size_t NA_KV_BYTES = (size_t)NA_MAX_PAIRS * 4;      // one key or value array
 constexpr size_t NA_CNT_BYTES = (size_t)MAX_RADIX * NA_MAX_TILES * 8;
 constexpr size_t NA_SCRATCH_BYTES = 4 * NA_KV_BYTES + 2 * NA_CNT_BYTES + 256;

@@ -295,6 +295,63 @@ __global__ void __launch_bounds__(256) lane_kernel(PathsRef P, const int32_t* __
     }
 }
 
+// Warp-convergent insertion: every lane of the warp calls these together
+// (`active` marks the lanes with something to insert); the probe loop runs
+// while any lane is still probing, so the warp never splits into nested
+// divergent branches.
+__device__ __forceinline__ bool hash_add_conv(unsigned long long* tab, uint32_t nslots, uint32_t key,
+                                              uint32_t amount, bool active) {
+    uint32_t s = active ? hslot(key, nslots) : 0;
+    bool pending = active, ok = true;
+    uint32_t probes = 0;
+    while (__any_sync(0xffffffffu, pending)) {
+        if (pending) {
+            unsigned long long cur = tab[s];
+            bool mine = cur != EMPTY && (uint32_t)(cur >> 32) == key;
+            if (cur == EMPTY) {
+                unsigned long long prev = atomicCAS(&tab[s], EMPTY, ((unsigned long long)key << 32) | amount);
+                if (prev == EMPTY) pending = false;
+                else mine = (uint32_t)(prev >> 32) == key;
+            }
+            if (mine) {
+                atomicAdd(&tab[s], (unsigned long long)amount);
+                pending = false;
+            }
+            if (pending) {
+                s = (s + 1 == nslots) ? 0 : s + 1;
+                if (++probes >= nslots) {
+                    pending = false;
+                    ok = false;
+                }
+            }
+        }
+    }
+    return ok;
+}
+
+// insert the distinct vertices u != v of path r (lanes with active == false pass r = -1)
+template <int STRIDE>
+__device__ __forceinline__ bool insert_path_conv(const PathsRef& P, int32_t r, int32_t v, unsigned long long* tab,
+                                                 uint32_t nslots, bool active) {
+    active &= (uint32_t)r < (uint64_t)P.R;
+    int32_t x[STRIDE];
+    const int4* src = (const int4*)(P.rows + (int64_t)(active ? r : 0) * STRIDE);
+#pragma unroll
+    for (int k = 0; k < STRIDE / 4; ++k) {
+        int4 q = active ? __ldg(src + k) : make_int4(-1, -1, -1, -1);
+        x[4 * k] = q.x; x[4 * k + 1] = q.y; x[4 * k + 2] = q.z; x[4 * k + 3] = q.w;
+    }
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < STRIDE; ++j) {
+        bool take = active && j < P.L && x[j] != v;
+#pragma unroll
+        for (int i = 0; i < j; ++i) take &= (x[i] != x[j]);
+        if (__any_sync(0xffffffffu, take)) ok &= hash_add_conv(tab, nslots, (uint32_t)x[j], 1u, take);
+    }
+    return ok;
+}
+
 struct Tiers {
     int32_t* list[4];    // query indices per tier: warp, CTA, global, lane
     int* count;          // [0..2] warp/CTA/global sizes, [3..4] fetch counters (warp, CTA), [5] lane size
@@ -345,7 +402,11 @@ __device__ void cta_query(const PathsRef& P, int32_t v, int64_t qi, unsigned lon
     for (uint32_t s = threadIdx.x; s < nslots; s += blockDim.x) tab[s] = EMPTY;
     __syncthreads();
     bool ok = true;
-    for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) ok &= insert_path<STRIDE, true>(P, P.pid[e], v, tab, nslots);
+    for (int64_t base = a + (threadIdx.x & ~31u); base < b; base += blockDim.x) {   // warp-uniform
+        const int64_t e = base + (threadIdx.x & 31);
+        const bool act = e < b;
+        ok &= insert_path_conv<STRIDE>(P, act ? P.pid[e] : -1, v, tab, nslots, act);
+    }
     if (!ok) flag_status(status, ST_HASH_FULL);
     __syncthreads();
     WarpTopK t;
@@ -372,7 +433,11 @@ __device__ void warp_query(const PathsRef& P, int32_t v, int64_t qi, unsigned lo
     for (uint32_t s = lane; s < ns; s += 32) tab[s] = EMPTY;
     __syncwarp();
     bool ok = true;
-    for (int64_t e = a + lane; e < b; e += 32) ok &= insert_path<STRIDE, true>(P, P.pid[e], v, tab, ns);
+    for (int64_t base = a; base < b; base += 32) {                   // warp-uniform trip count
+        const int64_t e = base + lane;
+        const bool act = e < b;
+        ok &= insert_path_conv<STRIDE>(P, act ? P.pid[e] : -1, v, tab, ns, act);
+    }
     if (!ok) flag_status(status, ST_HASH_FULL);
     __syncwarp();
     WarpTopK t;
@@ -596,7 +661,11 @@ __global__ void __launch_bounds__(512) b_scatter_kernel(PathsRef P, const int32_
     for (uint32_t s = threadIdx.x; s < nslots; s += blockDim.x) tab[s] = EMPTY;
     __syncthreads();
     bool ok = true;
-    for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) ok &= insert_path<STRIDE, true>(P, P.pid[e], v, tab, nslots);
+    for (int64_t base = a + (threadIdx.x & ~31u); base < b; base += blockDim.x) {   // warp-uniform
+        const int64_t e = base + (threadIdx.x & 31);
+        const bool act = e < b;
+        ok &= insert_path_conv<STRIDE>(P, act ? P.pid[e] : -1, v, tab, nslots, act);
+    }
     if (!ok) flag_status(status, ST_HASH_FULL);
     __syncthreads();
     const uint32_t nb = (uint32_t)(B.bucket_off[g + 1] - B.bucket_off[g]);
@@ -631,9 +700,11 @@ __global__ void __launch_bounds__(1024) b_count_kernel(BPlan B, int k, unsigned 
     for (uint32_t s = threadIdx.x; s < nslots; s += blockDim.x) tab[s] = EMPTY;
     __syncthreads();
     bool ok = true;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        unsigned long long x = B.pairs[bk * B_CAP + i];
-        ok &= hash_add<true>(tab, nslots, (uint32_t)(x >> 32), (uint32_t)x);
+    for (int base = threadIdx.x & ~31; base < cnt; base += blockDim.x) {              // warp-uniform
+        const int i = base + (threadIdx.x & 31);
+        const bool act = i < cnt;
+        const unsigned long long x = act ? B.pairs[bk * B_CAP + i] : 0ull;
+        ok &= hash_add_conv(tab, nslots, (uint32_t)(x >> 32), (uint32_t)x, act);
     }
     if (!ok) flag_status(status, ST_HASH_FULL);
     __syncthreads();

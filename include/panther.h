@@ -223,6 +223,13 @@ PANTHER_API panther_status panther_tune_topk(panther_ctx* ctx, const panther_ind
                                              const int32_t* queries, int64_t q, int k, int32_t* out_ids,
                                              uint32_t* out_counts, int* chosen);
 
+/* Set the batched form's launch shape directly (for example one chosen by
+ * panther_tune_topk in an earlier run): threads per CTA in {256, 512, 1024},
+ * shared-table slots (a multiple of 32, at least threads/32*512, at most
+ * 24,576), CTAs per SM in [1, 8]. Results do not depend on the shape.
+ * Errors: EINVAL. */
+PANTHER_API panther_status panther_set_topk_shape(panther_ctx* ctx, int threads, int table_slots, int ctas_per_sm);
+
 /* ---------------------------------------------------- Panther++ (3.3) --- */
 
 /* theta(v) = the D largest counts cnt(v,u), u != v, descending, zero padded,

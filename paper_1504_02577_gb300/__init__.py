@@ -51,6 +51,7 @@ SIGNATURES = {
     "panther_build_index_noalloc": ([_vp, _vp, _vp, _vp, _i64, _P(_i64)], _int),
     "panther_topk": ([_vp, _vp, _vp, _vp, _i64, _int, _vp, _vp, _int], _int),
     "panther_tune_topk": ([_vp, _vp, _vp, _vp, _i64, _int, _vp, _vp, _P(_int)], _int),
+    "panther_set_topk_shape": ([_vp, _int, _int, _int], _int),
     "pantherpp_vectors": ([_vp, _vp, _vp, _int, _P(_vp)], _int),
     "pantherpp_vecs_view": ([_vp, _P(_vp), _P(_i64), _P(_int)], _int),
     "pantherpp_knn": ([_vp, _vp, _vp, _i64, _int, _vp, _vp, _int], _int),
@@ -199,6 +200,10 @@ def panther_tune_topk(ctx: int, ix: int, p: int, queries, q: int, k: int, out_id
     _check(ctx, load_library().panther_tune_topk(ctx, ix, p, _ptr(queries), q, k, _ptr(out_ids), _ptr(out_counts),
                                                  chosen))
     return list(chosen)
+
+
+def panther_set_topk_shape(ctx: int, threads: int, table_slots: int, ctas_per_sm: int) -> None:
+    _check(ctx, load_library().panther_set_topk_shape(ctx, threads, table_slots, ctas_per_sm))
 
 
 def pantherpp_vectors(ctx: int, ix: int, p: int, D: int) -> int:

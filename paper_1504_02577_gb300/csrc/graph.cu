@@ -186,6 +186,54 @@ __global__ void rows_check_kernel(const int64_t* __restrict__ row_ptr, int64_t n
     if (b - a > BIG_DEG) big[atomicAdd(nbig, 1)] = (int32_t)v;
 }
 
+// rows of degree <= SMALL_STATS: one thread per row
+constexpr int64_t SMALL_STATS = 16;
+
+__global__ void __launch_bounds__(256) stats_thread_kernel(const int64_t* __restrict__ row_ptr, int64_t n,
+                                                           const int32_t* __restrict__ col,
+                                                           const uint32_t* __restrict__ w, StatsOut o) {
+    uint64_t h1 = 0, h2 = 0, mx = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = row_ptr[v], b = row_ptr[v + 1];
+        if (b < a || b - a > SMALL_STATS) continue;
+        uint64_t s = 0;
+        bool bad = false;
+        int32_t prev = -1;
+        for (int64_t i = a; i < b; ++i) {
+            int32_t u = col[i];
+            uint32_t ww = w[i];
+            bad |= (u < 0) || ((int64_t)u >= n) || ((int64_t)u == v) || (ww == 0) || (i > a && prev >= u);
+            prev = u;
+            s += ww;
+            if (u >= 0) {
+                h1 += edge_hash((uint64_t)v, (uint64_t)u, ww);
+                h2 += edge_hash((uint64_t)u, (uint64_t)v, ww);
+            }
+        }
+        const uint64_t deg = (uint64_t)(b - a);
+        o.vrec[v] = make_uint4((uint32_t)a, (uint32_t)deg, (uint32_t)s, (uint32_t)(s >> 32));
+        if (deg > 0 && (__umul64hi(s, deg) != 0 || s * deg >= (1ull << 63))) flag_status(o.status, ST_OVERFLOW);
+        if (bad) {
+            flag_status(o.status, ST_GRAPH_BAD);
+            atomicMin(o.status + 1, (uint32_t)v);
+        }
+        mx = s > mx ? s : mx;
+    }
+    // one atomic per warp
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+        h1 += __shfl_xor_sync(0xffffffffu, h1, d);
+        h2 += __shfl_xor_sync(0xffffffffu, h2, d);
+        uint64_t m2 = __shfl_xor_sync(0xffffffffu, mx, d);
+        mx = m2 > mx ? m2 : mx;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(o.acc + 0, (unsigned long long)mx);
+        atomicAdd(o.acc + 1, (unsigned long long)h1);
+        atomicAdd(o.acc + 2, (unsigned long long)h2);
+    }
+}
+
 __global__ void stats_warp_kernel(const int64_t* __restrict__ row_ptr, int64_t n, const int32_t* __restrict__ col,
                                   const uint32_t* __restrict__ w, StatsOut o) {
     WarpG g;
@@ -194,7 +242,7 @@ __global__ void stats_warp_kernel(const int64_t* __restrict__ row_ptr, int64_t n
     uint64_t h1 = 0, h2 = 0, mx = 0;
     for (int64_t v = wid; v < n; v += nw) {
         int64_t a = row_ptr[v], b = row_ptr[v + 1];
-        if (b < a || b - a > BIG_DEG) continue;
+        if (b < a || b - a > BIG_DEG || b - a <= SMALL_STATS) continue;
         row_stats(g, v, a, b - a, n, col, w, o, h1, h2, mx);
     }
     if (g.rank() == 0) {
@@ -570,8 +618,10 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
 
     StatsOut so{g->vrec, ctx->d_status, acc};
     unsigned gw = grid_for(ctx, 64, n, 256);
+    stats_thread_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->num_sms * 16), 256, 0, s>>>(
+        d_rp, n, g->col, d_w, so);
     stats_warp_kernel<<<gw, 256, 0, s>>>(d_rp, n, g->col, d_w, so);
-    ctx->launches++;
+    ctx->launches += 2;
     if (h_nbig) {
         stats_block_kernel<<<h_nbig, BLK, 0, s>>>(d_rp, n, g->col, d_w, big, so);
         ctx->launches++;

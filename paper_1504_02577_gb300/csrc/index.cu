@@ -33,42 +33,40 @@ struct Src {
     int first;          // 1 for pass 0
 };
 
-// load item i of the current source; returns false if it is not a pair
-__device__ __forceinline__ bool load_item(const Src& s, int64_t i, uint32_t& key, int32_t& val) {
+// raw word of item i (pass 0: the path entry, -1 past the end; later passes: the key)
+__device__ __forceinline__ int32_t load_raw(const Src& s, int64_t i) {
+    if (s.first) return i < s.R * s.stride ? __ldg(s.rows + i) : -1;
+    return i < s.count ? __ldg(s.keys + i) : 0;
+}
+
+// is item i a pair (pass 0: inside the path, first occurrence in its row)?
+// Every lane of the warp must call it (one __match_any_sync in pass 0).
+__device__ __forceinline__ bool item_ok(const Src& s, int64_t i, int32_t x) {
     if (s.first) {
-        int64_t total = s.R * s.stride;
-        bool inb = i < total;
-        int32_t x = inb ? s.rows[i] : -1;
-        int j = (int)(i & (s.stride - 1));
-        unsigned lane = threadIdx.x & 31;
-        unsigned peers = __match_any_sync(0xffffffffu, x);
-        unsigned rowbase = lane & ~(unsigned)(s.stride - 1);
-        unsigned rowmask = (s.stride == 32) ? 0xffffffffu : (((1u << s.stride) - 1u) << rowbase);
-        unsigned before = peers & rowmask & ((1u << lane) - 1u);
-        key = (uint32_t)x;
-        val = (int32_t)(i / s.stride);
-        return inb && j < s.L && before == 0;
-    } else {
-        bool inb = i < s.count;
-        key = inb ? (uint32_t)s.keys[i] : 0u;
-        val = inb ? s.vals[i] : 0;
-        return inb;
+        const unsigned lane = threadIdx.x & 31;
+        const unsigned peers = __match_any_sync(0xffffffffu, x);
+        const unsigned rowbase = lane & ~(unsigned)(s.stride - 1);
+        const unsigned rowmask = (s.stride == 32) ? 0xffffffffu : (((1u << s.stride) - 1u) << rowbase);
+        const unsigned before = peers & rowmask & ((1u << lane) - 1u);
+        const int j = (int)(i & (s.stride - 1));
+        return i < s.R * s.stride && j < s.L && before == 0;
     }
+    return i < s.count;
 }
 
 __global__ void __launch_bounds__(IX_T) hist_kernel(Src s, int shift, int radix, int64_t ntiles,
                                                     int64_t* __restrict__ counts) {
     __shared__ unsigned h[MAX_RADIX];
     for (int d = threadIdx.x; d < radix; d += IX_T) h[d] = 0;
+    const int64_t base = (int64_t)blockIdx.x * IX_TILE + (int64_t)(threadIdx.x >> 5) * (IX_ROUNDS * 32) +
+                         (threadIdx.x & 31);
+    int32_t x[IX_ROUNDS];
+#pragma unroll
+    for (int k = 0; k < IX_ROUNDS; ++k) x[k] = load_raw(s, base + k * 32);   // all loads in flight
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * IX_TILE;
-    int w = threadIdx.x >> 5;
-    for (int k = 0; k < IX_ROUNDS; ++k) {
-        int64_t i = base + (int64_t)w * (IX_ROUNDS * 32) + k * 32 + (threadIdx.x & 31);
-        uint32_t key;
-        int32_t val;
-        if (load_item(s, i, key, val)) atomicAdd(&h[(key >> shift) & (radix - 1)], 1u);
-    }
+#pragma unroll
+    for (int k = 0; k < IX_ROUNDS; ++k)
+        if (item_ok(s, base + k * 32, x[k])) atomicAdd(&h[((uint32_t)x[k] >> shift) & (radix - 1)], 1u);
     __syncthreads();
     for (int d = threadIdx.x; d < radix; d += IX_T) counts[(int64_t)d * ntiles + blockIdx.x] = h[d];
 }
@@ -88,11 +86,9 @@ __global__ void __launch_bounds__(IX_T, 2) scatter_kernel(Src s, int shift, int 
     uint32_t lrank[IX_ROUNDS / 2];
     uint32_t okmask = 0;
 #pragma unroll
-    for (int k = 0; k < IX_ROUNDS; ++k) {
-        int32_t val;
-        bool ok = load_item(s, base + k * 32 + lane, key[k], val);
-        okmask |= (ok ? 1u : 0u) << k;
-    }
+    for (int k = 0; k < IX_ROUNDS; ++k) key[k] = (uint32_t)load_raw(s, base + k * 32 + lane);   // loads in flight
+#pragma unroll
+    for (int k = 0; k < IX_ROUNDS; ++k) okmask |= (item_ok(s, base + k * 32 + lane, (int32_t)key[k]) ? 1u : 0u) << k;
     __syncthreads();
     // phase 1: per-warp digit counts and each item's rank within the warp
 #pragma unroll
@@ -119,16 +115,21 @@ __global__ void __launch_bounds__(IX_T, 2) scatter_kernel(Src s, int shift, int 
         }
     }
     __syncthreads();
-    // phase 3: stable scatter in item order
+    // phase 3: stable scatter in item order (values loaded together first)
+    int32_t val[IX_ROUNDS];
+#pragma unroll
+    for (int k = 0; k < IX_ROUNDS; ++k) {
+        const int64_t i = base + k * 32 + lane;
+        val[k] = s.first ? (int32_t)(i / s.stride) : (((okmask >> k) & 1u) ? __ldg(s.vals + i) : 0);
+    }
 #pragma unroll
     for (int k = 0; k < IX_ROUNDS; ++k) {
         if ((okmask >> k) & 1u) {
             uint32_t d = (key[k] >> shift) & (radix - 1);
             uint32_t r = (k & 1) ? (lrank[k >> 1] >> 16) : (lrank[k >> 1] & 0xffffu);
             int64_t pos = (int64_t)toff[d] + wc[w][d] + r;
-            int64_t i = base + k * 32 + lane;
             okeys[pos] = (int32_t)key[k];
-            ovals[pos] = s.first ? (int32_t)(i / s.stride) : s.vals[i];   // value re-read (L2-resident tile)
+            ovals[pos] = val[k];
         }
     }
 }

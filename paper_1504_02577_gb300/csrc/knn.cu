@@ -326,13 +326,16 @@ __device__ __forceinline__ Row select_group(Row r, const RowConst& c, const floa
                                             int64_t nexact) {
     if (c.qid < 0) return r;
     if (fast) {
+        // exact tiles hold exact rows in ascending id order, after every row
+        // already in the list, so a candidate tied with the k-th key never
+        // wins its tie: only y < thr can enter
         float m = y[0];
 #pragma unroll
         for (int j = 1; j < 32; ++j) m = fminf(m, y[j]);
-        if (m <= r.thr) {
+        if (m < r.thr) {
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-                if (y[j] <= r.thr) r = take_exact(r, c, y[j], cid[j]);
+                if (y[j] < r.thr) r = take_exact(r, c, y[j], cid[j]);
         }
     } else {
 #pragma unroll
@@ -528,7 +531,8 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
 constexpr int F_T = 128, F_TILE = 32;
 
 __global__ void __launch_bounds__(F_T) fp32_kernel(const uint32_t* __restrict__ theta, int D, const int32_t* __restrict__ qv,
-                                                   const float* __restrict__ qnrm, int64_t qpad,
+                                                   const uint8_t* __restrict__ qexact, const float* __restrict__ qnrm,
+                                                   int64_t qpad, int64_t nexact,
                                                    const int32_t* __restrict__ cidv, const float* __restrict__ cnrmv,
                                                    const float* __restrict__ cncfv, int64_t npad, int k,
                                                    float2* __restrict__ lists, int32_t* __restrict__ shortlist,
@@ -540,8 +544,10 @@ __global__ void __launch_bounds__(F_T) fp32_kernel(const uint32_t* __restrict__ 
     const int64_t slot = (int64_t)blockIdx.x * F_T + threadIdx.x;
     const float epsD = (float)(D + 3) * (1.0f / 8388608.0f);
     const int qid = slot < qpad ? qv[slot] : -1;
-    // FP32 products are not exact in general: every pair carries a bound
-    const RowConst rc{qid, false, 2.0f * epsD * (slot < qpad ? qnrm[slot] : 0.f), lst + threadIdx.x * KN_KMAX,
+    // rows with every entry <= 256 give exact FP32 products and partial sums
+    // (all integers below 2^24); other pairs carry the bound
+    const bool qex = slot < qpad && qexact[slot] != 0;
+    const RowConst rc{qid, qex, 2.0f * epsD * (slot < qpad ? qnrm[slot] : 0.f), lst + threadIdx.x * KN_KMAX,
                       shortlist + (slot < qpad ? slot : 0) * KN_SCAP, overflow + (slot < qpad ? slot : 0), k};
     Row r{__int_as_float(0x7f800000), 0x7fffffff, 0, 0};
     float a[KN_K];
@@ -567,7 +573,7 @@ __global__ void __launch_bounds__(F_T) fp32_kernel(const uint32_t* __restrict__ 
             for (int d = 0; d < KN_K; ++d) s = fmaf(a[d], cb[c][d], s);
             float y = fmaf(-2.0f, s, cn2[c]);
             float E = (fmaf(rc.anrm, cnr[c], epsD * cn2[c]) + 1.0f) * 1.0001f;
-            if (__fsub_rd(y, E) <= r.thr) r = take_bounded(r, rc, y, E, cidx[c], false);
+            if (__fsub_rd(y, E) <= r.thr) r = take_bounded(r, rc, y, E, cidx[c], c0 + c < nexact);
         }
     }
     if (slot < qpad) {
@@ -931,8 +937,8 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* v, const i
         screen_kernel<<<(unsigned)grid, KN_THREADS, KN_SMEM_BYTES, s>>>(tmA, tmB, S);
         ctx->launches++;
     } else {
-        fp32_kernel<<<(unsigned)(qpad / F_T), F_T, 0, s>>>(v->theta, v->D, qv, qn, qpad, x.cid, x.cnrm, x.cncf,
-                                                            x.npad, k, lists, sl, sc, ovf);
+        fp32_kernel<<<(unsigned)(qpad / F_T), F_T, 0, s>>>(v->theta, v->D, qv, qex, qn, qpad, x.nexact, x.cid,
+                                                            x.cnrm, x.cncf, x.npad, k, lists, sl, sc, ovf);
         ctx->launches++;
     }
     PCK(ctx, cudaGetLastError());

@@ -71,17 +71,28 @@ __global__ void __launch_bounds__(IX_T) hist_kernel(Src s, int shift, int radix,
     for (int d = threadIdx.x; d < radix; d += IX_T) counts[(int64_t)d * ntiles + blockIdx.x] = h[d];
 }
 
+// One tile per CTA: rank every item stably (per-warp digit counters), stage
+// the tile in shared memory in digit order, then write each digit's run with
+// consecutive threads storing consecutive positions (coalesced stores).
+constexpr size_t SC_SMEM = (size_t)IX_WARPS * MAX_RADIX * 4 + (size_t)MAX_RADIX * 8 + (size_t)MAX_RADIX * 4 +
+                           (size_t)IX_TILE * 8 + 64;
+
 __global__ void __launch_bounds__(IX_T, 2) scatter_kernel(Src s, int shift, int radix, int64_t ntiles,
-                                                       const int64_t* __restrict__ offs, int32_t* __restrict__ okeys,
-                                                       int32_t* __restrict__ ovals) {
-    __shared__ unsigned wc[IX_WARPS][MAX_RADIX];   // per-warp digit counts, then starts within the tile
-    __shared__ long long toff[MAX_RADIX];          // global start of each digit's run from this tile
+                                                          const int64_t* __restrict__ offs,
+                                                          int32_t* __restrict__ okeys, int32_t* __restrict__ ovals) {
+    extern __shared__ __align__(16) unsigned char sc_smem[];
+    unsigned (*wc)[MAX_RADIX] = (unsigned (*)[MAX_RADIX])sc_smem;                       // [warps][radix]
+    long long* toff = (long long*)(sc_smem + (size_t)IX_WARPS * MAX_RADIX * 4);        // [radix]
+    unsigned* tstart = (unsigned*)(toff + MAX_RADIX);                                  // [radix]
+    int32_t* skey = (int32_t*)(tstart + MAX_RADIX);                                    // [tile]
+    int32_t* sval = skey + IX_TILE;                                                    // [tile]
+    __shared__ unsigned wsum[IX_WARPS];
     const int w = threadIdx.x >> 5;
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     for (int d = threadIdx.x; d < IX_WARPS * MAX_RADIX; d += IX_T) (&wc[0][0])[d] = 0;
-    const int64_t base = (int64_t)blockIdx.x * IX_TILE + (int64_t)w * (IX_ROUNDS * 32);
-    // the warp's items stay in registers; lrank = rank among the warp's items of the same digit
+    const int64_t tile0 = (int64_t)blockIdx.x * IX_TILE;
+    const int64_t base = tile0 + (int64_t)w * (IX_ROUNDS * 32);
     uint32_t key[IX_ROUNDS];
     uint32_t lrank[IX_ROUNDS / 2];
     uint32_t okmask = 0;
@@ -90,7 +101,7 @@ __global__ void __launch_bounds__(IX_T, 2) scatter_kernel(Src s, int shift, int 
 #pragma unroll
     for (int k = 0; k < IX_ROUNDS; ++k) okmask |= (item_ok(s, base + k * 32 + lane, (int32_t)key[k]) ? 1u : 0u) << k;
     __syncthreads();
-    // phase 1: per-warp digit counts and each item's rank within the warp
+    // phase 1: per-warp digit counts and each item's rank within its warp
 #pragma unroll
     for (int k = 0; k < IX_ROUNDS; ++k) {
         bool ok = (okmask >> k) & 1u;
@@ -104,18 +115,40 @@ __global__ void __launch_bounds__(IX_T, 2) scatter_kernel(Src s, int shift, int 
         __syncwarp();
     }
     __syncthreads();
-    // phase 2: start of each warp's run = counts of the earlier warps (tile-relative)
-    for (int d = threadIdx.x; d < radix; d += IX_T) {
-        toff[d] = offs[(int64_t)d * ntiles + blockIdx.x];
-        unsigned run = 0;
+    // phase 2: per digit, the warps' starts within the digit and the digit's
+    // total; then the tile-level exclusive scan of the totals (digit starts)
+    unsigned tot = 0;
+    const int d2 = threadIdx.x;               // IX_T >= MAX_RADIX: one digit per thread
+    if (d2 < radix) {
+        toff[d2] = offs[(int64_t)d2 * ntiles + blockIdx.x];
         for (int ww = 0; ww < IX_WARPS; ++ww) {
-            unsigned c = wc[ww][d];
-            wc[ww][d] = run;
-            run += c;
+            unsigned c = wc[ww][d2];
+            wc[ww][d2] = tot;
+            tot += c;
         }
     }
+    unsigned x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((int)lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
     __syncthreads();
-    // phase 3: stable scatter in item order (values loaded together first)
+    if (w == 0) {
+        unsigned y = lane < IX_WARPS ? wsum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned z = __shfl_up_sync(0xffffffffu, y, o);
+            if ((int)lane >= o) y += z;
+        }
+        if (lane < IX_WARPS) wsum[lane] = y;
+    }
+    __syncthreads();
+    if (d2 < radix) tstart[d2] = x - tot + (w ? wsum[w - 1] : 0u);
+    const unsigned nvalid = wsum[IX_WARPS - 1];
+    __syncthreads();
+    // phase 3a: stage keys and values in digit order (values loaded together first)
     int32_t val[IX_ROUNDS];
 #pragma unroll
     for (int k = 0; k < IX_ROUNDS; ++k) {
@@ -127,10 +160,19 @@ __global__ void __launch_bounds__(IX_T, 2) scatter_kernel(Src s, int shift, int 
         if ((okmask >> k) & 1u) {
             uint32_t d = (key[k] >> shift) & (radix - 1);
             uint32_t r = (k & 1) ? (lrank[k >> 1] >> 16) : (lrank[k >> 1] & 0xffffu);
-            int64_t pos = (int64_t)toff[d] + wc[w][d] + r;
-            okeys[pos] = (int32_t)key[k];
-            ovals[pos] = val[k];
+            unsigned sp = tstart[d] + wc[w][d] + r;
+            skey[sp] = (int32_t)key[k];
+            sval[sp] = val[k];
         }
+    }
+    __syncthreads();
+    // phase 3b: consecutive staged items of one digit go to consecutive positions
+    for (unsigned j = threadIdx.x; j < nvalid; j += IX_T) {
+        const int32_t kk = skey[j];
+        const uint32_t d = ((uint32_t)kk >> shift) & (radix - 1);
+        const int64_t pos = (int64_t)toff[d] + (j - tstart[d]);
+        okeys[pos] = kk;
+        ovals[pos] = sval[j];
     }
 }
 
@@ -205,6 +247,7 @@ extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_pa
         panther_free_index(ix);
         return st;
     }
+    PCK(ctx, cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM));
     Src src{};
     src.rows = p->rows;
     src.R = p->R;
@@ -231,7 +274,7 @@ extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_pa
             if (!e) e = cudaStreamSynchronize(s);
             if (e) { cleanup(); panther_free_index(ix); return cuda_err(ctx, e, "index count"); }
         }
-        scatter_kernel<<<(unsigned)ntiles, IX_T, 0, s>>>(src, shift, radix, ntiles, offs, ok, ov);
+        scatter_kernel<<<(unsigned)ntiles, IX_T, SC_SMEM, s>>>(src, shift, radix, ntiles, offs, ok, ov);
         ctx->launches++;
         e = cudaGetLastError();
         if (e) { cleanup(); panther_free_index(ix); return cuda_err(ctx, e, "index scatter"); }
@@ -352,6 +395,7 @@ extern "C" panther_status panther_build_index_noalloc(panther_ctx* ctx, const pa
     const int radix = 1 << rb;
     const int64_t tiles0 = ceil_div(p->R * p->stride, IX_TILE);
     if (tiles0 > NA_MAX_TILES) return set_err(ctx, PANTHER_EOVERFLOW, "too many path rows for the static scratch");
+    PCK(ctx, cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM));
     Src src{};
     src.rows = p->rows;
     src.R = p->R;
@@ -373,7 +417,7 @@ extern "C" panther_status panther_build_index_noalloc(panther_ctx* ctx, const pa
             PCK(ctx, cudaStreamSynchronize(s));
         }
         int32_t* outv = last ? dev_pid : ov;     // the final pass writes the caller's pid array
-        scatter_kernel<<<(unsigned)ntiles, IX_T, 0, s>>>(src, pass * rb, radix, ntiles, offs, ok, outv);
+        scatter_kernel<<<(unsigned)ntiles, IX_T, SC_SMEM, s>>>(src, pass * rb, radix, ntiles, offs, ok, outv);
         ctx->launches++;
         PCK(ctx, cudaGetLastError());
         src.first = 0;

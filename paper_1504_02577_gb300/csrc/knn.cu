@@ -246,8 +246,8 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-    uint32_t r[32];
+// 32 columns of this thread's TMEM lane into r (asynchronous: wait before use)
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -257,9 +257,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// ties the registers to a point after the wait, so no use is scheduled before it
+__device__ __forceinline__ void reg_fence(uint32_t (&r)[32]) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31]));
 }
 
 // ---------------------------------------------------------- selection ---
@@ -329,9 +336,14 @@ __device__ __forceinline__ Row select_group(Row r, const RowConst& c, const floa
         // exact tiles hold exact rows in ascending id order, after every row
         // already in the list, so a candidate tied with the k-th key never
         // wins its tie: only y < thr can enter
-        float m = y[0];
+        float t16[16];
 #pragma unroll
-        for (int j = 1; j < 32; ++j) m = fminf(m, y[j]);
+        for (int j = 0; j < 16; ++j) t16[j] = fminf(y[j], y[j + 16]);
+#pragma unroll
+        for (int w = 8; w; w >>= 1)
+#pragma unroll
+            for (int j = 0; j < w; ++j) t16[j] = fminf(t16[j], t16[j + w]);
+        const float m = t16[0];
         if (m < r.thr) {
 #pragma unroll
             for (int j = 0; j < 32; ++j)
@@ -498,12 +510,32 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
                 const float* cnrm = (const float*)(info + KN_N * 4);
                 const float* cncf = (const float*)(info + KN_N * 8);
                 const bool fast = qtile_exact && S.ctile[ct];
-                for (int g = 0; g < KN_N / 32; ++g) {
-                    float y[32];
+                const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + b * KN_N;
+#pragma unroll
+                for (int h = 0; h < KN_N / 128; ++h) {
+                    uint32_t u0[32], u1[32], u2[32], u3[32];
                     __syncwarp();
-                    tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + b * KN_N + g * 32, y);
-                    r = select_group(r, rc, y, fast, cid + g * 32, cnrm + g * 32, cncf + g * 32,
-                                     ct * KN_N + g * 32, S.nexact);
+                    tmem_ld32_async(tbase + h * 128 + 0, u0);
+                    tmem_ld32_async(tbase + h * 128 + 32, u1);
+                    tmem_ld32_async(tbase + h * 128 + 64, u2);
+                    tmem_ld32_async(tbase + h * 128 + 96, u3);
+                    tmem_wait_ld();
+                    reg_fence(u0);
+                    reg_fence(u1);
+                    reg_fence(u2);
+                    reg_fence(u3);
+                    float y[32];
+#define KN_GROUP(U, G)                                                                                   \
+    {                                                                                                    \
+        _Pragma("unroll") for (int j = 0; j < 32; ++j) y[j] = __uint_as_float(U[j]);                     \
+        const int c0 = h * 128 + (G) * 32;                                                               \
+        r = select_group(r, rc, y, fast, cid + c0, cnrm + c0, cncf + c0, ct * KN_N + c0, S.nexact);      \
+    }
+                    KN_GROUP(u0, 0)
+                    KN_GROUP(u1, 1)
+                    KN_GROUP(u2, 2)
+                    KN_GROUP(u3, 3)
+#undef KN_GROUP
                 }
                 tc_fence_before();
                 __syncwarp();

@@ -228,39 +228,6 @@ __device__ __forceinline__ bool row_has(const int32_t (&r)[8], int32_t u) {
     return h;
 }
 
-// count the distinct u != v of the first NP rows (each at its first
-// occurrence, against the later rows) and keep the best scores
-template <int NP>
-__device__ __forceinline__ void lane_count(const int32_t (&row)[LANE_NP][8], int32_t v, uint64_t (&best)[LANE_K]) {
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int32_t u = row[i][j];
-            bool first = u >= 0 && u != v;
-#pragma unroll
-            for (int jj = 0; jj < j; ++jj) first &= row[i][jj] != u;
-#pragma unroll
-            for (int ii = 0; ii < i; ++ii) first &= !row_has(row[ii], u);
-            if (first) {
-                uint32_t c = 1;
-#pragma unroll
-                for (int ii = i + 1; ii < NP; ++ii) c += row_has(row[ii], u) ? 1u : 0u;
-                uint64_t sc = ((uint64_t)c << 32) | (uint64_t)(0xffffffffu - (uint32_t)u);
-                if (sc > best[LANE_K - 1]) {
-#pragma unroll
-                    for (int t = 0; t < LANE_K; ++t) {   // sorted insertion (descending)
-                        uint64_t hi = best[t] > sc ? best[t] : sc;
-                        uint64_t lo = best[t] > sc ? sc : best[t];
-                        best[t] = hi;
-                        sc = lo;
-                    }
-                }
-            }
-        }
-    }
-}
-
 __global__ void __launch_bounds__(256) lane_kernel(PathsRef P, const int32_t* __restrict__ queries,
                                                    const int32_t* __restrict__ list, const int* __restrict__ count,
                                                    int slot, OutRef o) {
@@ -291,13 +258,31 @@ __global__ void __launch_bounds__(256) lane_kernel(PathsRef P, const int32_t* __
         uint64_t best[LANE_K];
 #pragma unroll
         for (int t = 0; t < LANE_K; ++t) best[t] = 0;
-        switch (np) {   // work grows with np^2: one unrolled body per path count
-            case 1: lane_count<1>(row, v, best); break;
-            case 2: lane_count<2>(row, v, best); break;
-            case 3: lane_count<3>(row, v, best); break;
-            case 4: lane_count<4>(row, v, best); break;
-            case 5: lane_count<5>(row, v, best); break;
-            default: lane_count<LANE_NP>(row, v, best); break;
+#pragma unroll
+        for (int i = 0; i < LANE_NP; ++i) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int32_t u = row[i][j];
+                bool first = u >= 0 && u != v;
+#pragma unroll
+                for (int jj = 0; jj < j; ++jj) first &= row[i][jj] != u;
+#pragma unroll
+                for (int ii = 0; ii < i; ++ii) first &= !row_has(row[ii], u);
+                if (first) {
+                    uint32_t c = 1;
+#pragma unroll
+                    for (int ii = i + 1; ii < LANE_NP; ++ii) c += row_has(row[ii], u) ? 1u : 0u;
+                    uint64_t sc = ((uint64_t)c << 32) | (uint64_t)(0xffffffffu - (uint32_t)u);
+                    // sorted insertion (descending)
+#pragma unroll
+                    for (int t = 0; t < LANE_K; ++t) {
+                        uint64_t hi = best[t] > sc ? best[t] : sc;
+                        uint64_t lo = best[t] > sc ? sc : best[t];
+                        best[t] = hi;
+                        sc = lo;
+                    }
+                }
+            }
         }
 #pragma unroll
         for (int t = 0; t < LANE_K; ++t) {

@@ -572,15 +572,20 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
     g->n = n;
     g->m = m;
     g->modes = modes;
-    int64_t* d_rp = nullptr;
-    uint32_t* d_w = nullptr;
+    // Host inputs are staged in temporary device buffers; device inputs are
+    // read in place (the call returns only after the tables are built, and the
+    // tables carry the neighbour ids, so nothing of the CSR is kept).
+    int64_t* t_rp = nullptr;
+    int32_t* t_col = nullptr;
+    uint32_t* t_w = nullptr;
     int32_t* big = nullptr;
     int* nbig = nullptr;
     unsigned long long* acc = nullptr;
     panther_status st = PANTHER_OK;
     auto fail = [&](panther_status e) {
-        dev_free(ctx, d_rp);
-        dev_free(ctx, d_w);
+        dev_free(ctx, t_rp);
+        dev_free(ctx, t_col);
+        dev_free(ctx, t_w);
         dev_free(ctx, big);
         dev_free(ctx, nbig);
         dev_free(ctx, acc);
@@ -588,19 +593,26 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
         panther_free_graph(g);
         return e;
     };
-    if ((st = dev_alloc(ctx, (void**)&d_rp, sizeof(int64_t) * (n + 1))) ||
-        (st = dev_alloc(ctx, (void**)&g->col, sizeof(int32_t) * m)) ||
-        (st = dev_alloc(ctx, (void**)&d_w, sizeof(uint32_t) * m)) ||
-        (st = dev_alloc(ctx, (void**)&g->vrec, sizeof(uint4) * n)) ||
+    if ((st = dev_alloc(ctx, (void**)&g->vrec, sizeof(uint4) * n)) ||
         (st = dev_alloc(ctx, (void**)&big, sizeof(int32_t) * (n + 1))) ||
         (st = dev_alloc(ctx, (void**)&nbig, sizeof(int) * 2)) ||
         (st = dev_alloc(ctx, (void**)&acc, sizeof(unsigned long long) * 4)))
         return fail(st);
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(d_rp, row_ptr, sizeof(int64_t) * (n + 1), kind, s)) ||
-        (m && (e = cudaMemcpyAsync(g->col, col, sizeof(int32_t) * m, kind, s))) ||
-        (m && (e = cudaMemcpyAsync(d_w, w, sizeof(uint32_t) * m, kind, s))) ||
-        (e = cudaMemsetAsync(nbig, 0, sizeof(int) * 2, s)) ||
+    if (mem == PANTHER_MEM_HOST) {
+        if ((st = dev_alloc(ctx, (void**)&t_rp, sizeof(int64_t) * (n + 1))) ||
+            (st = dev_alloc(ctx, (void**)&t_col, sizeof(int32_t) * m)) ||
+            (st = dev_alloc(ctx, (void**)&t_w, sizeof(uint32_t) * m)))
+            return fail(st);
+        if ((e = cudaMemcpyAsync(t_rp, row_ptr, sizeof(int64_t) * (n + 1), kind, s)) ||
+            (m && (e = cudaMemcpyAsync(t_col, col, sizeof(int32_t) * m, kind, s))) ||
+            (m && (e = cudaMemcpyAsync(t_w, w, sizeof(uint32_t) * m, kind, s))))
+            return fail(cuda_err(ctx, e, "graph upload"));
+    }
+    const int64_t* d_rp = mem == PANTHER_MEM_HOST ? t_rp : row_ptr;
+    const int32_t* d_col = mem == PANTHER_MEM_HOST ? t_col : col;
+    const uint32_t* d_w = mem == PANTHER_MEM_HOST ? t_w : w;
+    if ((e = cudaMemsetAsync(nbig, 0, sizeof(int) * 2, s)) ||
         (e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 4, s)) ||
         (e = cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s)) ||
         (e = cudaMemsetAsync(ctx->d_status + 1, 0xff, sizeof(uint32_t), s)))
@@ -619,11 +631,11 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
     StatsOut so{g->vrec, ctx->d_status, acc};
     unsigned gw = grid_for(ctx, 64, n, 256);
     stats_thread_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->num_sms * 16), 256, 0, s>>>(
-        d_rp, n, g->col, d_w, so);
-    stats_warp_kernel<<<gw, 256, 0, s>>>(d_rp, n, g->col, d_w, so);
+        d_rp, n, d_col, d_w, so);
+    stats_warp_kernel<<<gw, 256, 0, s>>>(d_rp, n, d_col, d_w, so);
     ctx->launches += 2;
     if (h_nbig) {
-        stats_block_kernel<<<h_nbig, BLK, 0, s>>>(d_rp, n, g->col, d_w, big, so);
+        stats_block_kernel<<<h_nbig, BLK, 0, s>>>(d_rp, n, d_col, d_w, big, so);
         ctx->launches++;
     }
     unsigned long long h_acc[3];
@@ -649,11 +661,11 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
         size_t esz = g->prefix_wide ? sizeof(uint4) : sizeof(uint2);
         if ((st = dev_alloc(ctx, &g->prefix, esz * (size_t)m))) return fail(st);
         if (g->prefix_wide) {
-            prefix_warp_kernel<true><<<gw, 256, 0, s>>>(d_rp, n, g->col, d_w, g->prefix);
-            if (h_nbig) prefix_block_kernel<true><<<h_nbig, BLK, 0, s>>>(d_rp, g->col, d_w, big, g->prefix);
+            prefix_warp_kernel<true><<<gw, 256, 0, s>>>(d_rp, n, d_col, d_w, g->prefix);
+            if (h_nbig) prefix_block_kernel<true><<<h_nbig, BLK, 0, s>>>(d_rp, d_col, d_w, big, g->prefix);
         } else {
-            prefix_warp_kernel<false><<<gw, 256, 0, s>>>(d_rp, n, g->col, d_w, g->prefix);
-            if (h_nbig) prefix_block_kernel<false><<<h_nbig, BLK, 0, s>>>(d_rp, g->col, d_w, big, g->prefix);
+            prefix_warp_kernel<false><<<gw, 256, 0, s>>>(d_rp, n, d_col, d_w, g->prefix);
+            if (h_nbig) prefix_block_kernel<false><<<h_nbig, BLK, 0, s>>>(d_rp, d_col, d_w, big, g->prefix);
         }
         ctx->launches += h_nbig ? 2 : 1;
         if ((e = cudaGetLastError())) return fail(cuda_err(ctx, e, "prefix table"));
@@ -668,8 +680,8 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
             return fail(st);
         }
         alias_thread_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->num_sms * 16), 256, 0, s>>>(
-            g->vrec, n, g->col, d_w, g->alias);
-        alias_warp_kernel<<<gw, 256, 0, s>>>(g->vrec, n, g->col, d_w, g->alias, sidx, scum);
+            g->vrec, n, d_col, d_w, g->alias);
+        alias_warp_kernel<<<gw, 256, 0, s>>>(g->vrec, n, d_col, d_w, g->alias, sidx, scum);
         ctx->launches += 2;
         if (h_nbig) {
             int64_t* bign = nullptr;
@@ -678,8 +690,8 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
                 dev_free(ctx, scum);
                 return fail(st);
             }
-            alias_block_kernel<<<h_nbig, BLK, 0, s>>>(g->vrec, g->col, d_w, big, g->alias, sidx, scum, bign);
-            alias_assign_kernel<<<(unsigned)(h_nbig * ASSIGN_SPLIT), 256, 0, s>>>(g->vrec, g->col, d_w, big, bign,
+            alias_block_kernel<<<h_nbig, BLK, 0, s>>>(g->vrec, d_col, d_w, big, g->alias, sidx, scum, bign);
+            alias_assign_kernel<<<(unsigned)(h_nbig * ASSIGN_SPLIT), 256, 0, s>>>(g->vrec, d_col, d_w, big, bign,
                                                                                g->alias, sidx, scum);
             ctx->launches += 2;
             dev_free(ctx, bign);
@@ -689,13 +701,14 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
         dev_free(ctx, scum);
         if (e) return fail(cuda_err(ctx, e, "alias table"));
     }
-    dev_free(ctx, d_rp);
-    dev_free(ctx, d_w);
+    dev_free(ctx, t_rp);
+    dev_free(ctx, t_col);
+    dev_free(ctx, t_w);
     dev_free(ctx, big);
     dev_free(ctx, nbig);
     dev_free(ctx, acc);
     if ((e = cudaStreamSynchronize(s))) {
-        d_rp = nullptr; d_w = nullptr; big = nullptr; nbig = nullptr; acc = nullptr;
+        t_rp = nullptr; t_col = nullptr; t_w = nullptr; big = nullptr; nbig = nullptr; acc = nullptr;
         return fail(cuda_err(ctx, e, "graph tables"));
     }
     *out = g;

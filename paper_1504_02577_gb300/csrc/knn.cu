@@ -47,7 +47,8 @@ constexpr int KN_K = 64;           // padded vector length (bf16)
 constexpr int KN_STAGES = 4;
 constexpr int KN_KMAX = 32;
 constexpr int KN_SCAP = 256;       // shortlist capacity per query
-constexpr int KN_THREADS = 192;    // warp 0 TMA, warp 1 MMA, warps 2-5 selection
+constexpr int KN_SPLIT = 2;        // selection warps per TMEM lane quarter (each takes one column slice)
+constexpr int KN_THREADS = 64 + 128 * KN_SPLIT;   // warp 0 TMA, warp 1 MMA, then the selection warps
 constexpr float KN_ALPHA = 0.0157f;    // >= 2(2u+u^2) + 2 gamma (1+u)^2
 constexpr float KN_BETA = 1.6e-5f;     // >= gamma = 2^-16
 constexpr uint32_t MAX_EXACT = 256;
@@ -383,8 +384,8 @@ struct ScreenArgs {
 constexpr uint32_t SM_A = 0;                                   // 16 KB
 constexpr uint32_t SM_B = SM_A + KN_M * KN_K * 2;              // KN_STAGES x 32 KB
 constexpr uint32_t SM_INFO = SM_B + KN_STAGES * KN_N * KN_K * 2;  // KN_STAGES x 3 KB
-constexpr uint32_t SM_LIST = SM_INFO + KN_STAGES * KN_N * 12;  // 128 x KMAX x 8 B
-constexpr uint32_t SM_BAR = SM_LIST + KN_M * KN_KMAX * 8;      // barriers
+constexpr uint32_t SM_LIST = SM_INFO + KN_STAGES * KN_N * 12;  // 128 x SPLIT x KMAX x 8 B
+constexpr uint32_t SM_BAR = SM_LIST + KN_M * KN_SPLIT * KN_KMAX * 8;   // barriers
 constexpr uint32_t SM_TOTAL = SM_BAR + 256;
 constexpr uint32_t KN_SMEM_BYTES = SM_TOTAL + 1024;
 
@@ -408,11 +409,11 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < KN_STAGES; ++s) {
             mbar_init(FULL(s), 1);
-            mbar_init(EMPTY(s), 1 + 4);
+            mbar_init(EMPTY(s), 1 + 4 * KN_SPLIT);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(TFULL(b), 1);
-            mbar_init(TEMPTY(b), 4);
+            mbar_init(TEMPTY(b), 4 * KN_SPLIT);
         }
         mbar_init(AFULL, 1);
         mbar_init(AEMPTY, 1);
@@ -485,14 +486,16 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
     } else {
         // --------------------------------------------------- selection ---
         const int quarter = warp & 3;             // TMEM lanes 32*quarter .. +31
+        const int half = (warp - 2) >> 2;         // column slice of every tile this warp screens
         const int row = quarter * 32 + lane;
-        float2* mylist = (float2*)(gbase + SM_LIST) + row * KN_KMAX;
+        float2* mylist = (float2*)(gbase + SM_LIST) + (row * KN_SPLIT + half) * KN_KMAX;
         int64_t it = 0;
         for (int64_t qt = blockIdx.x; qt < S.nqt; qt += gridDim.x) {
             const int64_t slot = qt * KN_M + row;
             Row r{__int_as_float(0x7f800000), 0x7fffffff, 0, 0};
+            const int64_t state = slot * KN_SPLIT + half;
             const RowConst rc{S.qv[slot], S.qexact[slot] != 0, KN_ALPHA * S.qnrm[slot], mylist,
-                              S.shortlist + slot * KN_SCAP, S.overflow + slot, S.k};
+                              S.shortlist + state * KN_SCAP, S.overflow + slot, S.k};
             const bool qtile_exact = S.qtile[qt] != 0;
             bool ok = true;
             for (int64_t ct = 0; ct < S.nct; ++ct, ++it) {
@@ -511,8 +514,8 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
                 const float* cncf = (const float*)(info + KN_N * 8);
                 const bool fast = qtile_exact && S.ctile[ct];
                 const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + b * KN_N;
-#pragma unroll
-                for (int h = 0; h < KN_N / 128; ++h) {
+                {
+                    const int h = half;                   // 128 columns per selection warp
                     uint32_t u0[32], u1[32], u2[32], u3[32];
                     __syncwarp();
                     tmem_ld32_async(tbase + h * 128 + 0, u0);
@@ -546,8 +549,8 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
             }
             if (!ok) break;
             for (int i = 0; i < S.k; ++i)
-                S.lists[slot * S.k + i] = i < r.n ? mylist[i] : make_float2(0.f, __int_as_float(-1));
-            S.scount[slot] = r.scount;
+                S.lists[state * S.k + i] = i < r.n ? mylist[i] : make_float2(0.f, __int_as_float(-1));
+            S.scount[state] = r.scount;
         }
     }
     tc_fence_before();
@@ -580,7 +583,7 @@ __global__ void __launch_bounds__(F_T) fp32_kernel(const uint32_t* __restrict__ 
     // (all integers below 2^24); other pairs carry the bound
     const bool qex = slot < qpad && qexact[slot] != 0;
     const RowConst rc{qid, qex, 2.0f * epsD * (slot < qpad ? qnrm[slot] : 0.f), lst + threadIdx.x * KN_KMAX,
-                      shortlist + (slot < qpad ? slot : 0) * KN_SCAP, overflow + (slot < qpad ? slot : 0), k};
+                      shortlist + (slot < qpad ? slot : 0) * KN_SPLIT * KN_SCAP, overflow + (slot < qpad ? slot : 0), k};
     Row r{__int_as_float(0x7f800000), 0x7fffffff, 0, 0};
     float a[KN_K];
 #pragma unroll
@@ -609,8 +612,12 @@ __global__ void __launch_bounds__(F_T) fp32_kernel(const uint32_t* __restrict__ 
         }
     }
     if (slot < qpad) {
-        for (int i = 0; i < k; ++i) lists[slot * k + i] = i < r.n ? rc.list[i] : make_float2(0.f, __int_as_float(-1));
-        scount[slot] = r.scount;
+        for (int i = 0; i < k; ++i) {
+            lists[(slot * KN_SPLIT) * k + i] = i < r.n ? rc.list[i] : make_float2(0.f, __int_as_float(-1));
+            for (int h = 1; h < KN_SPLIT; ++h) lists[(slot * KN_SPLIT + h) * k + i] = make_float2(0.f, __int_as_float(-1));
+        }
+        scount[slot * KN_SPLIT] = r.scount;
+        for (int h = 1; h < KN_SPLIT; ++h) scount[slot * KN_SPLIT + h] = 0;
     }
 }
 
@@ -642,10 +649,18 @@ __global__ void rerank_kernel(const uint32_t* __restrict__ theta, int D, const i
     const int32_t v = qv[slot];
     if (v < 0 || overflow[slot]) return;   // padding, or handled by the brute-force fallback
     const int64_t qi = qidx[slot];
-    const int ns = min(scount[slot], KN_SCAP);
-    const int total = k + ns;
+    // candidates: the lists of the column slices, then their shortlists
+    int ns[KN_SPLIT];
+    int nst = 0;
+#pragma unroll
+    for (int h = 0; h < KN_SPLIT; ++h) {
+        ns[h] = min(scount[slot * KN_SPLIT + h], KN_SCAP);
+        nst += ns[h];
+    }
+    const int nl = KN_SPLIT * k;
+    const int total = nl + nst;
     // each lane holds up to ceil(total/32) candidates
-    constexpr int PER = (KN_KMAX + KN_SCAP + 31) / 32;
+    constexpr int PER = (KN_SPLIT * (KN_KMAX + KN_SCAP) + 31) / 32;
     uint64_t dd[PER];
     int id[PER];
 #pragma unroll
@@ -654,7 +669,14 @@ __global__ void rerank_kernel(const uint32_t* __restrict__ theta, int D, const i
         id[t] = -1;
         dd[t] = ~0ull;
         if (i < total) {
-            int c = i < k ? __float_as_int(lists[slot * k + i].y) : shortlist[slot * KN_SCAP + (i - k)];
+            int c;
+            if (i < nl) {
+                c = __float_as_int(lists[slot * nl + i].y);
+            } else {
+                int j = i - nl, h = 0;
+                while (h < KN_SPLIT - 1 && j >= ns[h]) j -= ns[h++];
+                c = shortlist[(slot * KN_SPLIT + h) * KN_SCAP + j];
+            }
             if (c >= 0) {
                 id[t] = c;
                 dd[t] = exact_d2(theta, D, v, c);
@@ -924,11 +946,11 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* v, const i
     if ((st = dev_alloc(ctx, (void**)&qf, sizeof(int64_t) * q)) ||
         (st = dev_alloc(ctx, (void**)&qv, sizeof(int32_t) * qpad)) ||
         (st = dev_alloc(ctx, (void**)&qidx, sizeof(int32_t) * qpad)) ||
-        (st = dev_alloc(ctx, (void**)&sl, sizeof(int32_t) * qpad * KN_SCAP)) ||
-        (st = dev_alloc(ctx, (void**)&sc, sizeof(int32_t) * qpad)) ||
+        (st = dev_alloc(ctx, (void**)&sl, sizeof(int32_t) * qpad * KN_SPLIT * KN_SCAP)) ||
+        (st = dev_alloc(ctx, (void**)&sc, sizeof(int32_t) * qpad * KN_SPLIT)) ||
         (st = dev_alloc(ctx, (void**)&ovf, sizeof(int) * qpad)) || (st = dev_alloc(ctx, (void**)&qex, qpad)) ||
         (st = dev_alloc(ctx, (void**)&qtile, qpad / KN_M)) || (st = dev_alloc(ctx, (void**)&qn, sizeof(float) * qpad)) ||
-        (st = dev_alloc(ctx, (void**)&lists, sizeof(float2) * qpad * k)) ||
+        (st = dev_alloc(ctx, (void**)&lists, sizeof(float2) * qpad * KN_SPLIT * k)) ||
         (!fp32 && (st = dev_alloc(ctx, (void**)&A, (size_t)qpad * KN_K * 2)))) {
         cleanup();
         return st;
@@ -981,14 +1003,14 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* v, const i
     ctx->launches += 2;
     PCK(ctx, cudaGetLastError());
     // screening statistics (pairs screened, kept for rerank, overflowed queries)
-    std::vector<int32_t> hsc(qpad);
+    std::vector<int32_t> hsc(qpad * KN_SPLIT);
     std::vector<int> hov(qpad);
-    PCK(ctx, cudaMemcpyAsync(hsc.data(), sc, sizeof(int32_t) * qpad, cudaMemcpyDeviceToHost, s));
+    PCK(ctx, cudaMemcpyAsync(hsc.data(), sc, sizeof(int32_t) * qpad * KN_SPLIT, cudaMemcpyDeviceToHost, s));
     PCK(ctx, cudaMemcpyAsync(hov.data(), ovf, sizeof(int) * qpad, cudaMemcpyDeviceToHost, s));
     PCK(ctx, cudaStreamSynchronize(s));
     int64_t kept = 0, over = 0;
     for (int64_t i = 0; i < qpad; ++i) {
-        kept += hsc[i];
+        for (int h = 0; h < KN_SPLIT; ++h) kept += hsc[i * KN_SPLIT + h];
         over += hov[i];
     }
     ctx->knn_stats[0] = q * n;

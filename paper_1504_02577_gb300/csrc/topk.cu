@@ -603,6 +603,21 @@ __global__ void g_select_kernel(GPlan G, unsigned long long* arena, int k, unsig
     }
 }
 
+// merge the partial lists of one query with a whole CTA (warps take lists
+// strided, then a tree merge)
+__global__ void __launch_bounds__(256) g_merge_cta_kernel(GPlan G, const unsigned long long* __restrict__ partial,
+                                                          OutRef o) {
+    __shared__ unsigned long long lists[8 * KMAX];
+    const int g = blockIdx.x;
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned lane = threadIdx.x & 31;
+    WarpTopK t;
+    for (int64_t it = G.sel_off[g] + w; it < G.sel_off[g + 1]; it += nw)
+        t.merge(partial[it * KMAX + lane], partial[it * KMAX + 32 + lane]);
+    cta_merge(t, lists);
+    if (w == 0) write_list(t, o, G.qidx[g]);
+}
+
 __global__ void g_merge_kernel(GPlan G, const unsigned long long* __restrict__ partial, OutRef o) {
     int g = blockIdx.x;
     if (g >= G.ng || threadIdx.x >= 32) return;
@@ -624,9 +639,10 @@ __global__ void g_merge_kernel(GPlan G, const unsigned long long* __restrict__ p
 // bucket that fills up marks its query, which is then counted again by the
 // global-table path.
 constexpr int B_SLOTS1 = 8192;     // pass-1 table (one chunk, T <= 7)
-constexpr int B_CAP = 12288;       // pairs per bucket
-constexpr int B_SLOTS2 = 16384;    // pass-2 table
-constexpr int B_TARGET = 4096;     // expected pairs per bucket when sizing nb
+constexpr int B_CAP = 4096;        // pairs per bucket
+constexpr int B_SLOTS2 = 8192;     // pass-2 table
+constexpr int B_TARGET = 2048;     // expected pairs per bucket when sizing nb
+constexpr int B_T2 = 256;          // threads of a pass-2 CTA
 
 struct BPlan {
     int bpaths;                // paths per pass-1 chunk
@@ -690,10 +706,10 @@ __global__ void __launch_bounds__(512) b_scatter_kernel(PathsRef P, const int32_
     }
 }
 
-__global__ void __launch_bounds__(1024) b_count_kernel(BPlan B, int k, unsigned long long* __restrict__ partial,
+__global__ void __launch_bounds__(B_T2) b_count_kernel(BPlan B, int k, unsigned long long* __restrict__ partial,
                                                        uint32_t* status) {
     extern __shared__ unsigned long long tab[];
-    __shared__ unsigned long long lists[32 * KMAX];
+    __shared__ unsigned long long lists[(B_T2 / 32) * KMAX];
     const int64_t bk = blockIdx.x;
     const int cnt = min(B.cursor[bk], B_CAP);
     const uint32_t nslots = table_size(cnt, 1024, B_SLOTS2);
@@ -855,9 +871,9 @@ static panther_status hub_buckets(panther_ctx* ctx, const PathsRef& P, const int
         if (stride == 8) b_scatter_kernel<8><<<g1, 512, B_SLOTS1 * 8, s>>>(P, queries, B, ctx->d_status);
         else if (stride == 16) b_scatter_kernel<16><<<g1, 512, B_SLOTS1 * 8, s>>>(P, queries, B, ctx->d_status);
         else b_scatter_kernel<32><<<g1, 512, B_SLOTS1 * 8, s>>>(P, queries, B, ctx->d_status);
-        b_count_kernel<<<(unsigned)nbt, 1024, B_SLOTS2 * 8, s>>>(B, k, partial, ctx->d_status);
+        b_count_kernel<<<(unsigned)nbt, B_T2, B_SLOTS2 * 8, s>>>(B, k, partial, ctx->d_status);
         GPlan G{B.qidx, nullptr, nullptr, nullptr, B.bucket_off, rng};
-        g_merge_kernel<<<rng, 32, 0, s>>>(G, partial, o);
+        g_merge_cta_kernel<<<rng, 256, 0, s>>>(G, partial, o);
         ctx->launches += 3;
         PCK(ctx, cudaGetLastError());
         std::vector<int> hov(rng);

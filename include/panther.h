@@ -131,10 +131,12 @@ PANTHER_API panther_status panther_sample_size(double eps, double delta, double 
  *   w        uint32[m], weights >= 1; w(u,v) = w(v,u)
  *   mem      PANTHER_MEM_HOST or PANTHER_MEM_DEVICE for the three arrays
  *   modes    PANTHER_MODE_PREFIX | PANTHER_MODE_ALIAS: tables to build
- * The arrays are copied; the caller keeps ownership. The call validates the
- * graph on the device (ranges, sorted rows, no self-loops, symmetry with
- * equal weights, every row sum * degree < 2^63) and returns after the
- * tables are built (it synchronises the stream).
+ * Host arrays are staged in temporary device buffers; device arrays are read
+ * in place during the call. The caller keeps ownership and nothing of the
+ * CSR is kept afterwards (the tables hold what sampling needs). The call
+ * validates the graph on the device (ranges, sorted rows, no self-loops,
+ * symmetry with equal weights, every row sum * degree < 2^63) and returns
+ * after the tables are built (it synchronises the stream).
  * Errors: EINVAL (bad arguments or graph), EOVERFLOW (m >= 2^32, row sum too
  * large), ENOMEM, ECUDA. */
 PANTHER_API panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64_t m,

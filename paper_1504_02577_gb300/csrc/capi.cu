@@ -163,7 +163,6 @@ panther_status pantherpp_vecs_view(const pantherpp_vecs* v, const uint32_t** dev
 void panther_free_graph(panther_graph* g) {
     if (!g) return;
     panther_ctx* c = g->ctx;
-    dev_free(c, g->col);
     dev_free(c, g->vrec);
     dev_free(c, g->prefix);
     dev_free(c, g->alias);

@@ -40,7 +40,6 @@ struct panther_graph {
     panther_ctx* ctx = nullptr;
     int64_t n = 0, m = 0;
     int modes = 0;
-    int32_t* col = nullptr;          // [m]
     uint4* vrec = nullptr;           // [n]: {start, deg, S_lo, S_hi}
     void* prefix = nullptr;          // [m]: uint2 {cum, col} or uint4 {cum_lo, cum_hi, col, 0}
     int prefix_wide = 0;             // 1 when a row sum reaches 2^32

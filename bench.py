@@ -531,12 +531,167 @@ def run_knn(args, ws, rank, local):
         "gpu_launches": int(launches), "clocks": clocks,
     }
 
+
+# --------------------------------------------------------- serving arm ---
+def _requests(n, count, rng):
+    """Mixed requests: 75% top-k (k in {5,10,50}, 1-4,096 vertices, log-uniform
+    sizes), 25% k-NN (k = 10, 1-1,024 vertices); query vertices uniform."""
+    reqs = []
+    for _ in range(count):
+        if rng.random() < 0.75:
+            kind, k, size = 0, int(rng.choice([5, 10, 50])), int(np.floor(4097 ** rng.random()))
+        else:
+            kind, k, size = 1, 10, int(np.floor(1025 ** rng.random()))
+        size = max(1, size)
+        q = rng.integers(0, n, size=size).astype(np.int32)
+        reqs.append((kind, q, k))
+    return reqs
+
+
+def run_serve(args, ws, rank, local):
+    """Request loop over the resident graph, paths, index and Panther++ vectors
+    of the scale workload: capacity from a saturating burst, then Poisson
+    arrivals at 0.5 / 0.8 / 0.95 of it (p50 / p99 latency), against the same
+    requests executed one after another, and a check that every checked
+    request returns the same rows alone and in the mix."""
+    import threading
+    import torch
+    import synth
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_02577_gb300 as pk
+
+    torch.cuda.set_device(local)
+    p = dict(synth.WORKLOADS["scale"])
+    if args.n:
+        p["R"] = max(1, p["R"] * args.n // p["n"])
+        p["n"] = args.n
+    g = synth.workload_graph("scale", n=p["n"])
+    ctx = pk.panther_create(local)
+    gh = pk.panther_build_graph(ctx, g.n, g.m, g.row_ptr, g.col, g.w, pk.MEM_HOST, pk.MODE_ALIAS)
+    ph = pk.panther_sample_paths(ctx, gh, 1, p["R"], p["T"], pk.MODE_ALIAS)
+    ih = pk.panther_build_index(ctx, ph)
+    vh = pk.pantherpp_vectors(ctx, ih, ph, 50)
+    pk.panther_free_graph(gh)
+    pk.panther_sync(ctx)
+    rng = np.random.default_rng(1)
+
+    def outputs(req):
+        kind, q, k = req
+        return (np.empty((q.shape[0], k), np.int32),
+                np.empty((q.shape[0], k), np.uint32 if kind == 0 else np.uint64))
+
+    def alone(req, plain=False):
+        kind, q, k = req
+        ids, vals = outputs(req)
+        if kind == 0:
+            flag = pk.TOPK_PLAIN if plain else pk.TOPK_BATCHED
+            pk.panther_topk(ctx, ih, ph, q, q.shape[0], k, ids, vals, flag | pk.IO_HOST)
+        else:
+            pk.pantherpp_knn(ctx, vh, q, q.shape[0], k, ids, vals, pk.KNN_BF16_SCREEN | pk.IO_HOST)
+        return ids, vals
+
+    # serial plain execution of the same kind of stream (one request after another)
+    serial = _requests(g.n, 60, rng)
+    alone(serial[0], plain=True)
+    t0 = time.perf_counter()
+    nq_serial = 0
+    for r in serial:
+        alone(r, plain=True)
+        nq_serial += r[1].shape[0]
+    serial_qps = nq_serial / (time.perf_counter() - t0)
+
+    srv = pk.panther_serve_create(local, ih, ph, vh, 8 << 30, 4096, 4)
+
+    def run_stream(reqs, rate):
+        """Submit with exponential inter-arrival times (rate = requests/s; 0 = all at once)."""
+        outs = [outputs(r) for r in reqs]
+        tickets = [None] * len(reqs)
+        lat = [None] * len(reqs)
+        done = threading.Event()
+
+        def waiter():
+            for i in range(len(reqs)):
+                while tickets[i] is None:
+                    time.sleep(0.0002)
+                lat[i] = pk.panther_serve_wait(srv, tickets[i], 600.0)
+            done.set()
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        t_start = time.perf_counter()
+        t_next = t_start
+        arr = np.random.default_rng(7)
+        for i, (kind, q, k) in enumerate(reqs):
+            if rate > 0:
+                t_next += arr.exponential(1.0 / rate)
+                while time.perf_counter() < t_next:
+                    time.sleep(0.0001)
+            while True:
+                try:
+                    tickets[i] = pk.panther_serve_submit(srv, kind, q, k, outs[i][0], outs[i][1])
+                    break
+                except pk.PantherError:
+                    time.sleep(0.0005)   # full: retry (admission by budget and slots)
+        done.wait()
+        th.join()
+        wall = time.perf_counter() - t_start
+        nq = sum(r[1].shape[0] for r in reqs)
+        return outs, np.array(lat), wall, nq
+
+    burst = _requests(g.n, 300, rng)
+    _, lat_b, wall_b, nq_b = run_stream(burst, 0)
+    cap_rps = len(burst) / wall_b
+    levels = {}
+    check = None
+    for frac in (0.5, 0.8, 0.95):
+        reqs = _requests(g.n, 400, rng)
+        outs, lat, wall, nq = run_stream(reqs, frac * cap_rps)
+        kinds = np.array([r[0] for r in reqs])
+        levels[str(frac)] = {"offered_rps": round(frac * cap_rps, 1), "achieved_rps": round(len(reqs) / wall, 1),
+                             "queries_per_s": round(nq / wall, 1), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                             "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                             "topk_p50_ms": round(float(np.percentile(lat[kinds == 0], 50)), 3),
+                             "topk_p99_ms": round(float(np.percentile(lat[kinds == 0], 99)), 3),
+                             "knn_p50_ms": round(float(np.percentile(lat[kinds == 1], 50)), 3),
+                             "knn_p99_ms": round(float(np.percentile(lat[kinds == 1], 99)), 3)}
+        check = (reqs, outs)
+    st = pk.panther_serve_stats(srv)
+    pk.panther_serve_destroy(srv)
+    # identity: each of a sample of requests equals the same request alone
+    reqs, outs = check
+    same = True
+    for i in range(0, len(reqs), 20):
+        a_ids, a_vals = alone(reqs[i])
+        same &= bool(np.array_equal(a_ids, outs[i][0]) and np.array_equal(a_vals, outs[i][1]))
+    pk.pantherpp_free_vecs(vh)
+    pk.panther_free_index(ih)
+    pk.panther_free_paths(ph)
+    pk.panther_destroy(ctx)
+    top = levels["0.95"]
+    return {
+        "metric": METRIC, "value": top["queries_per_s"], "unit": "queries/s (served, 0.95 load)", "n_gpus": ws,
+        "steps": len(burst), "warmup": 0, "ms_per_step": round(1e3 * wall_b / len(burst), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/u64 (integer counts)",
+        "data": "synthetic",
+        "config": {"workload": "serve", "graph": f"Chung-Lu n={g.n} m={g.m} (scale workload)", "R": p["R"],
+                   "mix": "75% top-k k in {5,10,50} 1-4096 vertices log-uniform, 25% k-NN k=10 1-1024 vertices",
+                   "streams": 4, "mem_budget_gib": 8},
+        "capacity_rps": round(cap_rps, 1), "burst_p50_ms": round(float(np.percentile(lat_b, 50)), 3),
+        "burst_p99_ms": round(float(np.percentile(lat_b, 99)), 3), "poisson": levels,
+        "serial_plain_queries_per_s": round(serial_qps, 1),
+        "speedup_vs_serial": round(top["queries_per_s"] / serial_qps, 2),
+        "identical_alone_and_mixed": same,
+        "server_stats": {"submitted": st[0], "completed": st[1], "batches": st[2], "max_requests_per_batch": st[3],
+                         "max_batches_in_flight": st[4], "refused": st[5]},
+    }
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="scale", choices=["scale", "batched", "small", "knn"])
+    ap.add_argument("--workload", default="scale", choices=["scale", "batched", "small", "knn", "serve"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and batched-vs-plain")
     ap.add_argument("--n", type=int, default=None,
@@ -555,7 +710,12 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
-    out = run_knn(args, ws, rank, local) if args.workload == "knn" else run_ours(args, ws, rank, local)
+    if args.workload == "knn":
+        out = run_knn(args, ws, rank, local)
+    elif args.workload == "serve":
+        out = run_serve(args, ws, rank, local)
+    else:
+        out = run_ours(args, ws, rank, local)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:

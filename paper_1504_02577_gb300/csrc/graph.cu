@@ -17,13 +17,18 @@
 //                j* = min{ j : D_j > E_i } and alias = L_(i+1);
 //                otherwise thr = S and alias = itself.
 //   D = inclusive prefix of deficits, E = inclusive prefix of excesses.
+//
+// Rows of degree <= 16 take one thread (the sequential construction), rows up
+// to BIG_DEG one warp, and longer rows are cut into segments of SEG entries
+// spread over CTAs, with a per-row scan of the segment sums in between.
 #include <algorithm>
+#include <vector>
 
 #include "internal.cuh"
 
 namespace {
 
-constexpr int64_t BIG_DEG = 2048;   // rows above this go to one CTA each
+constexpr int64_t BIG_DEG = 2048;   // rows above this are split into segments
 constexpr int BLK = 512;            // threads of the CTA-per-row kernels
 
 // ------------------------------------------------------------ groups ---
@@ -48,11 +53,10 @@ struct WarpG {
         return v;
     }
     __device__ __forceinline__ bool any(bool p) const { return __any_sync(0xffffffffu, p); }
-    // exclusive scan of the chunk (thread r holds item r); returns the chunk total
+    // inclusive scan of the chunk (thread r holds item r); returns the chunk total
     __device__ __forceinline__ uint64_t chunk_scan(uint64_t (&v)[IPT]) const {
         uint64_t tot;
-        uint64_t inc = incl_scan(v[0], &tot);
-        v[0] = inc - v[0];
+        v[0] = incl_scan(v[0], &tot);
         return tot;
     }
 };
@@ -93,21 +97,21 @@ struct BlockG {
         return t;
     }
     __device__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
-    // exclusive scan of the chunk in blocked order (thread r holds items
+    // inclusive scan of the chunk in blocked order (thread r holds items
     // r*IPT .. r*IPT+IPT-1): a sequential scan per thread, one block scan of
     // the thread totals; returns the chunk total
-    __device__ uint64_t chunk_scan(uint64_t (&v)[IPT]) const {
+    template <int N>
+    __device__ uint64_t chunk_scan(uint64_t (&v)[N]) const {
         uint64_t run = 0;
 #pragma unroll
-        for (int j = 0; j < IPT; ++j) {
-            uint64_t x = v[j];
+        for (int j = 0; j < N; ++j) {
+            run += v[j];
             v[j] = run;
-            run += x;
         }
         uint64_t tot;
         uint64_t before = incl_scan(run, &tot) - run;
 #pragma unroll
-        for (int j = 0; j < IPT; ++j) v[j] += before;
+        for (int j = 0; j < N; ++j) v[j] += before;
         return tot;
     }
 };
@@ -234,6 +238,78 @@ __global__ void __launch_bounds__(256) stats_thread_kernel(const int64_t* __rest
     }
 }
 
+// ------------------------------------------------ rows above BIG_DEG ---
+// Their work is split into segments of SEG entries (one CTA of BLK threads,
+// SEG_IPT consecutive entries per thread): the plan seg_off[i] ..
+// seg_off[i+1] holds the segments of big row i.
+constexpr int SEG_IPT = 8;
+constexpr int64_t SEG = (int64_t)BLK * SEG_IPT;
+
+__device__ __forceinline__ int64_t seg_owner(const int64_t* seg_off, int64_t nbig, int64_t item) {
+    int64_t lo = 0, hi = nbig - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (seg_off[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void big_deg_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ big, int64_t nbig,
+                               int64_t* __restrict__ deg) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nbig) deg[i] = row_ptr[big[i] + 1] - row_ptr[big[i]];
+}
+
+__global__ void stats_seg_kernel(const int64_t* __restrict__ row_ptr, int64_t n, const int32_t* __restrict__ col,
+                                 const uint32_t* __restrict__ w, const int32_t* __restrict__ big,
+                                 const int64_t* __restrict__ seg_off, int64_t nbig,
+                                 unsigned long long* __restrict__ bigS, StatsOut o) {
+    __shared__ uint64_t sh[BLK / 32 + 1];
+    BlockG g{sh};
+    const int64_t i = seg_owner(seg_off, nbig, blockIdx.x);
+    const int64_t v = big[i];
+    const int64_t start = row_ptr[v], end = row_ptr[v + 1];
+    const int64_t a = start + (blockIdx.x - seg_off[i]) * SEG;
+    const int64_t b = a + SEG < end ? a + SEG : end;
+    uint64_t sum = 0, a1 = 0, a2 = 0;
+    bool bad = false;
+    for (int64_t e = a + threadIdx.x; e < b; e += BLK) {
+        int32_t u = col[e];
+        uint32_t ww = w[e];
+        bad |= (u < 0) || ((int64_t)u >= n) || ((int64_t)u == v) || (ww == 0) || (e > start && col[e - 1] >= u);
+        sum += ww;
+        if (u >= 0) {
+            a1 += edge_hash((uint64_t)v, (uint64_t)u, ww);
+            a2 += edge_hash((uint64_t)u, (uint64_t)v, ww);
+        }
+    }
+    sum = g.sum(sum);
+    a1 = g.sum(a1);
+    a2 = g.sum(a2);
+    bad = g.any(bad);
+    if (threadIdx.x == 0) {
+        atomicAdd(bigS + i, (unsigned long long)sum);
+        atomicAdd(o.acc + 1, (unsigned long long)a1);
+        atomicAdd(o.acc + 2, (unsigned long long)a2);
+        if (bad) {
+            flag_status(o.status, ST_GRAPH_BAD);
+            atomicMin(o.status + 1, (uint32_t)v);
+        }
+    }
+}
+
+__global__ void big_finalize_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ big, int64_t nbig,
+                                    const unsigned long long* __restrict__ bigS, StatsOut o) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nbig) return;
+    const int64_t v = big[i];
+    const uint64_t start = (uint64_t)row_ptr[v], deg = (uint64_t)(row_ptr[v + 1] - row_ptr[v]);
+    const uint64_t S = bigS[i];
+    o.vrec[v] = make_uint4((uint32_t)start, (uint32_t)deg, (uint32_t)S, (uint32_t)(S >> 32));
+    if (__umul64hi(S, deg) != 0 || S * deg >= (1ull << 63)) flag_status(o.status, ST_OVERFLOW);
+    atomicMax(o.acc + 0, (unsigned long long)S);
+}
+
 __global__ void stats_warp_kernel(const int64_t* __restrict__ row_ptr, int64_t n, const int32_t* __restrict__ col,
                                   const uint32_t* __restrict__ w, StatsOut o) {
     WarpG g;
@@ -246,20 +322,6 @@ __global__ void stats_warp_kernel(const int64_t* __restrict__ row_ptr, int64_t n
         row_stats(g, v, a, b - a, n, col, w, o, h1, h2, mx);
     }
     if (g.rank() == 0) {
-        atomicMax(o.acc + 0, (unsigned long long)mx);
-        atomicAdd(o.acc + 1, (unsigned long long)h1);
-        atomicAdd(o.acc + 2, (unsigned long long)h2);
-    }
-}
-
-__global__ void stats_block_kernel(const int64_t* __restrict__ row_ptr, int64_t n, const int32_t* __restrict__ col,
-                                   const uint32_t* __restrict__ w, const int32_t* __restrict__ big, StatsOut o) {
-    __shared__ uint64_t sh[BLK / 32 + 1];
-    BlockG g{sh};
-    int64_t v = big[blockIdx.x];
-    uint64_t h1 = 0, h2 = 0, mx = 0;
-    row_stats(g, v, row_ptr[v], row_ptr[v + 1] - row_ptr[v], n, col, w, o, h1, h2, mx);
-    if (threadIdx.x == 0) {
         atomicMax(o.acc + 0, (unsigned long long)mx);
         atomicAdd(o.acc + 1, (unsigned long long)h1);
         atomicAdd(o.acc + 2, (unsigned long long)h2);
@@ -284,7 +346,7 @@ __device__ void row_prefix(const G& g, int64_t start, int64_t deg, const int32_t
         for (int j = 0; j < IPT; ++j) {
             int64_t i = base + (int64_t)g.rank() * IPT + j;
             if (i < deg) {
-                uint64_t inc = carry + v[j] + w[start + i];
+                uint64_t inc = carry + v[j];
                 if (WIDE)
                     ((uint4*)tab)[start + i] =
                         make_uint4((uint32_t)inc, (uint32_t)(inc >> 32), (uint32_t)col[start + i], 0u);
@@ -359,13 +421,13 @@ __device__ int64_t row_alias_prep(const G& g, int64_t start, int64_t deg, uint64
             int64_t i = base + (int64_t)g.rank() * IPT + j;
             f[j] = (i < deg && (uint64_t)w[start + i] * d < S) ? 1 : 0;
         }
-        uint64_t ts = g.chunk_scan(f);   // f = smalls before each item within the chunk
+        uint64_t ts = g.chunk_scan(f);   // f = smalls up to and including each item within the chunk
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
             int64_t i = base + (int64_t)g.rank() * IPT + j;
             if (i < deg) {
                 bool sm = (uint64_t)w[start + i] * d < S;
-                int64_t rs = (int64_t)(cs + f[j]);      // smalls before i
+                int64_t rs = (int64_t)(cs + f[j]) - (sm ? 1 : 0);   // smalls before i
                 int64_t rl = i - rs;                     // larges before i
                 if (sm) sidx[start + nsm - 1 - rs] = (int32_t)i;
                 else sidx[start + nsm + nl - 1 - rl] = (int32_t)i;
@@ -387,14 +449,11 @@ __device__ int64_t row_alias_prep(const G& g, int64_t start, int64_t deg, uint64
                 uint64_t q = p < cnt ? (uint64_t)w[start + sidx[start + o0 + p]] * d : 0;
                 x[j] = p < cnt ? (part == 0 ? S - q : q - S) : 0;
             }
-            uint64_t y[IPT];
-#pragma unroll
-            for (int j = 0; j < IPT; ++j) y[j] = x[j];
-            uint64_t tot = g.chunk_scan(y);
+            uint64_t tot = g.chunk_scan(x);   // inclusive
 #pragma unroll
             for (int j = 0; j < IPT; ++j) {
                 int64_t p = base + (int64_t)g.rank() * IPT + j;
-                if (p < cnt) scum[start + o0 + p] = carry + y[j] + x[j];
+                if (p < cnt) scum[start + o0 + p] = carry + x[j];
             }
             carry += tot;
         }
@@ -519,26 +578,156 @@ __global__ void alias_warp_kernel(const uint4* __restrict__ vrec, int64_t n, con
     }
 }
 
-__global__ void alias_block_kernel(const uint4* __restrict__ vrec, const int32_t* __restrict__ col,
-                                   const uint32_t* __restrict__ w, const int32_t* __restrict__ big, uint4* tab,
-                                   int32_t* sidx, uint64_t* scum, int64_t* bign) {
-    __shared__ uint64_t sh[BLK / 32 + 1];
-    BlockG g{sh};
-    uint4 r = vrec[big[blockIdx.x]];
-    int64_t nsm = row_alias_prep(g, (int64_t)r.x, (int64_t)r.y, (uint64_t)r.z | ((uint64_t)r.w << 32), w, sidx, scum);
-    if (threadIdx.x == 0) bign[blockIdx.x] = nsm;
+// Passes A-C for the rows above BIG_DEG, split over segments. In pop order
+// (descending index) the smalls come first, so the small at index i has pop
+// position nsm-1-rs(i) (rs = smalls before i) and its inclusive prefix of
+// deficits D is the sum over the smalls at index >= i: a suffix sum in index
+// order. Likewise for the larges and E. Each segment therefore needs only the
+// smalls before it and the deficit / excess sums after it within its row.
+struct SegRow {
+    int64_t row, start, deg, a, b;   // entries a .. b-1 of the row's deg
+    uint64_t S;
+};
+
+__device__ __forceinline__ SegRow seg_row(const uint4* vrec, const int32_t* big, const int64_t* seg_off,
+                                          int64_t nbig) {
+    SegRow r;
+    r.row = seg_owner(seg_off, nbig, blockIdx.x);
+    const uint4 v = vrec[big[r.row]];
+    r.start = (int64_t)v.x;
+    r.deg = (int64_t)v.y;
+    r.S = (uint64_t)v.z | ((uint64_t)v.w << 32);
+    r.a = (blockIdx.x - seg_off[r.row]) * SEG;
+    r.b = r.a + SEG < r.deg ? r.a + SEG : r.deg;
+    return r;
 }
 
-// pass D for the rows above BIG_DEG: ASSIGN_SPLIT CTAs per row
-constexpr int ASSIGN_SPLIT = 32;
+// per segment: smalls, sum of deficits S - q, sum of excesses q - S
+__global__ void __launch_bounds__(BLK) big_count_kernel(const uint4* __restrict__ vrec, const uint32_t* __restrict__ w,
+                                                        const int32_t* __restrict__ big,
+                                                        const int64_t* __restrict__ seg_off, int64_t nbig,
+                                                        uint64_t* __restrict__ segsum) {
+    __shared__ uint64_t sh[BLK / 32 + 1];
+    BlockG g{sh};
+    const SegRow r = seg_row(vrec, big, seg_off, nbig);
+    const uint64_t d = (uint64_t)r.deg;
+    uint64_t ns = 0, df = 0, ex = 0;
+    for (int64_t i = r.a + threadIdx.x; i < r.b; i += BLK) {
+        const uint64_t q = (uint64_t)w[r.start + i] * d;
+        if (q < r.S) {
+            ++ns;
+            df += r.S - q;
+        } else {
+            ex += q - r.S;
+        }
+    }
+    ns = g.sum(ns);
+    df = g.sum(df);
+    ex = g.sum(ex);
+    if (threadIdx.x == 0) {
+        segsum[3 * blockIdx.x + 0] = ns;
+        segsum[3 * blockIdx.x + 1] = df;
+        segsum[3 * blockIdx.x + 2] = ex;
+    }
+}
+
+// one warp per big row: smalls before each segment, deficit and excess sums
+// after it (in place over segsum), and the row's small count
+__global__ void big_rowscan_kernel(const int64_t* __restrict__ seg_off, int64_t nbig, uint64_t* __restrict__ segsum,
+                                   int64_t* __restrict__ bign) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= nbig) return;
+    WarpG g;
+    const int64_t s0 = seg_off[row], s1 = seg_off[row + 1];
+    uint64_t tdf = 0, tex = 0;
+    for (int64_t sg = s0 + lane; sg < s1; sg += 32) {
+        tdf += segsum[3 * sg + 1];
+        tex += segsum[3 * sg + 2];
+    }
+    tdf = g.sum(tdf);
+    tex = g.sum(tex);
+    uint64_t cns = 0, cdf = 0, cex = 0;
+    for (int64_t base = s0; base < s1; base += 32) {
+        const int64_t sg = base + lane;
+        const bool ok = sg < s1;
+        const uint64_t ns = ok ? segsum[3 * sg + 0] : 0, df = ok ? segsum[3 * sg + 1] : 0,
+                       ex = ok ? segsum[3 * sg + 2] : 0;
+        uint64_t t_ns, t_df, t_ex;
+        const uint64_t i_ns = g.incl_scan(ns, &t_ns), i_df = g.incl_scan(df, &t_df), i_ex = g.incl_scan(ex, &t_ex);
+        if (ok) {
+            segsum[3 * sg + 0] = cns + i_ns - ns;
+            segsum[3 * sg + 1] = tdf - (cdf + i_df);
+            segsum[3 * sg + 2] = tex - (cex + i_ex);
+        }
+        cns += t_ns;
+        cdf += t_df;
+        cex += t_ex;
+    }
+    if (lane == 0) bign[row] = (int64_t)cns;
+}
+
+// pop-order positions (sidx) and inclusive prefixes D / E (scum) of a segment
+__global__ void __launch_bounds__(BLK) big_place_kernel(const uint4* __restrict__ vrec, const uint32_t* __restrict__ w,
+                                                        const int32_t* __restrict__ big,
+                                                        const int64_t* __restrict__ seg_off, int64_t nbig,
+                                                        const uint64_t* __restrict__ segsum,
+                                                        const int64_t* __restrict__ bign, int32_t* __restrict__ sidx,
+                                                        uint64_t* __restrict__ scum) {
+    __shared__ uint64_t sh[BLK / 32 + 1];
+    BlockG g{sh};
+    const SegRow r = seg_row(vrec, big, seg_off, nbig);
+    const uint64_t d = (uint64_t)r.deg;
+    const uint64_t ns_before = segsum[3 * blockIdx.x + 0], df_after = segsum[3 * blockIdx.x + 1],
+                   ex_after = segsum[3 * blockIdx.x + 2];
+    const int64_t nsm = bign[r.row];
+    const int64_t i0 = r.a + (int64_t)threadIdx.x * SEG_IPT;
+    uint64_t q[SEG_IPT], x[SEG_IPT];   // q = S marks an entry past the segment (in neither class)
+    int32_t pos[SEG_IPT];
+#pragma unroll
+    for (int j = 0; j < SEG_IPT; ++j) {
+        q[j] = i0 + j < r.b ? (uint64_t)w[r.start + i0 + j] * d : r.S;
+        x[j] = q[j] < r.S ? 1 : 0;
+    }
+    g.chunk_scan(x);   // smalls up to and including each entry within the segment
+#pragma unroll
+    for (int j = 0; j < SEG_IPT; ++j) {
+        const int64_t i = i0 + j;
+        const int64_t rs = (int64_t)(ns_before + x[j]) - (q[j] < r.S ? 1 : 0);   // smalls before i
+        pos[j] = q[j] < r.S ? (int32_t)(nsm - 1 - rs) : (int32_t)(r.deg - 1 - (i - rs));
+    }
+    // deficits, then excesses: suffix within the segment = total - inclusive prefix + own
+#pragma unroll
+    for (int j = 0; j < SEG_IPT; ++j) x[j] = q[j] < r.S ? r.S - q[j] : 0;
+    uint64_t tot = g.chunk_scan(x);
+#pragma unroll
+    for (int j = 0; j < SEG_IPT; ++j)
+        if (q[j] < r.S) {
+            sidx[r.start + pos[j]] = (int32_t)(i0 + j);
+            scum[r.start + pos[j]] = df_after + (tot - x[j]) + (r.S - q[j]);
+        }
+#pragma unroll
+    for (int j = 0; j < SEG_IPT; ++j) x[j] = (q[j] >= r.S && i0 + j < r.b) ? q[j] - r.S : 0;
+    tot = g.chunk_scan(x);
+#pragma unroll
+    for (int j = 0; j < SEG_IPT; ++j)
+        if (q[j] >= r.S && i0 + j < r.b) {
+            sidx[r.start + pos[j]] = (int32_t)(i0 + j);
+            scum[r.start + pos[j]] = ex_after + (tot - x[j]) + (q[j] - r.S);
+        }
+}
+
+// pass D for the rows above BIG_DEG: one CTA per segment of the row
 __global__ void alias_assign_kernel(const uint4* __restrict__ vrec, const int32_t* __restrict__ col,
                                     const uint32_t* __restrict__ w, const int32_t* __restrict__ big,
-                                    const int64_t* __restrict__ bign, uint4* tab, const int32_t* __restrict__ sidx,
+                                    const int64_t* __restrict__ bign, const int64_t* __restrict__ seg_off,
+                                    int64_t nbig, uint4* tab, const int32_t* __restrict__ sidx,
                                     const uint64_t* __restrict__ scum) {
-    const int64_t row = blockIdx.x / ASSIGN_SPLIT, part = blockIdx.x % ASSIGN_SPLIT;
+    const int64_t row = seg_owner(seg_off, nbig, blockIdx.x);
+    const int64_t parts = seg_off[row + 1] - seg_off[row], part = blockIdx.x - seg_off[row];
     uint4 r = vrec[big[row]];
     alias_assign((int64_t)r.x, (int64_t)r.y, (uint64_t)r.z | ((uint64_t)r.w << 32), bign[row], col, w, tab, sidx,
-                 scum, part * blockDim.x + threadIdx.x, (int64_t)ASSIGN_SPLIT * blockDim.x);
+                 scum, part * blockDim.x + threadIdx.x, parts * blockDim.x);
 }
 
 unsigned grid_for(panther_ctx* ctx, int64_t items_per_block_unit, int64_t n, int threads) {
@@ -628,6 +817,38 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
         return fail(cuda_err(ctx, e, "row check"));
     if (h_st[0]) return fail(set_err(ctx, PANTHER_EINVAL, "row_ptr is not a valid CSR offset array"));
 
+    // segment plan of the rows above BIG_DEG
+    int64_t* bdeg = nullptr;
+    int64_t* seg_off = nullptr;
+    unsigned long long* bigS = nullptr;
+    int64_t nseg = 0;
+    std::vector<int64_t> hseg(1, 0);
+    if (h_nbig) {
+        std::vector<int64_t> hdeg(h_nbig);
+        if ((st = dev_alloc(ctx, (void**)&bdeg, sizeof(int64_t) * h_nbig)) ||
+            (st = dev_alloc(ctx, (void**)&seg_off, sizeof(int64_t) * (h_nbig + 1))) ||
+            (st = dev_alloc(ctx, (void**)&bigS, sizeof(unsigned long long) * h_nbig)))
+            return fail(st);
+        big_deg_kernel<<<(unsigned)ceil_div(h_nbig, 256), 256, 0, s>>>(d_rp, big, h_nbig, bdeg);
+        ctx->launches++;
+        if ((e = cudaMemcpyAsync(hdeg.data(), bdeg, sizeof(int64_t) * h_nbig, cudaMemcpyDeviceToHost, s)) ||
+            (e = cudaStreamSynchronize(s)))
+            return fail(cuda_err(ctx, e, "big-row plan"));
+        hseg.resize(h_nbig + 1);
+        for (int i = 0; i < h_nbig; ++i) hseg[i + 1] = hseg[i] + ceil_div(hdeg[i], SEG);
+        nseg = hseg[h_nbig];
+        if ((e = cudaMemcpyAsync(seg_off, hseg.data(), sizeof(int64_t) * (h_nbig + 1), cudaMemcpyHostToDevice, s)) ||
+            (e = cudaMemsetAsync(bigS, 0, sizeof(unsigned long long) * h_nbig, s)))
+            return fail(cuda_err(ctx, e, "big-row plan"));
+    }
+    auto free_plan = [&]() {
+        dev_free(ctx, bdeg);
+        dev_free(ctx, seg_off);
+        dev_free(ctx, bigS);
+        bdeg = nullptr;
+        seg_off = nullptr;
+        bigS = nullptr;
+    };
     StatsOut so{g->vrec, ctx->d_status, acc};
     unsigned gw = grid_for(ctx, 64, n, 256);
     stats_thread_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->num_sms * 16), 256, 0, s>>>(
@@ -635,31 +856,32 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
     stats_warp_kernel<<<gw, 256, 0, s>>>(d_rp, n, d_col, d_w, so);
     ctx->launches += 2;
     if (h_nbig) {
-        stats_block_kernel<<<h_nbig, BLK, 0, s>>>(d_rp, n, d_col, d_w, big, so);
-        ctx->launches++;
+        stats_seg_kernel<<<(unsigned)nseg, BLK, 0, s>>>(d_rp, n, d_col, d_w, big, seg_off, h_nbig, bigS, so);
+        big_finalize_kernel<<<(unsigned)ceil_div(h_nbig, 256), 256, 0, s>>>(d_rp, big, h_nbig, bigS, so);
+        ctx->launches += 2;
     }
     unsigned long long h_acc[3];
     if ((e = cudaMemcpyAsync(h_acc, acc, sizeof(h_acc), cudaMemcpyDeviceToHost, s)) ||
         (e = cudaMemcpyAsync(h_st, ctx->d_status, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) ||
         (e = cudaStreamSynchronize(s)))
-        return fail(cuda_err(ctx, e, "graph validation"));
+        return free_plan(), fail(cuda_err(ctx, e, "graph validation"));
     if (h_st[0] & ST_OVERFLOW) {
         cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s);
-        return fail(set_err(ctx, PANTHER_EOVERFLOW, "a row's weight sum times its degree reaches 2^63"));
+        return free_plan(), fail(set_err(ctx, PANTHER_EOVERFLOW, "a row's weight sum times its degree reaches 2^63"));
     }
     if (h_st[0]) {
         cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s);
-        return fail(set_err(ctx, PANTHER_EINVAL,
+        return free_plan(), fail(set_err(ctx, PANTHER_EINVAL,
                             "malformed graph at row %u (column range, order, self-loop or zero weight)", h_st[1]));
     }
     if (h_acc[1] != h_acc[2])
-        return fail(set_err(ctx, PANTHER_EINVAL, "graph is not symmetric with equal weights"));
+        return free_plan(), fail(set_err(ctx, PANTHER_EINVAL, "graph is not symmetric with equal weights"));
     g->max_row_sum = h_acc[0];
     g->prefix_wide = h_acc[0] >= (1ull << 32) ? 1 : 0;
 
     if (modes & PANTHER_MODE_PREFIX) {
         size_t esz = g->prefix_wide ? sizeof(uint4) : sizeof(uint2);
-        if ((st = dev_alloc(ctx, &g->prefix, esz * (size_t)m))) return fail(st);
+        if ((st = dev_alloc(ctx, &g->prefix, esz * (size_t)m))) return free_plan(), fail(st);
         if (g->prefix_wide) {
             prefix_warp_kernel<true><<<gw, 256, 0, s>>>(d_rp, n, d_col, d_w, g->prefix);
             if (h_nbig) prefix_block_kernel<true><<<h_nbig, BLK, 0, s>>>(d_rp, d_col, d_w, big, g->prefix);
@@ -668,7 +890,7 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
             if (h_nbig) prefix_block_kernel<false><<<h_nbig, BLK, 0, s>>>(d_rp, d_col, d_w, big, g->prefix);
         }
         ctx->launches += h_nbig ? 2 : 1;
-        if ((e = cudaGetLastError())) return fail(cuda_err(ctx, e, "prefix table"));
+        if ((e = cudaGetLastError())) return free_plan(), fail(cuda_err(ctx, e, "prefix table"));
     }
     if (modes & PANTHER_MODE_ALIAS) {
         int32_t* sidx = nullptr;
@@ -677,7 +899,7 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
             (st = dev_alloc(ctx, (void**)&sidx, sizeof(int32_t) * m)) ||
             (st = dev_alloc(ctx, (void**)&scum, sizeof(uint64_t) * m))) {
             dev_free(ctx, sidx);
-            return fail(st);
+            return free_plan(), fail(st);
         }
         alias_thread_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->num_sms * 16), 256, 0, s>>>(
             g->vrec, n, d_col, d_w, g->alias);
@@ -688,19 +910,31 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
             if ((st = dev_alloc(ctx, (void**)&bign, sizeof(int64_t) * h_nbig))) {
                 dev_free(ctx, sidx);
                 dev_free(ctx, scum);
-                return fail(st);
+                return free_plan(), fail(st);
             }
-            alias_block_kernel<<<h_nbig, BLK, 0, s>>>(g->vrec, d_col, d_w, big, g->alias, sidx, scum, bign);
-            alias_assign_kernel<<<(unsigned)(h_nbig * ASSIGN_SPLIT), 256, 0, s>>>(g->vrec, d_col, d_w, big, bign,
-                                                                               g->alias, sidx, scum);
-            ctx->launches += 2;
+            uint64_t* segsum = nullptr;
+            if ((st = dev_alloc(ctx, (void**)&segsum, sizeof(uint64_t) * 3 * nseg))) {
+                dev_free(ctx, bign);
+                dev_free(ctx, sidx);
+                dev_free(ctx, scum);
+                return free_plan(), fail(st);
+            }
+            big_count_kernel<<<(unsigned)nseg, BLK, 0, s>>>(g->vrec, d_w, big, seg_off, h_nbig, segsum);
+            big_rowscan_kernel<<<(unsigned)ceil_div(h_nbig * 32, 256), 256, 0, s>>>(seg_off, h_nbig, segsum, bign);
+            big_place_kernel<<<(unsigned)nseg, BLK, 0, s>>>(g->vrec, d_w, big, seg_off, h_nbig, segsum, bign, sidx,
+                                                            scum);
+            alias_assign_kernel<<<(unsigned)nseg, 256, 0, s>>>(g->vrec, d_col, d_w, big, bign, seg_off, h_nbig,
+                                                               g->alias, sidx, scum);
+            ctx->launches += 4;
+            dev_free(ctx, segsum);
             dev_free(ctx, bign);
         }
         e = cudaGetLastError();
         dev_free(ctx, sidx);
         dev_free(ctx, scum);
-        if (e) return fail(cuda_err(ctx, e, "alias table"));
+        if (e) return free_plan(), fail(cuda_err(ctx, e, "alias table"));
     }
+    free_plan();
     dev_free(ctx, t_rp);
     dev_free(ctx, t_col);
     dev_free(ctx, t_w);

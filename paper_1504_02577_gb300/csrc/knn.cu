@@ -372,10 +372,11 @@ struct ScreenArgs {
     const uint8_t* qexact;   // [qpad]
     const uint8_t* qtile;    // [qpad/128] all-exact flags
     int64_t nqt;
+    int64_t nchunk;          // candidate ranges per query tile (work item = tile x range)
     int k;
-    float2* lists;           // [qpad][k]
-    int32_t* shortlist;      // [qpad][KN_SCAP]
-    int32_t* scount;         // [qpad]
+    float2* lists;           // [qpad][nchunk][KN_SPLIT][k]
+    int32_t* shortlist;      // [qpad][nchunk][KN_SPLIT][KN_SCAP]
+    int32_t* scount;         // [qpad][nchunk][KN_SPLIT]
     int* overflow;           // [qpad]
     uint32_t* status;
 };
@@ -434,12 +435,14 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
         if (lane == 0) {
             int64_t it = 0;
             int j = 0;
-            for (int64_t qt = blockIdx.x; qt < S.nqt; qt += gridDim.x, ++j) {
+            for (int64_t wi = blockIdx.x; wi < S.nqt * S.nchunk; wi += gridDim.x, ++j) {
+                const int64_t qt = wi / S.nchunk, ch = wi % S.nchunk;
+                const int64_t ct0 = ch * S.nct / S.nchunk, ct1 = (ch + 1) * S.nct / S.nchunk;
                 if (!mbar_wait(AEMPTY, (j & 1) ^ 1, S.status, abort_flag)) break;
                 mbar_expect_tx(AFULL, KN_M * KN_K * 2);
                 tma_load_2d(base + SM_A, &tmA, 0, (int)(qt * KN_M), AFULL);
                 bool ok = true;
-                for (int64_t ct = 0; ct < S.nct; ++ct, ++it) {
+                for (int64_t ct = ct0; ct < ct1; ++ct, ++it) {
                     int s = (int)(it % KN_STAGES);
                     uint32_t ph = (uint32_t)((it / KN_STAGES) & 1);
                     if (!mbar_wait(EMPTY(s), ph ^ 1, S.status, abort_flag)) { ok = false; break; }
@@ -458,10 +461,12 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
         if (lane == 0) {
             int64_t it = 0;
             int j = 0;
-            for (int64_t qt = blockIdx.x; qt < S.nqt; qt += gridDim.x, ++j) {
+            for (int64_t wi = blockIdx.x; wi < S.nqt * S.nchunk; wi += gridDim.x, ++j) {
+                const int64_t ch = wi % S.nchunk;
+                const int64_t ct0 = ch * S.nct / S.nchunk, ct1 = (ch + 1) * S.nct / S.nchunk;
                 if (!mbar_wait(AFULL, j & 1, S.status, abort_flag)) break;
                 bool ok = true;
-                for (int64_t ct = 0; ct < S.nct; ++ct, ++it) {
+                for (int64_t ct = ct0; ct < ct1; ++ct, ++it) {
                     int s = (int)(it % KN_STAGES);
                     uint32_t ph = (uint32_t)((it / KN_STAGES) & 1);
                     int b = (int)(it & 1);
@@ -490,15 +495,17 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
         const int row = quarter * 32 + lane;
         float2* mylist = (float2*)(gbase + SM_LIST) + (row * KN_SPLIT + half) * KN_KMAX;
         int64_t it = 0;
-        for (int64_t qt = blockIdx.x; qt < S.nqt; qt += gridDim.x) {
+        for (int64_t wi = blockIdx.x; wi < S.nqt * S.nchunk; wi += gridDim.x) {
+            const int64_t qt = wi / S.nchunk, ch = wi % S.nchunk;
+            const int64_t ct0 = ch * S.nct / S.nchunk, ct1 = (ch + 1) * S.nct / S.nchunk;
             const int64_t slot = qt * KN_M + row;
             Row r{__int_as_float(0x7f800000), 0x7fffffff, 0, 0};
-            const int64_t state = slot * KN_SPLIT + half;
+            const int64_t state = (slot * S.nchunk + ch) * KN_SPLIT + half;
             const RowConst rc{S.qv[slot], S.qexact[slot] != 0, KN_ALPHA * S.qnrm[slot], mylist,
                               S.shortlist + state * KN_SCAP, S.overflow + slot, S.k};
             const bool qtile_exact = S.qtile[qt] != 0;
             bool ok = true;
-            for (int64_t ct = 0; ct < S.nct; ++ct, ++it) {
+            for (int64_t ct = ct0; ct < ct1; ++ct, ++it) {
                 int s = (int)(it % KN_STAGES);
                 uint32_t ph = (uint32_t)((it / KN_STAGES) & 1);
                 int b = (int)(it & 1);
@@ -637,24 +644,29 @@ __device__ __forceinline__ bool pair_less(uint64_t d1, int i1, uint64_t d2, int 
     return d1 < d2 || (d1 == d2 && i1 < i2);
 }
 
-// one warp per query slot: exact distances of every kept candidate, top-k
+// One warp per (query slot, candidate range): exact distances of every kept
+// candidate, top-k of the range. With one range per query the rows go to the
+// output; otherwise to part_d2 / part_id ([qpad][nchunk][k]) for chunk_merge.
 __global__ void rerank_kernel(const uint32_t* __restrict__ theta, int D, const int32_t* __restrict__ qv,
-                              const int32_t* __restrict__ qidx, int64_t qpad, int k, const float2* __restrict__ lists,
-                              const int32_t* __restrict__ shortlist, const int32_t* __restrict__ scount,
-                              const int* __restrict__ overflow, int32_t* __restrict__ out_ids,
-                              uint64_t* __restrict__ out_d2) {
-    const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                              const int32_t* __restrict__ qidx, int64_t qpad, int64_t nchunk, int k,
+                              const float2* __restrict__ lists, const int32_t* __restrict__ shortlist,
+                              const int32_t* __restrict__ scount, const int* __restrict__ overflow,
+                              int32_t* __restrict__ out_ids, uint64_t* __restrict__ out_d2,
+                              int32_t* __restrict__ part_id, uint64_t* __restrict__ part_d2) {
+    const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (slot >= qpad) return;
+    if (grp >= qpad * nchunk) return;
+    const int64_t slot = grp / nchunk;
     const int32_t v = qv[slot];
     if (v < 0 || overflow[slot]) return;   // padding, or handled by the brute-force fallback
-    const int64_t qi = qidx[slot];
+    int32_t* oid = nchunk == 1 ? out_ids + (int64_t)qidx[slot] * k : part_id + grp * k;
+    uint64_t* od = nchunk == 1 ? out_d2 + (int64_t)qidx[slot] * k : part_d2 + grp * k;
     // candidates: the lists of the column slices, then their shortlists
     int ns[KN_SPLIT];
     int nst = 0;
 #pragma unroll
     for (int h = 0; h < KN_SPLIT; ++h) {
-        ns[h] = min(scount[slot * KN_SPLIT + h], KN_SCAP);
+        ns[h] = min(scount[grp * KN_SPLIT + h], KN_SCAP);
         nst += ns[h];
     }
     const int nl = KN_SPLIT * k;
@@ -671,11 +683,11 @@ __global__ void rerank_kernel(const uint32_t* __restrict__ theta, int D, const i
         if (i < total) {
             int c;
             if (i < nl) {
-                c = __float_as_int(lists[slot * nl + i].y);
+                c = __float_as_int(lists[grp * nl + i].y);
             } else {
                 int j = i - nl, h = 0;
                 while (h < KN_SPLIT - 1 && j >= ns[h]) j -= ns[h++];
-                c = shortlist[(slot * KN_SPLIT + h) * KN_SCAP + j];
+                c = shortlist[(grp * KN_SPLIT + h) * KN_SCAP + j];
             }
             if (c >= 0) {
                 id[t] = c;
@@ -708,19 +720,82 @@ __global__ void rerank_kernel(const uint32_t* __restrict__ theta, int D, const i
             }
         }
         if (lane == 0) {
-            out_ids[qi * k + r] = bi == 0x7fffffff ? -1 : bi;
-            out_d2[qi * k + r] = bi == 0x7fffffff ? ~0ull : bd;
+            oid[r] = bi == 0x7fffffff ? -1 : bi;
+            od[r] = bi == 0x7fffffff ? ~0ull : bd;
         }
         if (bi == 0x7fffffff) {
             for (int rr = r + 1; rr < k && lane == 0; ++rr) {
-                out_ids[qi * k + rr] = -1;
-                out_d2[qi * k + rr] = ~0ull;
+                oid[rr] = -1;
+                od[rr] = ~0ull;
             }
             break;
         }
         lastd = bd;
         lasti = bi;
         first = false;
+    }
+}
+
+// one CTA per query slot: top-k of the nchunk exact top-k lists of its ranges
+// (the ranges are disjoint, so no candidate appears twice)
+__global__ void __launch_bounds__(256) chunk_merge_kernel(const int32_t* __restrict__ qv,
+                                                          const int32_t* __restrict__ qidx,
+                                                          const int* __restrict__ overflow, int64_t qpad,
+                                                          int64_t nchunk, int k, const int32_t* __restrict__ part_id,
+                                                          const uint64_t* __restrict__ part_d2,
+                                                          int32_t* __restrict__ out_ids,
+                                                          uint64_t* __restrict__ out_d2) {
+    __shared__ uint64_t sd[8];
+    __shared__ int si[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t total = nchunk * k;
+    for (int64_t slot = blockIdx.x; slot < qpad; slot += gridDim.x) {
+        if (qv[slot] < 0 || overflow[slot]) continue;
+        const int64_t qi = qidx[slot], base = slot * total;
+        uint64_t lastd = 0;
+        int lasti = -1;
+        for (int r = 0; r < k; ++r) {
+            uint64_t bd = ~0ull;
+            int bi = 0x7fffffff;
+            for (int64_t t = threadIdx.x; t < total; t += 256) {
+                const int id = part_id[base + t];
+                if (id < 0) continue;
+                const uint64_t d = part_d2[base + t];
+                if ((r == 0 || pair_less(lastd, lasti, d, id)) && pair_less(d, id, bd, bi)) {
+                    bd = d;
+                    bi = id;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                uint64_t od = __shfl_xor_sync(0xffffffffu, bd, o);
+                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (pair_less(od, oi, bd, bi)) {
+                    bd = od;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                sd[warp] = bd;
+                si[warp] = bi;
+            }
+            __syncthreads();
+            bd = sd[0];
+            bi = si[0];
+#pragma unroll
+            for (int w = 1; w < 8; ++w)
+                if (pair_less(sd[w], si[w], bd, bi)) {
+                    bd = sd[w];
+                    bi = si[w];
+                }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                out_ids[qi * k + r] = bi == 0x7fffffff ? -1 : bi;
+                out_d2[qi * k + r] = bi == 0x7fffffff ? ~0ull : bd;
+            }
+            lastd = bd;
+            lasti = bi;
+        }
     }
 }
 
@@ -813,17 +888,17 @@ __global__ void fill_i32(int32_t* p, int64_t n, int32_t v) {
 
 // ---------------------------------------------------------------- host ---
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn(panther_ctx* ctx) {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    // looked up once (thread-safe static initialisation: serving workers race here)
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-        else
-            set_err(ctx, PANTHER_ECUDA, "cuTensorMapEncodeTiled is not available");
-    }
+            return (PFN_cuTensorMapEncodeTiled_v12000)p;
+        return nullptr;
+    }();
+    if (!fn) set_err(ctx, PANTHER_ECUDA, "cuTensorMapEncodeTiled is not available");
     return fn;
 }
 
@@ -924,33 +999,57 @@ extern "C" panther_status pantherpp_vectors(panther_ctx* ctx, const panther_inde
     return PANTHER_OK;
 }
 
+// Candidate ranges per query tile: with fewer query tiles than SMs, the
+// candidate tiles are cut into ranges so that tiles x ranges work items fill
+// the GPU; the choice minimises waves x range length, at least KN_STAGES
+// candidate tiles per range. The FP32 form always takes one range.
+static int64_t knn_ranges(int64_t nqt, int64_t nct, int num_sms, bool fp32) {
+    if (fp32 || nqt >= num_sms) return 1;
+    const int64_t pmax = std::max<int64_t>(1, std::min<int64_t>(nct / KN_STAGES, 256));
+    int64_t best = 1;
+    double best_cost = (double)ceil_div(nqt, num_sms);
+    for (int64_t p = 2; p <= pmax; ++p) {
+        double cost = (double)ceil_div(nqt * p, num_sms) / (double)p;
+        if (cost < best_cost * 0.999) {
+            best = p;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+
 static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* v, const int32_t* queries, int64_t q, int k,
                               int32_t* ids, uint64_t* d2, bool fp32) {
     const pantherpp_vecs& x = *v;
     cudaStream_t s = ctx->stream;
     const int64_t n = v->n;
     const int64_t qpad = ceil_div(q, KN_M) * KN_M;
+    const int64_t nch = knn_ranges(qpad / KN_M, x.npad / KN_N, ctx->num_sms, fp32);
     panther_status st;
     int64_t* qf = nullptr;
-    int32_t *qv = nullptr, *qidx = nullptr, *sl = nullptr, *sc = nullptr;
+    int32_t *qv = nullptr, *qidx = nullptr, *sl = nullptr, *sc = nullptr, *pid = nullptr;
     int* ovf = nullptr;
     uint8_t *qex = nullptr, *qtile = nullptr;
     float* qn = nullptr;
     float2* lists = nullptr;
     uint16_t* A = nullptr;
+    uint64_t* pd = nullptr;
     auto cleanup = [&]() {
         dev_free(ctx, qf); dev_free(ctx, qv); dev_free(ctx, qidx); dev_free(ctx, sl); dev_free(ctx, sc);
         dev_free(ctx, ovf); dev_free(ctx, qex); dev_free(ctx, qtile); dev_free(ctx, qn); dev_free(ctx, lists);
-        dev_free(ctx, A);
+        dev_free(ctx, A); dev_free(ctx, pid); dev_free(ctx, pd);
     };
+    const int64_t nstate = qpad * nch * KN_SPLIT;
     if ((st = dev_alloc(ctx, (void**)&qf, sizeof(int64_t) * q)) ||
         (st = dev_alloc(ctx, (void**)&qv, sizeof(int32_t) * qpad)) ||
         (st = dev_alloc(ctx, (void**)&qidx, sizeof(int32_t) * qpad)) ||
-        (st = dev_alloc(ctx, (void**)&sl, sizeof(int32_t) * qpad * KN_SPLIT * KN_SCAP)) ||
-        (st = dev_alloc(ctx, (void**)&sc, sizeof(int32_t) * qpad * KN_SPLIT)) ||
+        (st = dev_alloc(ctx, (void**)&sl, sizeof(int32_t) * nstate * KN_SCAP)) ||
+        (st = dev_alloc(ctx, (void**)&sc, sizeof(int32_t) * nstate)) ||
         (st = dev_alloc(ctx, (void**)&ovf, sizeof(int) * qpad)) || (st = dev_alloc(ctx, (void**)&qex, qpad)) ||
         (st = dev_alloc(ctx, (void**)&qtile, qpad / KN_M)) || (st = dev_alloc(ctx, (void**)&qn, sizeof(float) * qpad)) ||
-        (st = dev_alloc(ctx, (void**)&lists, sizeof(float2) * qpad * KN_SPLIT * k)) ||
+        (st = dev_alloc(ctx, (void**)&lists, sizeof(float2) * nstate * k)) ||
+        (nch > 1 && ((st = dev_alloc(ctx, (void**)&pid, sizeof(int32_t) * qpad * nch * k)) ||
+                     (st = dev_alloc(ctx, (void**)&pd, sizeof(uint64_t) * qpad * nch * k)))) ||
         (!fp32 && (st = dev_alloc(ctx, (void**)&A, (size_t)qpad * KN_K * 2)))) {
         cleanup();
         return st;
@@ -966,7 +1065,10 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* v, const i
     else lastq = (int32_t)(q - 1);
     PCK(ctx, cudaStreamSynchronize(s));
     uint8_t lastex = 1;
-    if (lastq >= 0 && lastq < n) PCK(ctx, cudaMemcpy(&lastex, v->exact + lastq, 1, cudaMemcpyDeviceToHost));
+    if (lastq >= 0 && lastq < n) {
+        PCK(ctx, cudaMemcpyAsync(&lastex, v->exact + lastq, 1, cudaMemcpyDeviceToHost, s));
+        PCK(ctx, cudaStreamSynchronize(s));
+    }
     const int64_t nexq = last + lastex;
     fill_i32<<<gp, 256, 0, s>>>(qv, qpad, -1);
     fill_i32<<<gp, 256, 0, s>>>(qidx, qpad, 0);
@@ -985,9 +1087,9 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* v, const i
             return PANTHER_ECUDA;
         }
         ScreenArgs S{x.cid, x.cnrm, x.cncf, x.ctile, x.npad / KN_N, x.nexact, qv, qn, qex, qtile, qpad / KN_M,
-                     k, lists, sl, sc, ovf, ctx->d_status};
+                     nch, k, lists, sl, sc, ovf, ctx->d_status};
         PCK(ctx, cudaFuncSetAttribute(screen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KN_SMEM_BYTES));
-        int64_t grid = std::min<int64_t>(qpad / KN_M, ctx->num_sms);
+        int64_t grid = std::min<int64_t>(qpad / KN_M * nch, ctx->num_sms);
         screen_kernel<<<(unsigned)grid, KN_THREADS, KN_SMEM_BYTES, s>>>(tmA, tmB, S);
         ctx->launches++;
     } else {
@@ -996,23 +1098,26 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* v, const i
         ctx->launches++;
     }
     PCK(ctx, cudaGetLastError());
-    rerank_kernel<<<(unsigned)ceil_div(qpad * 32, 256), 256, 0, s>>>(v->theta, v->D, qv, qidx, qpad, k, lists, sl,
-                                                                      sc, ovf, ids, d2);
+    rerank_kernel<<<(unsigned)ceil_div(qpad * nch * 32, 256), 256, 0, s>>>(v->theta, v->D, qv, qidx, qpad, nch, k,
+                                                                            lists, sl, sc, ovf, ids, d2, pid, pd);
+    if (nch > 1) {
+        chunk_merge_kernel<<<(unsigned)std::min<int64_t>(qpad, 8 * ctx->num_sms), 256, 0, s>>>(
+            qv, qidx, ovf, qpad, nch, k, pid, pd, ids, d2);
+        ctx->launches++;
+    }
     brute_kernel<<<(unsigned)std::min<int64_t>(qpad, 4 * ctx->num_sms), 1024, 0, s>>>(v->theta, v->D, n, qv, qidx,
                                                                                        ovf, qpad, k, ids, d2);
     ctx->launches += 2;
     PCK(ctx, cudaGetLastError());
     // screening statistics (pairs screened, kept for rerank, overflowed queries)
-    std::vector<int32_t> hsc(qpad * KN_SPLIT);
+    std::vector<int32_t> hsc(nstate);
     std::vector<int> hov(qpad);
-    PCK(ctx, cudaMemcpyAsync(hsc.data(), sc, sizeof(int32_t) * qpad * KN_SPLIT, cudaMemcpyDeviceToHost, s));
+    PCK(ctx, cudaMemcpyAsync(hsc.data(), sc, sizeof(int32_t) * nstate, cudaMemcpyDeviceToHost, s));
     PCK(ctx, cudaMemcpyAsync(hov.data(), ovf, sizeof(int) * qpad, cudaMemcpyDeviceToHost, s));
     PCK(ctx, cudaStreamSynchronize(s));
     int64_t kept = 0, over = 0;
-    for (int64_t i = 0; i < qpad; ++i) {
-        for (int h = 0; h < KN_SPLIT; ++h) kept += hsc[i * KN_SPLIT + h];
-        over += hov[i];
-    }
+    for (int64_t i = 0; i < nstate; ++i) kept += hsc[i];
+    for (int64_t i = 0; i < qpad; ++i) over += hov[i];
     ctx->knn_stats[0] = q * n;
     ctx->knn_stats[1] = kept;
     ctx->knn_stats[2] = over;

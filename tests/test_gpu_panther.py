@@ -99,12 +99,38 @@ def _big_row_graph():
     return synth.graph_from_edges(n, edges, ws)
 
 
-@pytest.mark.parametrize("which", ["small", "bigrow", "wide"])
+def _hub_rows_graph():
+    # rows split into 1, 1, 2 and 5 segments of 4096 entries: equal weights
+    # (every entry exactly at capacity), random, one dominant weight, and
+    # log-uniform weights; plus a path through the other vertices
+    n = 30_000
+    rng = np.random.default_rng(9)
+    edges, ws = [], []
+    for hub, deg in enumerate([2049, 4096, 4097, 20_000]):
+        for j, u in enumerate(range(4, 4 + deg)):
+            edges.append((hub, u))
+            if hub == 0:
+                ws.append(7)
+            elif hub == 1:
+                ws.append(int(rng.integers(1, 2**20)))
+            elif hub == 2:
+                ws.append(2**24 if j == 1234 else 1)
+            else:
+                ws.append(int(np.exp(rng.uniform(0, np.log(2**16)))))
+    for u in range(4, n - 1):
+        edges.append((u, u + 1))
+        ws.append(int(rng.integers(1, 50)))
+    return synth.graph_from_edges(n, edges, ws)
+
+
+@pytest.mark.parametrize("which", ["small", "bigrow", "hubrows", "wide"])
 def test_transition_tables_match_oracle(pk, small, which):
     if which == "small":
         g = small
     elif which == "bigrow":
         g = _big_row_graph()
+    elif which == "hubrows":
+        g = _hub_rows_graph()
     else:
         # row sums beyond 2^32 switch the prefix table to 64-bit entries
         g = synth.graph_from_edges(40, [(0, i) for i in range(1, 40)] + [(1, 2)],

@@ -30,10 +30,12 @@ def _vectors(pk, g, seed, R, T, D, queries=None, k=None, fp32=False, both=False)
         if k:
             q = torch.as_tensor(queries, dtype=torch.int32, device="cuda:0")
             forms = [False, True] if both else [fp32]
-            for f in forms:
-                ids, d2 = P.knn(q, k, fp32=f)
-                P.sync()
-                out[("fp32" if f else "bf16")] = (ids.cpu().numpy(), d2.cpu().numpy().view(np.uint64))
+            for kk in (k if isinstance(k, (list, tuple)) else [k]):
+                for f in forms:
+                    ids, d2 = P.knn(q, kk, fp32=f)
+                    P.sync()
+                    key = ("fp32" if f else "bf16") + ("" if kk == k else f"_k{kk}")
+                    out[key] = (ids.cpu().numpy(), d2.cpu().numpy().view(np.uint64))
             out["stats"] = pk.pantherpp_knn_stats(P.h.ctx)
         P.sync()
     return out
@@ -133,7 +135,9 @@ def test_knn_host_io_and_errors(pk, small_case):
 def test_knn_workload_shape_sampled(pk):
     """A 200K-vertex graph shaped like the k-NN workload (mean degree 20, gamma 2.3,
     log-uniform weights), R = 5 paths per vertex, D = 50: all-vertex theta checked on
-    a sample of rows, and the exact top-10 of sampled queries (incl. the heaviest)."""
+    a sample of rows, and the exact top-10 and top-32 of sampled queries (incl. the
+    heaviest). One query tile against 782 candidate tiles: the candidate range is cut
+    into pieces screened by different CTAs and merged."""
     g = synth.chung_lu(200_000, 20, 2.3, ("loguniform", 1, 1024), seed=1)
     R, T, D, k = 1_000_000, 5, 50, 10
     P = oracle.sample_paths(g, 1, R, T, oracle.ALIAS)
@@ -141,9 +145,10 @@ def test_knn_workload_shape_sampled(pk):
     th = o.theta_all(D)
     sizes = np.diff(o.off)
     q = np.unique(np.concatenate([np.argsort(-sizes)[:40], np.arange(0, g.n, 4001)])).astype(np.int32)
-    out = _vectors(pk, g, 1, R, T, D, queries=q, k=k, both=False)
+    out = _vectors(pk, g, 1, R, T, D, queries=q, k=[k, 32], both=False)
     assert np.array_equal(out["theta"], th)
-    ids, d2 = out["bf16"]
-    for i, v in enumerate(q):
-        rid, rd = oracle.knn(th, int(v), k)
-        assert ids[i].tolist() == rid.tolist() and d2[i].tolist() == rd.tolist(), i
+    for key, kk in (("bf16_k10", k), ("bf16_k32", 32)):
+        ids, d2 = out[key]
+        for i, v in enumerate(q):
+            rid, rd = oracle.knn(th, int(v), kk)
+            assert ids[i].tolist() == rid.tolist() and d2[i].tolist() == rd.tolist(), (key, i)

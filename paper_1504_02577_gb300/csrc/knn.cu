@@ -738,9 +738,12 @@ __global__ void rerank_kernel(const uint32_t* __restrict__ theta, int D, const i
 
 // one CTA per query slot: top-k of the nchunk exact top-k lists of its ranges
 // (the ranges are disjoint, so no candidate appears twice)
+// With `slots` given, entry i of the lists belongs to query slot slots[i]
+// (the brute-force fallback); otherwise to slot i, skipping overflowed slots.
 __global__ void __launch_bounds__(256) chunk_merge_kernel(const int32_t* __restrict__ qv,
                                                           const int32_t* __restrict__ qidx,
-                                                          const int* __restrict__ overflow, int64_t qpad,
+                                                          const int* __restrict__ overflow,
+                                                          const int32_t* __restrict__ slots, int64_t count,
                                                           int64_t nchunk, int k, const int32_t* __restrict__ part_id,
                                                           const uint64_t* __restrict__ part_d2,
                                                           int32_t* __restrict__ out_ids,
@@ -749,9 +752,10 @@ __global__ void __launch_bounds__(256) chunk_merge_kernel(const int32_t* __restr
     __shared__ int si[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t total = nchunk * k;
-    for (int64_t slot = blockIdx.x; slot < qpad; slot += gridDim.x) {
-        if (qv[slot] < 0 || overflow[slot]) continue;
-        const int64_t qi = qidx[slot], base = slot * total;
+    for (int64_t e = blockIdx.x; e < count; e += gridDim.x) {
+        const int64_t slot = slots ? slots[e] : e;
+        if (qv[slot] < 0 || (!slots && overflow[slot])) continue;
+        const int64_t qi = qidx[slot], base = e * total;
         uint64_t lastd = 0;
         int lasti = -1;
         for (int r = 0; r < k; ++r) {
@@ -799,51 +803,60 @@ __global__ void __launch_bounds__(256) chunk_merge_kernel(const int32_t* __restr
     }
 }
 
-// exact brute force for the (rare) queries whose shortlist overflowed
-__global__ void brute_kernel(const uint32_t* __restrict__ theta, int D, int64_t n, const int32_t* __restrict__ qv,
-                             const int32_t* __restrict__ qidx, const int* __restrict__ overflow, int64_t qpad, int k,
-                             int32_t* __restrict__ out_ids, uint64_t* __restrict__ out_d2) {
-    __shared__ uint64_t sd[1024];
-    __shared__ int si[1024];
-    for (int64_t slot = blockIdx.x; slot < qpad; slot += gridDim.x) {
-        if (!overflow[slot] || qv[slot] < 0) continue;
-        const int32_t v = qv[slot];
-        const int64_t qi = qidx[slot];
-        uint64_t lastd = 0;
-        int lasti = -1;
-        for (int r = 0; r < k; ++r) {
-            uint64_t bd = ~0ull;
-            int bi = 0x7fffffff;
-            for (int64_t u = threadIdx.x; u < n; u += blockDim.x) {
-                if (u == v) continue;
-                uint64_t d = exact_d2(theta, D, v, (int32_t)u);
-                bool after = r == 0 || pair_less(lastd, lasti, d, (int)u);
-                if (after && pair_less(d, (int)u, bd, bi)) {
-                    bd = d;
-                    bi = (int)u;
+// Exact brute force for the (rare) queries whose shortlist overflowed: the
+// vertex range of each such query is cut into nparts pieces, one warp each.
+// A warp keeps its k best (d2, id) sorted across its lanes (lane l holds rank
+// l); a batch of 32 candidates costs one compare and a ballot unless one of
+// them beats the k-th entry. The nparts lists go through chunk_merge_kernel.
+__global__ void __launch_bounds__(256) brute_warp_kernel(const uint32_t* __restrict__ theta, int D, int64_t n,
+                                                         const int32_t* __restrict__ qv,
+                                                         const int32_t* __restrict__ ovslots, int64_t nov,
+                                                         int64_t nparts, int k, int32_t* __restrict__ part_id,
+                                                         uint64_t* __restrict__ part_d2) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= nov * nparts) return;
+    const int64_t oi = gw / nparts, part = gw % nparts;
+    const int32_t v = qv[ovslots[oi]];
+    const int64_t u0 = part * n / nparts, u1 = (part + 1) * n / nparts;
+    uint64_t ld = ~0ull;   // this lane's rank of the list
+    int li = 0x7fffffff;
+    for (int64_t base = u0; base < u1; base += 32) {
+        const int64_t u = base + lane;
+        uint64_t d = ~0ull;
+        if (u < u1 && u != v) d = exact_d2(theta, D, v, (int32_t)u);
+        const uint64_t td = __shfl_sync(0xffffffffu, ld, k - 1);
+        const int ti = __shfl_sync(0xffffffffu, li, k - 1);
+        unsigned pass = __ballot_sync(0xffffffffu, u < u1 && u != v && pair_less(d, (int)u, td, ti));
+        while (pass) {
+            const int src = __ffs(pass) - 1;
+            pass &= pass - 1;
+            const uint64_t nd = __shfl_sync(0xffffffffu, d, src);
+            const int ni = (int)__shfl_sync(0xffffffffu, (int)u, src);
+            // entries at or after the insertion point move up one lane
+            const bool after = pair_less(nd, ni, ld, li);
+            const unsigned am = __ballot_sync(0xffffffffu, after);
+            const uint64_t upd = __shfl_up_sync(0xffffffffu, ld, 1);
+            const int upi = __shfl_up_sync(0xffffffffu, li, 1);
+            if (am) {
+                const int pos = __ffs(am) - 1;
+                if (lane == pos) {
+                    ld = nd;
+                    li = ni;
+                } else if (lane > pos) {
+                    ld = upd;
+                    li = upi;
                 }
             }
-            sd[threadIdx.x] = bd;
-            si[threadIdx.x] = bi;
-            __syncthreads();
-            for (int o = blockDim.x / 2; o; o >>= 1) {
-                if ((int)threadIdx.x < o && pair_less(sd[threadIdx.x + o], si[threadIdx.x + o], sd[threadIdx.x],
-                                                      si[threadIdx.x])) {
-                    sd[threadIdx.x] = sd[threadIdx.x + o];
-                    si[threadIdx.x] = si[threadIdx.x + o];
-                }
-                __syncthreads();
-            }
-            bd = sd[0];
-            bi = si[0];
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                out_ids[qi * k + r] = bi == 0x7fffffff ? -1 : bi;
-                out_d2[qi * k + r] = bi == 0x7fffffff ? ~0ull : bd;
-            }
-            lastd = bd;
-            lasti = bi;
+            // candidates of this batch that no longer beat the k-th entry drop out
+            const uint64_t td2 = __shfl_sync(0xffffffffu, ld, k - 1);
+            const int ti2 = __shfl_sync(0xffffffffu, li, k - 1);
+            pass &= __ballot_sync(0xffffffffu, pair_less(d, (int)u, td2, ti2));
         }
+    }
+    if (lane < k) {
+        part_id[gw * k + lane] = li == 0x7fffffff ? -1 : li;
+        part_d2[gw * k + lane] = ld;
     }
 }
 
@@ -1100,14 +1113,12 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* v, const i
     PCK(ctx, cudaGetLastError());
     rerank_kernel<<<(unsigned)ceil_div(qpad * nch * 32, 256), 256, 0, s>>>(v->theta, v->D, qv, qidx, qpad, nch, k,
                                                                             lists, sl, sc, ovf, ids, d2, pid, pd);
+    ctx->launches++;
     if (nch > 1) {
         chunk_merge_kernel<<<(unsigned)std::min<int64_t>(qpad, 8 * ctx->num_sms), 256, 0, s>>>(
-            qv, qidx, ovf, qpad, nch, k, pid, pd, ids, d2);
+            qv, qidx, ovf, nullptr, qpad, nch, k, pid, pd, ids, d2);
         ctx->launches++;
     }
-    brute_kernel<<<(unsigned)std::min<int64_t>(qpad, 4 * ctx->num_sms), 1024, 0, s>>>(v->theta, v->D, n, qv, qidx,
-                                                                                       ovf, qpad, k, ids, d2);
-    ctx->launches += 2;
     PCK(ctx, cudaGetLastError());
     // screening statistics (pairs screened, kept for rerank, overflowed queries)
     std::vector<int32_t> hsc(nstate);
@@ -1116,8 +1127,41 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* v, const i
     PCK(ctx, cudaMemcpyAsync(hov.data(), ovf, sizeof(int) * qpad, cudaMemcpyDeviceToHost, s));
     PCK(ctx, cudaStreamSynchronize(s));
     int64_t kept = 0, over = 0;
+    std::vector<int32_t> hslots;
     for (int64_t i = 0; i < nstate; ++i) kept += hsc[i];
-    for (int64_t i = 0; i < qpad; ++i) over += hov[i];
+    for (int64_t i = 0; i < qpad; ++i)
+        if (hov[i]) hslots.push_back((int32_t)i);
+    over = (int64_t)hslots.size();
+    if (over) {
+        // the overflowed queries: exact brute force over all vertices, spread over the GPU
+        const int64_t nparts = std::max<int64_t>(1, std::min<int64_t>(1024, ceil_div(n, 4096)));
+        int32_t* dsl = nullptr;
+        int32_t* bid = nullptr;
+        uint64_t* bd = nullptr;
+        auto bfree = [&]() { dev_free(ctx, dsl); dev_free(ctx, bid); dev_free(ctx, bd); };
+        if ((st = dev_alloc(ctx, (void**)&dsl, sizeof(int32_t) * over)) ||
+            (st = dev_alloc(ctx, (void**)&bid, sizeof(int32_t) * over * nparts * k)) ||
+            (st = dev_alloc(ctx, (void**)&bd, sizeof(uint64_t) * over * nparts * k))) {
+            bfree();
+            cleanup();
+            return st;
+        }
+        cudaError_t ce = cudaMemcpyAsync(dsl, hslots.data(), sizeof(int32_t) * over, cudaMemcpyHostToDevice, s);
+        if (!ce) {
+            brute_warp_kernel<<<(unsigned)ceil_div(over * nparts * 32, 256), 256, 0, s>>>(
+                v->theta, v->D, n, qv, dsl, over, nparts, k, bid, bd);
+            chunk_merge_kernel<<<(unsigned)std::min<int64_t>(over, 8 * ctx->num_sms), 256, 0, s>>>(
+                qv, qidx, ovf, dsl, over, nparts, k, bid, bd, ids, d2);
+            ctx->launches += 2;
+            ce = cudaGetLastError();
+        }
+        if (!ce) ce = cudaStreamSynchronize(s);   // the host slot list must outlive the copy
+        bfree();
+        if (ce) {
+            cleanup();
+            return cuda_err(ctx, ce, "k-NN brute-force fallback");
+        }
+    }
     ctx->knn_stats[0] = q * n;
     ctx->knn_stats[1] = kept;
     ctx->knn_stats[2] = over;

@@ -92,6 +92,24 @@ def test_knn_large_counts_and_ragged_queries(pk):
             assert d2[i].tolist() == rd.tolist(), (form, i)
 
 
+def test_knn_shortlist_overflow_falls_back_exactly(pk):
+    # counts in the tens of thousands on a dense graph: the BF16 error bound
+    # covers hundreds of candidates per query, shortlists overflow and those
+    # queries are answered by the exact brute-force pass
+    g = synth.chung_lu(1500, 60, 2.2, ("uniform", 1, 4), seed=8)
+    R, T, D, k = 4_000_000, 5, 50, 10
+    th = _oracle_theta(g, 6, R, T, D)
+    rng = np.random.default_rng(2)
+    q = rng.integers(0, g.n, size=200).astype(np.int32)
+    out = _vectors(pk, g, 6, R, T, D, queries=q, k=k, both=False)
+    assert np.array_equal(out["theta"], th)
+    assert out["stats"][2] > 0                          # some queries overflowed
+    ids, d2 = out["bf16"]
+    for i, v in enumerate(q):
+        rid, rd = oracle.knn(th, int(v), k)
+        assert ids[i].tolist() == rid.tolist() and d2[i].tolist() == rd.tolist(), i
+
+
 def test_knn_mass_ties_and_padding(pk):
     # many identical vectors (distance-0 ties broken by id) and k larger than
     # the number of other vertices

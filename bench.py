@@ -227,11 +227,13 @@ def run_ours(args, ws, rank, local):
     with Clocks(local) as clk:
         start, end = ev(), ev()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")   # lets a profiler keep only the timed launches
         start.record(P.stream)
         for _ in range(args.steps):
             step(rec)
         end.record(P.stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     launches = P.launches() - l0
     P.sync()
     ms_total = start.elapsed_time(end)
@@ -489,11 +491,13 @@ def run_knn(args, ws, rank, local):
     l0 = P.launches()
     with Clocks(local) as clk:
         s, e = ev(), ev()
+        torch.cuda.nvtx.range_push("timed")
         s.record(P.stream)
         for _ in range(args.steps):
             ids, d2 = P.knn(qv, k)
         e.record(P.stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     launches = P.launches() - l0
     st = pk.pantherpp_knn_stats(P.h.ctx)
     ms = _max_over_ranks(s.elapsed_time(e) / args.steps, ws)

@@ -181,6 +181,8 @@ void panther_free_index(panther_index* ix) {
     if (!ix) return;
     dev_free(ix->ctx, ix->off);
     dev_free(ix->ctx, ix->pid);
+    dev_free(ix->ctx, ix->cls);
+    dev_free(ix->ctx, ix->cls_hist);
     cudaStreamSynchronize(ix->ctx->stream);
     delete ix;
 }

@@ -9,6 +9,7 @@
 // stable scatter. The scatter ranks items with warp-private digit counters:
 // warps own contiguous sub-ranges of a tile and walk them in order, so the
 // sort is stable and path ids come out ascending within each vertex.
+#include <algorithm>
 #include <mutex>
 
 #include "internal.cuh"
@@ -189,6 +190,24 @@ __global__ void offsets_kernel(const int32_t* __restrict__ keys, int64_t nnz, in
     for (int64_t v = prev + 1; v <= cur; ++v) off[v] = i;
 }
 
+// cls[v] = min(|P_v|, 255) and its histogram (a count of v with any u never
+// exceeds |P_v| or |P_u|)
+__global__ void cls_kernel(const int64_t* __restrict__ off, int64_t n, uint8_t* __restrict__ cls,
+                           unsigned long long* __restrict__ hist) {
+    __shared__ unsigned h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t np = off[v + 1] - off[v];
+        const uint32_t c = np < 255 ? (uint32_t)np : 255u;
+        cls[v] = (uint8_t)c;
+        atomicAdd(&h[c], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+
 __global__ void total_kernel(const int64_t* __restrict__ counts, const int64_t* __restrict__ offs, int64_t len,
                              int64_t* __restrict__ total) {
     *total = offs[len - 1] + counts[len - 1];
@@ -242,7 +261,9 @@ extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_pa
         (st = dev_alloc(ctx, (void**)&counts, sizeof(int64_t) * radix * maxtiles)) ||
         (st = dev_alloc(ctx, (void**)&offs, sizeof(int64_t) * radix * maxtiles)) ||
         (st = dev_alloc(ctx, (void**)&tot, sizeof(int64_t))) ||
-        (st = dev_alloc(ctx, (void**)&ix->off, sizeof(int64_t) * (n + 1)))) {
+        (st = dev_alloc(ctx, (void**)&ix->off, sizeof(int64_t) * (n + 1))) ||
+        (st = dev_alloc(ctx, (void**)&ix->cls, n)) ||
+        (st = dev_alloc(ctx, (void**)&ix->cls_hist, sizeof(int64_t) * 256))) {
         cleanup();
         panther_free_index(ix);
         return st;
@@ -289,7 +310,14 @@ extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_pa
     }
     ix->nnz = count;
     offsets_kernel<<<(unsigned)ceil_div(count + 1, 256), 256, 0, s>>>(ik, count, n, ix->off, ctx->d_status);
-    ctx->launches++;
+    if (cudaError_t e = cudaMemsetAsync(ix->cls_hist, 0, sizeof(int64_t) * 256, s)) {
+        cleanup();
+        panther_free_index(ix);
+        return cuda_err(ctx, e, "index classes");
+    }
+    cls_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->num_sms * 8), 256, 0, s>>>(
+        ix->off, n, ix->cls, (unsigned long long*)ix->cls_hist);
+    ctx->launches += 2;
     // keep the final value array as pid; release everything else
     ix->pid = iv;
     if (iv == vA) vA = nullptr; else vB = nullptr;

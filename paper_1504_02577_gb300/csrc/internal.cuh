@@ -60,6 +60,8 @@ struct panther_index {
     int64_t n = 0, nnz = 0;
     int64_t* off = nullptr;          // [n+1]
     int32_t* pid = nullptr;          // [nnz]
+    uint8_t* cls = nullptr;          // [n] min(|P_v|, 255): an upper bound of any count with v
+    int64_t* cls_hist = nullptr;     // [256] vertices per cls value
 };
 
 struct pantherpp_vecs {

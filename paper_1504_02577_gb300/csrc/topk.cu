@@ -186,12 +186,14 @@ struct PathsRef {
     const int64_t* off;
     const int32_t* pid;
     int64_t n;
+    const uint8_t* cls;   // min(|P_u|, 255) per vertex
 };
 
-// insert the distinct vertices u != v of path r into the table
+// insert the distinct vertices u != v of path r into the table (with thr > 0
+// only the u with cls[u] >= thr)
 template <int STRIDE, bool SHARED>
 __device__ __forceinline__ bool insert_path(const PathsRef& P, int32_t r, int32_t v, unsigned long long* tab,
-                                            uint32_t nslots) {
+                                            uint32_t nslots, uint32_t thr = 0) {
     if ((uint32_t)r >= (uint64_t)P.R) return false;   // corrupt index entry: the caller flags it, nothing is read
     int32_t x[STRIDE];
     const int4* src = (const int4*)(P.rows + (int64_t)r * STRIDE);
@@ -207,7 +209,7 @@ __device__ __forceinline__ bool insert_path(const PathsRef& P, int32_t r, int32_
             bool dup = false;
 #pragma unroll
             for (int i = 0; i < j; ++i) dup |= (x[i] == x[j]);
-            if (!dup) ok &= hash_add<SHARED>(tab, nslots, (uint32_t)x[j]);
+            if (!dup && (thr == 0 || __ldg(P.cls + x[j]) >= thr)) ok &= hash_add<SHARED>(tab, nslots, (uint32_t)x[j]);
         }
     }
     return ok;
@@ -329,10 +331,11 @@ __device__ __forceinline__ bool hash_add_conv(unsigned long long* tab, uint32_t 
     return ok;
 }
 
-// insert the distinct vertices u != v of path r (lanes with active == false pass r = -1)
+// insert the distinct vertices u != v of path r (lanes with active == false pass r = -1);
+// with thr > 0 only the u with cls[u] >= thr
 template <int STRIDE>
 __device__ __forceinline__ bool insert_path_conv(const PathsRef& P, int32_t r, int32_t v, unsigned long long* tab,
-                                                 uint32_t nslots, bool active) {
+                                                 uint32_t nslots, bool active, uint32_t thr = 0) {
     active &= (uint32_t)r < (uint64_t)P.R;
     int32_t x[STRIDE];
     const int4* src = (const int4*)(P.rows + (int64_t)(active ? r : 0) * STRIDE);
@@ -347,6 +350,7 @@ __device__ __forceinline__ bool insert_path_conv(const PathsRef& P, int32_t r, i
         bool take = active && j < P.L && x[j] != v;
 #pragma unroll
         for (int i = 0; i < j; ++i) take &= (x[i] != x[j]);
+        if (thr && take) take = __ldg(P.cls + x[j]) >= thr;
         if (__any_sync(0xffffffffu, take)) ok &= hash_add_conv(tab, nslots, (uint32_t)x[j], 1u, take);
     }
     return ok;
@@ -544,6 +548,7 @@ struct GPlan {
     const int64_t* item_off;  // [ng+1] prefix of count work items
     const int64_t* sel_off;   // [ng+1] prefix of select work items
     int ng;
+    const uint32_t* thr;      // [ng] count only the u with cls[u] >= thr (0: every u), or null
 };
 
 constexpr int G_PATHS = 2048;     // paths per count item
@@ -569,9 +574,10 @@ __global__ void g_count_kernel(PathsRef P, const int32_t* __restrict__ queries, 
     int64_t a = P.off[v] + (item - G.item_off[g]) * G_PATHS;
     int64_t b = a + G_PATHS < P.off[v + 1] ? a + G_PATHS : P.off[v + 1];
     unsigned long long* tab = arena + G.tab_off[g];
+    const uint32_t thr = G.thr ? G.thr[g] : 0;
     bool ok = true;
     for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x)
-        ok &= insert_path<STRIDE, false>(P, P.pid[e], v, tab, G.tab_n[g]);
+        ok &= insert_path<STRIDE, false>(P, P.pid[e], v, tab, G.tab_n[g], thr);
     if (!ok) flag_status(status, ST_HASH_FULL);
 }
 
@@ -643,10 +649,13 @@ constexpr int B_CAP = 4096;        // pairs per bucket
 constexpr int B_SLOTS2 = 8192;     // pass-2 table
 constexpr int B_TARGET = 2048;     // expected pairs per bucket when sizing nb
 constexpr int B_T2 = 256;          // threads of a pass-2 CTA
+constexpr double HUB_PRUNE = 0.03;   // first-round threshold = HUB_PRUNE * |P_v| / max(k, 10)
+constexpr int64_t HUB_TABLE_BOUND = 1 << 19;   // filtered candidate bound counted in a device table
 
 struct BPlan {
     int bpaths;                // paths per pass-1 chunk
     const int32_t* qidx;       // [ng] query index
+    const uint32_t* thr;       // [ng] count only the u with cls[u] >= thr (0: every u)
     const int64_t* chunk_off;  // [ng+1] prefix of pass-1 chunks
     const int64_t* bucket_off; // [ng+1] prefix of buckets
     int ng;
@@ -673,14 +682,14 @@ __global__ void __launch_bounds__(512) b_scatter_kernel(PathsRef P, const int32_
     const int32_t v = queries ? queries[qi] : (int32_t)qi;
     const int64_t a = P.off[v] + (item - B.chunk_off[g]) * B.bpaths;
     const int64_t b = a + B.bpaths < P.off[v + 1] ? a + B.bpaths : P.off[v + 1];
-    const uint32_t nslots = B_SLOTS1;
+    const uint32_t nslots = B_SLOTS1, thr = B.thr[g];
     for (uint32_t s = threadIdx.x; s < nslots; s += blockDim.x) tab[s] = EMPTY;
     __syncthreads();
     bool ok = true;
     for (int64_t base = a + (threadIdx.x & ~31u); base < b; base += blockDim.x) {   // warp-uniform
         const int64_t e = base + (threadIdx.x & 31);
         const bool act = e < b;
-        ok &= insert_path_conv<STRIDE>(P, act ? P.pid[e] : -1, v, tab, nslots, act);
+        ok &= insert_path_conv<STRIDE>(P, act ? P.pid[e] : -1, v, tab, nslots, act, thr);
     }
     if (!ok) flag_status(status, ST_HASH_FULL);
     __syncthreads();
@@ -738,6 +747,22 @@ __global__ void __launch_bounds__(B_T2) b_count_kernel(BPlan B, int k, unsigned 
     }
 }
 
+// after a filtered round: the k-th count c of the query over the u with
+// cls[u] >= thr is a lower bound of its true k-th count, so every u of the true
+// top-k has |P_u| >= c. If c >= thr the filtered list is the answer (-1);
+// otherwise the query is counted again with threshold c.
+__global__ void hub_check_kernel(const int32_t* __restrict__ qidx, const uint32_t* __restrict__ thr, int ng, OutRef o,
+                                 int32_t* __restrict__ redo) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ng) return;
+    if (thr[i] == 0) {
+        redo[i] = -1;
+        return;
+    }
+    const uint32_t kth = o.cnt[(int64_t)qidx[i] * o.k + o.k - 1];
+    redo[i] = kth >= thr[i] ? -1 : (int32_t)kth;
+}
+
 __global__ void g_info_kernel(const int32_t* __restrict__ list, int ng, const int32_t* __restrict__ queries,
                               const int64_t* __restrict__ off, int64_t* __restrict__ np) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -789,7 +814,13 @@ static panther_status set_smem_attr(panther_ctx* ctx, size_t bytes) {
 struct HubQuery {
     int32_t qi;      // query index
     int64_t np;      // |P_v|
+    uint32_t thr;    // count only the u with cls[u] >= thr (0: every u)
 };
+
+// bound of the distinct candidates of a hub query under its threshold
+static int64_t hub_bound(const PathsRef& P, const HubQuery& h, const std::vector<int64_t>& above) {
+    return std::min<int64_t>(std::min<int64_t>(h.np * (P.L - 1), P.n - 1), above[h.thr]);
+}
 
 // device copy of a small host plan (kept until the stream reaches it)
 static panther_status upload(panther_ctx* ctx, const std::vector<char>& h, char** d) {
@@ -808,9 +839,13 @@ static size_t put(std::vector<char>& h, const std::vector<T>& v) {
 }
 
 // Bucketed counting of hub queries (largest first, rounds under the scratch
-// budget). Queries whose buckets overflowed are returned in `again`.
+// budget). Queries whose buckets overflowed are returned in `again`; filtered
+// queries whose k-th count came out below their threshold are returned in
+// `redo` with that count as the new threshold. `above[t]` = vertices with
+// cls >= t (sizes the buckets of a filtered query).
 static panther_status hub_buckets(panther_ctx* ctx, const PathsRef& P, const int32_t* queries, const OutRef& o, int k,
-                                  std::vector<HubQuery> hubs, std::vector<HubQuery>& again) {
+                                  std::vector<HubQuery> hubs, const std::vector<int64_t>& above,
+                                  std::vector<HubQuery>& again, std::vector<HubQuery>& redo) {
     cudaStream_t s = ctx->stream;
     std::sort(hubs.begin(), hubs.end(),
               [](const HubQuery& a, const HubQuery& b) { return a.np != b.np ? a.np > b.np : a.qi < b.qi; });
@@ -834,15 +869,16 @@ static panther_status hub_buckets(panther_ctx* ctx, const PathsRef& P, const int
     panther_status st;
     while (pos < hubs.size()) {
         std::vector<int32_t> rq;
+        std::vector<uint32_t> rt;
         std::vector<int64_t> coff{0}, boff{0};
         std::vector<HubQuery> rh;
         int64_t used = 0;
         while (pos < hubs.size()) {
             const HubQuery& h = hubs[pos];
-            int64_t cap = std::min<int64_t>(h.np * (P.L - 1), P.n - 1);
-            int64_t nb = std::max<int64_t>(1, ceil_div(cap, B_TARGET));
+            int64_t nb = std::max<int64_t>(1, ceil_div(hub_bound(P, h, above), B_TARGET));
             if (!rq.empty() && used + nb * per_bucket > budget) break;
             rq.push_back(h.qi);
+            rt.push_back(h.thr);
             rh.push_back(h);
             coff.push_back(coff.back() + ceil_div(h.np, bpaths));
             boff.push_back(boff.back() + nb);
@@ -852,44 +888,63 @@ static panther_status hub_buckets(panther_ctx* ctx, const PathsRef& P, const int
         const int rng = (int)rq.size();
         const int64_t nbt = boff.back();
         std::vector<char> hp;
-        size_t o_q = put(hp, rq), o_c = put(hp, coff), o_b = put(hp, boff);
+        size_t o_q = put(hp, rq), o_t = put(hp, rt), o_c = put(hp, coff), o_b = put(hp, boff);
         char* dplan = nullptr;
         unsigned long long *pairs = nullptr, *partial = nullptr;
         int *cursor = nullptr, *ovf = nullptr;
+        int32_t* dredo = nullptr;
         if ((st = upload(ctx, hp, &dplan)) || (st = dev_alloc(ctx, (void**)&pairs, 8ull * B_CAP * nbt)) ||
             (st = dev_alloc(ctx, (void**)&partial, 8ull * KMAX * nbt)) ||
             (st = dev_alloc(ctx, (void**)&cursor, sizeof(int) * nbt)) ||
-            (st = dev_alloc(ctx, (void**)&ovf, sizeof(int) * rng))) {
+            (st = dev_alloc(ctx, (void**)&ovf, sizeof(int) * rng)) ||
+            (st = dev_alloc(ctx, (void**)&dredo, sizeof(int32_t) * rng))) {
             dev_free(ctx, dplan); dev_free(ctx, pairs); dev_free(ctx, partial); dev_free(ctx, cursor);
+            dev_free(ctx, ovf);
             return st;
         }
         PCK(ctx, cudaMemsetAsync(cursor, 0, sizeof(int) * nbt, s));
         PCK(ctx, cudaMemsetAsync(ovf, 0, sizeof(int) * rng, s));
-        BPlan B{bpaths, (const int32_t*)(dplan + o_q), (const int64_t*)(dplan + o_c), (const int64_t*)(dplan + o_b),
-                rng, pairs, cursor, ovf};
+        BPlan B{bpaths, (const int32_t*)(dplan + o_q), (const uint32_t*)(dplan + o_t), (const int64_t*)(dplan + o_c),
+                (const int64_t*)(dplan + o_b), rng, pairs, cursor, ovf};
         const unsigned g1 = (unsigned)coff.back();
         if (stride == 8) b_scatter_kernel<8><<<g1, 512, B_SLOTS1 * 8, s>>>(P, queries, B, ctx->d_status);
         else if (stride == 16) b_scatter_kernel<16><<<g1, 512, B_SLOTS1 * 8, s>>>(P, queries, B, ctx->d_status);
         else b_scatter_kernel<32><<<g1, 512, B_SLOTS1 * 8, s>>>(P, queries, B, ctx->d_status);
         b_count_kernel<<<(unsigned)nbt, B_T2, B_SLOTS2 * 8, s>>>(B, k, partial, ctx->d_status);
-        GPlan G{B.qidx, nullptr, nullptr, nullptr, B.bucket_off, rng};
+        GPlan G{B.qidx, nullptr, nullptr, nullptr, B.bucket_off, rng, nullptr};
         g_merge_cta_kernel<<<rng, 256, 0, s>>>(G, partial, o);
-        ctx->launches += 3;
+        hub_check_kernel<<<(unsigned)ceil_div(rng, 256), 256, 0, s>>>(B.qidx, B.thr, rng, o, dredo);
+        ctx->launches += 4;
         PCK(ctx, cudaGetLastError());
         std::vector<int> hov(rng);
+        std::vector<int32_t> hredo(rng);
         PCK(ctx, cudaMemcpyAsync(hov.data(), ovf, sizeof(int) * rng, cudaMemcpyDeviceToHost, s));
+        PCK(ctx, cudaMemcpyAsync(hredo.data(), dredo, sizeof(int32_t) * rng, cudaMemcpyDeviceToHost, s));
         PCK(ctx, cudaStreamSynchronize(s));
-        for (int i = 0; i < rng; ++i)
-            if (hov[i]) again.push_back(rh[i]);
+        for (int i = 0; i < rng; ++i) {
+            if (hov[i]) {
+                HubQuery h = rh[i];
+                h.thr = 0;
+                again.push_back(h);
+            } else if (hredo[i] >= 0) {
+                HubQuery h = rh[i];
+                h.thr = (uint32_t)hredo[i];
+                redo.push_back(h);
+            }
+        }
         dev_free(ctx, dplan); dev_free(ctx, pairs); dev_free(ctx, partial); dev_free(ctx, cursor); dev_free(ctx, ovf);
+        dev_free(ctx, dredo);
     }
     return PANTHER_OK;
 }
 
-// Hub queries counted in per-query device tables (the fallback of the
-// bucketed path): rounds under the scratch budget.
+// Hub queries counted in per-query device tables of twice their candidate
+// bound (small filtered hubs, and the fallback of the bucketed path): rounds
+// under the scratch budget. Filtered queries whose k-th count came out below
+// their threshold are returned in `redo` (see hub_check_kernel).
 static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int32_t* queries, const OutRef& o, int k,
-                                 const std::vector<HubQuery>& hubs) {
+                                 const std::vector<HubQuery>& hubs, const std::vector<int64_t>& above,
+                                 std::vector<HubQuery>& redo) {
     cudaStream_t s = ctx->stream;
     const int64_t budget_slots = std::max<int64_t>(ctx->scratch_budget / 8 / 2, 1 << 20);
     const int stride = P.L <= 8 ? 8 : (P.L <= 16 ? 16 : 32);
@@ -900,14 +955,16 @@ static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int3
     while (pos < hubs.size()) {
         std::vector<int32_t> rq;
         std::vector<int64_t> roff, ioff{0}, soff{0};
-        std::vector<uint32_t> rn;
+        std::vector<uint32_t> rn, rt;
+        std::vector<HubQuery> rh;
         int64_t used = 0;
         while (pos < hubs.size()) {
             const HubQuery& h = hubs[pos];
-            int64_t cap = std::min<int64_t>(h.np * (P.L - 1), P.n - 1);
-            uint32_t slots = pow2_at_least(cap * 2);
+            uint32_t slots = pow2_at_least(hub_bound(P, h, above) * 2);
             if (!rq.empty() && used + slots > budget_slots) break;
             rq.push_back(h.qi);
+            rt.push_back(h.thr);
+            rh.push_back(h);
             roff.push_back(used);
             rn.push_back(slots);
             used += slots;
@@ -925,27 +982,41 @@ static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int3
         }
         const int rng = (int)rq.size();
         std::vector<char> hp;
-        size_t o_q = put(hp, rq), o_o = put(hp, roff), o_n = put(hp, rn), o_i = put(hp, ioff), o_s = put(hp, soff);
+        size_t o_q = put(hp, rq), o_o = put(hp, roff), o_n = put(hp, rn), o_i = put(hp, ioff), o_s = put(hp, soff),
+               o_t = put(hp, rt);
         char* dplan = nullptr;
         unsigned long long* partial = nullptr;
+        int32_t* dredo = nullptr;
         if ((st = upload(ctx, hp, &dplan)) ||
-            (st = dev_alloc(ctx, (void**)&partial, sizeof(unsigned long long) * KMAX * soff.back()))) {
+            (st = dev_alloc(ctx, (void**)&partial, sizeof(unsigned long long) * KMAX * soff.back())) ||
+            (st = dev_alloc(ctx, (void**)&dredo, sizeof(int32_t) * rng))) {
             dev_free(ctx, dplan);
+            dev_free(ctx, partial);
             dev_free(ctx, arena);
             return st;
         }
         GPlan G{(const int32_t*)(dplan + o_q), (const int64_t*)(dplan + o_o), (const uint32_t*)(dplan + o_n),
-                (const int64_t*)(dplan + o_i), (const int64_t*)(dplan + o_s), rng};
+                (const int64_t*)(dplan + o_i), (const int64_t*)(dplan + o_s), rng, (const uint32_t*)(dplan + o_t)};
         if (stride == 8) g_count_kernel<8><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
         else if (stride == 16) g_count_kernel<16><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
         else g_count_kernel<32><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
         g_select_kernel<<<(unsigned)soff.back(), 512, 0, s>>>(G, arena, k, partial);
-        g_merge_kernel<<<rng, 32, 0, s>>>(G, partial, o);
-        ctx->launches += 3;
+        g_merge_cta_kernel<<<rng, 256, 0, s>>>(G, partial, o);
+        hub_check_kernel<<<(unsigned)ceil_div(rng, 256), 256, 0, s>>>(G.qidx, G.thr, rng, o, dredo);
+        ctx->launches += 4;
         PCK(ctx, cudaGetLastError());
+        std::vector<int32_t> hredo(rng);
+        PCK(ctx, cudaMemcpyAsync(hredo.data(), dredo, sizeof(int32_t) * rng, cudaMemcpyDeviceToHost, s));
         PCK(ctx, cudaStreamSynchronize(s));   // the host plan must outlive the copy
+        for (int i = 0; i < rng; ++i)
+            if (hredo[i] >= 0) {
+                HubQuery h = rh[i];
+                h.thr = (uint32_t)hredo[i];
+                redo.push_back(h);
+            }
         dev_free(ctx, dplan);
         dev_free(ctx, partial);
+        dev_free(ctx, dredo);
     }
     dev_free(ctx, arena);
     return PANTHER_OK;
@@ -963,7 +1034,7 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
     else if (p->stride == 16) st = set_smem_attr<16>(ctx, smem);
     else st = set_smem_attr<32>(ctx, smem);
     if (st) return st;
-    PathsRef P{p->rows, p->R, p->L, ix->off, ix->pid, ix->n};
+    PathsRef P{p->rows, p->R, p->L, ix->off, ix->pid, ix->n, ix->cls};
     OutRef o{ids, cnt, k};
     const int64_t ccap = (int64_t)sh.cta_slots * 7 / 10;
 
@@ -1027,15 +1098,41 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
         }
         g_info_kernel<<<(unsigned)ceil_div(ng, 256), 256, 0, s>>>(lists + 2 * q, ng, queries, ix->off, d_np);
         ctx->launches++;
+        std::vector<int64_t> hist(256), above(257, 0);
         PCK(ctx, cudaMemcpyAsync(gq.data(), lists + 2 * q, sizeof(int32_t) * ng, cudaMemcpyDeviceToHost, s));
         PCK(ctx, cudaMemcpyAsync(npv.data(), d_np, sizeof(int64_t) * ng, cudaMemcpyDeviceToHost, s));
+        PCK(ctx, cudaMemcpyAsync(hist.data(), ix->cls_hist, sizeof(int64_t) * 256, cudaMemcpyDeviceToHost, s));
         PCK(ctx, cudaStreamSynchronize(s));
         dev_free(ctx, d_np);
+        for (int t = 255; t >= 0; --t) above[t] = above[t + 1] + hist[t];
+        // First round: count only candidates u with |P_u| >= HUB_PRUNE * |P_v| / max(k, 10)
+        // (the k-th count of a hub tends to lie well above that); a query whose
+        // k-th count comes out below its threshold is counted again with that
+        // count as the threshold, which is then exact (hub_check_kernel).
         std::vector<HubQuery> hubs(ng);
-        for (int i = 0; i < ng; ++i) hubs[i] = HubQuery{gq[i], npv[i]};
-        std::vector<HubQuery> again;
-        st = hub_buckets(ctx, P, queries, o, k, hubs, again);
-        if (!st && !again.empty()) st = hub_tables(ctx, P, queries, o, k, again);
+        for (int i = 0; i < ng; ++i) {
+            int64_t t = (int64_t)((double)npv[i] * HUB_PRUNE / std::max(k, 10));
+            hubs[i] = HubQuery{gq[i], npv[i], (uint32_t)(t < 2 ? 0 : std::min<int64_t>(t, 255))};
+        }
+        // queries with a small filtered candidate bound count straight into a
+        // device table (it stays in L2); the others go through the buckets
+        auto run = [&](const std::vector<HubQuery>& list, std::vector<HubQuery>& again,
+                       std::vector<HubQuery>& redo) -> panther_status {
+            std::vector<HubQuery> tq, bq;
+            for (const HubQuery& h : list)
+                (h.thr > 0 && hub_bound(P, h, above) <= HUB_TABLE_BOUND ? tq : bq).push_back(h);
+            panther_status r = PANTHER_OK;
+            if (!tq.empty()) r = hub_tables(ctx, P, queries, o, k, tq, above, redo);
+            if (!r && !bq.empty()) r = hub_buckets(ctx, P, queries, o, k, bq, above, again, redo);
+            return r;
+        };
+        std::vector<HubQuery> again, redo, redo2;
+        st = run(hubs, again, redo);
+        if (!st && !redo.empty()) st = run(redo, again, redo2);
+        // a threshold equal to a lower bound of the k-th count always holds
+        if (!st && !redo2.empty()) st = set_err(ctx, PANTHER_ECUDA, "hub threshold check failed twice");
+        std::vector<HubQuery> none;
+        if (!st && !again.empty()) st = hub_tables(ctx, P, queries, o, k, again, above, none);
         if (st) {
             dev_free(ctx, lists);
             dev_free(ctx, counts);

@@ -263,6 +263,31 @@ def test_topk_global_tier_hubs(pk):
     assert np.array_equal(out["cnt"], rcnt)
 
 
+def test_topk_hub_threshold_retry(pk):
+    # A 30,000-leaf star whose centre is a hub query: its first-round filter
+    # (candidates u with |P_u| >= 255) keeps only the twelve secondary hubs,
+    # whose counts with the centre lie far below 255, so the centre is counted
+    # again with its k-th count as the threshold (k = 10), or with no threshold
+    # at all when fewer than k candidates survive (k = 20).
+    n = 40_000
+    edges = [(0, u) for u in range(1, 30_001)]
+    for s_ in range(1, 13):
+        edges += [(s_, 30_001 + 300 * (s_ - 1) + j) for j in range(300) if 30_001 + 300 * (s_ - 1) + j < n]
+    g = synth.graph_from_edges(n, edges, [1] * len(edges))
+    R, T = 200_000, 5
+    q = np.array([0, 1, 2, 12, 500, 30_001, 0], dtype=np.int32)
+    ref = oracle.sample_paths(g, 5, R, T, oracle.ALIAS)
+    o = oracle.Oracle(g.n, ref)
+    sizes = np.diff(o.off)
+    assert sizes[0] * 5 > 30_000 and sizes[1:13].min() >= 255
+    for k in (10, 20, 1):
+        out = _run(pk, g, 5, R, T, pk.MODE_ALIAS, k=k, queries=q)
+        rid, rcnt = o.topk_many(q, k)
+        assert np.array_equal(out["ids"], rid), k
+        assert np.array_equal(out["cnt"], rcnt), k
+    assert rcnt[0].max() < 255        # so the first round cannot be the answer
+
+
 def test_topk_edge_cases(pk):
     g = synth.graph_from_edges(6, [(0, 1), (1, 2), (2, 0), (3, 4)], [1, 2, 3, 4])  # 5 isolated
     R, T = 400, 3

@@ -137,6 +137,33 @@ struct WarpTopK {
     }
 };
 
+// Bitonic sort, descending, of the 64 keys (a, b) of a warp: key a of lane l
+// has rank l, key b rank 32 + l once sorted.
+__device__ __forceinline__ void warp_sort64_desc(uint64_t& a, uint64_t& b) {
+    const unsigned lane = threadIdx.x & 31;
+#pragma unroll
+    for (int kk = 2; kk <= 64; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            if (j == 32) {
+                // partners a (index lane) and b (index 32 + lane) in the same lane
+                const bool desc = (lane & kk) == 0;     // kk == 64: always
+                const uint64_t hi = umax64(a, b), lo = umin64(a, b);
+                a = desc ? hi : lo;
+                b = desc ? lo : hi;
+            } else {
+                const uint64_t pa = __shfl_xor_sync(0xffffffffu, a, j);
+                const uint64_t pb = __shfl_xor_sync(0xffffffffu, b, j);
+                const bool lower = (lane & j) == 0;
+                const bool da = kk == 64 || (lane & kk) == 0;
+                const bool db = kk == 64 || ((32 + lane) & kk) == 0;
+                a = (lower == da) ? umax64(a, pa) : umin64(a, pa);
+                b = (lower == db) ? umax64(b, pb) : umin64(b, pb);
+            }
+        }
+    }
+}
+
 // merge the lists of all warps of the CTA into warp 0 (log-depth tree);
 // `lists` holds 64 entries per warp; every thread of the CTA must call it
 __device__ __forceinline__ void cta_merge(WarpTopK& t, unsigned long long* lists) {
@@ -157,6 +184,38 @@ __device__ __forceinline__ uint64_t slot_score(unsigned long long s) {
     if (s == EMPTY) return 0;
     uint32_t key = (uint32_t)(s >> 32), cnt = (uint32_t)s;
     return ((uint64_t)cnt << 32) | (uint64_t)(0xffffffffu - key);
+}
+
+// Top-k of a warp-private table of ns slots (ns a multiple of 32). With at
+// most 64 filled slots they are compacted in place and sorted once; otherwise
+// every slot is offered to a running list. The table is garbage afterwards.
+__device__ __forceinline__ WarpTopK warp_table_topk(unsigned long long* tab, uint32_t ns, int k) {
+    const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    int filled = 0;
+    for (uint32_t base = 0; base < ns; base += 32)
+        filled += __popc(__ballot_sync(0xffffffffu, tab[base + lane] != EMPTY));
+    WarpTopK t;
+    if (filled > 64) {
+        for (uint32_t base = 0; base < ns; base += 32) t.offer(slot_score(tab[base + lane]), k);
+        return t;
+    }
+    uint64_t mine[2] = {0, 0};
+    int pos = 0;
+    for (uint32_t base = 0; base < ns; base += 32) {
+        const uint64_t sc = slot_score(tab[base + lane]);
+        const unsigned m = __ballot_sync(0xffffffffu, sc != 0);
+        const int at = pos + __popc(m & lt);
+        // every lane read its slot before the ballot, and at < base + 32
+        if (sc) tab[at] = sc;
+        pos += __popc(m);
+    }
+    __syncwarp();
+    mine[0] = lane < (unsigned)filled ? tab[lane] : 0;
+    mine[1] = 32 + lane < (unsigned)filled ? tab[32 + lane] : 0;
+    warp_sort64_desc(mine[0], mine[1]);
+    t.a = mine[0];
+    t.b = mine[1];
+    return t;
 }
 
 struct OutRef {
@@ -444,8 +503,7 @@ __device__ void warp_query(const PathsRef& P, int32_t v, int64_t qi, unsigned lo
     }
     if (!ok) flag_status(status, ST_HASH_FULL);
     __syncwarp();
-    WarpTopK t;
-    for (uint32_t base = 0; base < ns; base += 32) t.offer(slot_score(tab[base + lane]), o.k);
+    WarpTopK t = warp_table_topk(tab, ns, o.k);
     write_list(t, o, qi);
     __syncwarp();
 }

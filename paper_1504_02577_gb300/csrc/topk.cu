@@ -508,6 +508,170 @@ __device__ void warp_query(const PathsRef& P, int32_t v, int64_t qi, unsigned lo
     __syncwarp();
 }
 
+
+// ------------------------------------------------- narrow warp tier ---
+// When every vertex id fits in 32 - cb bits and every warp-tier count in cb
+// bits, a slot is one 32-bit word key << cb | count: half the table, 32-bit
+// atomics, and 32-bit keys to sort.
+constexpr uint32_t EMPTY32 = 0xffffffffu;
+
+__device__ __forceinline__ bool hash_add32_conv(uint32_t* tab, uint32_t nslots, uint32_t key, int cb, bool active) {
+    uint32_t s = active ? hslot(key, nslots) : 0;
+    bool pending = active, ok = true;
+    uint32_t probes = 0;
+    const uint32_t mine_word = (key << cb) | 1u;
+    while (__any_sync(0xffffffffu, pending)) {
+        if (pending) {
+            uint32_t cur = tab[s];
+            bool mine = cur != EMPTY32 && (cur >> cb) == key;
+            if (cur == EMPTY32) {
+                uint32_t prev = atomicCAS(&tab[s], EMPTY32, mine_word);
+                if (prev == EMPTY32) pending = false;
+                else mine = (prev >> cb) == key;
+            }
+            if (mine) {
+                atomicAdd(&tab[s], 1u);
+                pending = false;
+            }
+            if (pending) {
+                s = (s + 1 == nslots) ? 0 : s + 1;
+                if (++probes >= nslots) {
+                    pending = false;
+                    ok = false;
+                }
+            }
+        }
+    }
+    return ok;
+}
+
+template <int STRIDE>
+__device__ __forceinline__ bool insert_path32(const PathsRef& P, int32_t r, int32_t v, uint32_t* tab, uint32_t nslots,
+                                              int cb, bool active) {
+    active &= (uint32_t)r < (uint64_t)P.R;
+    int32_t x[STRIDE];
+    const int4* src = (const int4*)(P.rows + (int64_t)(active ? r : 0) * STRIDE);
+#pragma unroll
+    for (int k = 0; k < STRIDE / 4; ++k) {
+        int4 q = active ? __ldg(src + k) : make_int4(-1, -1, -1, -1);
+        x[4 * k] = q.x; x[4 * k + 1] = q.y; x[4 * k + 2] = q.z; x[4 * k + 3] = q.w;
+    }
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < STRIDE; ++j) {
+        bool take = active && j < P.L && x[j] != v;
+#pragma unroll
+        for (int i = 0; i < j; ++i) take &= (x[i] != x[j]);
+        if (__any_sync(0xffffffffu, take)) ok &= hash_add32_conv(tab, nslots, (uint32_t)x[j], cb, take);
+    }
+    return ok;
+}
+
+// sort key of a narrow slot: count high, then ascending id (0 = empty)
+__device__ __forceinline__ uint32_t slot_score32(uint32_t w, int cb) {
+    if (w == EMPTY32) return 0;
+    const uint32_t kb = 32 - cb, kmask = (1u << kb) - 1u;   // 1 <= cb <= 16
+    return ((w & ((1u << cb) - 1u)) << kb) | (kmask - (w >> cb));
+}
+
+__device__ __forceinline__ uint64_t widen_score(uint32_t sc, int cb) {
+    if (!sc) return 0;
+    const uint32_t kb = 32 - cb, kmask = (1u << kb) - 1u;
+    const uint32_t cnt = sc >> kb, id = kmask - (sc & kmask);
+    return ((uint64_t)cnt << 32) | (uint64_t)(0xffffffffu - id);
+}
+
+// bitonic sort, descending, of the 64 32-bit keys (a: rank lane, b: rank 32 + lane)
+__device__ __forceinline__ void warp_sort64_desc32(uint32_t& a, uint32_t& b) {
+    const unsigned lane = threadIdx.x & 31;
+#pragma unroll
+    for (int kk = 2; kk <= 64; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            if (j == 32) {
+                const bool desc = (lane & kk) == 0;
+                const uint32_t hi = max(a, b), lo = min(a, b);
+                a = desc ? hi : lo;
+                b = desc ? lo : hi;
+            } else {
+                const uint32_t pa = __shfl_xor_sync(0xffffffffu, a, j);
+                const uint32_t pb = __shfl_xor_sync(0xffffffffu, b, j);
+                const bool lower = (lane & j) == 0;
+                const bool da = kk == 64 || (lane & kk) == 0;
+                const bool db = kk == 64 || ((32 + lane) & kk) == 0;
+                a = (lower == da) ? max(a, pa) : min(a, pa);
+                b = (lower == db) ? max(b, pb) : min(b, pb);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t warp_sort32_desc32(uint32_t a) {
+    const unsigned lane = threadIdx.x & 31;
+#pragma unroll
+    for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            const uint32_t pa = __shfl_xor_sync(0xffffffffu, a, j);
+            const bool lower = (lane & j) == 0;
+            const bool da = kk == 32 || (lane & kk) == 0;
+            a = (lower == da) ? max(a, pa) : min(a, pa);
+        }
+    }
+    return a;
+}
+
+// returns false (and does nothing) when the query has 2^cb - 1 or more paths:
+// its counts might not fit, or a slot might read as empty
+template <int STRIDE>
+__device__ bool warp_query32(const PathsRef& P, int32_t v, int64_t qi, uint32_t* tab, const OutRef& o, int cb,
+                             uint32_t* status) {
+    const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    const int64_t a = P.off[v], b = P.off[v + 1];
+    if (b - a >= (int64_t(1) << cb) - 1) return false;
+    const uint32_t ns = table_size((b - a) * (P.L - 1), 64, WSLOTS);
+    for (uint32_t s = lane; s < ns; s += 32) tab[s] = EMPTY32;
+    __syncwarp();
+    bool ok = true;
+    for (int64_t base = a; base < b; base += 32) {                   // warp-uniform trip count
+        const int64_t e = base + lane;
+        const bool act = e < b;
+        ok &= insert_path32<STRIDE>(P, act ? P.pid[e] : -1, v, tab, ns, cb, act);
+    }
+    if (!ok) flag_status(status, ST_HASH_FULL);
+    __syncwarp();
+    // top-k: compact the filled slots in place (at most 64: one sort), else offer them
+    int filled = 0;
+    for (uint32_t base = 0; base < ns; base += 32)
+        filled += __popc(__ballot_sync(0xffffffffu, tab[base + lane] != EMPTY32));
+    WarpTopK t;
+    if (filled > 64) {
+        for (uint32_t base = 0; base < ns; base += 32) t.offer(widen_score(slot_score32(tab[base + lane], cb), cb), o.k);
+    } else {
+        int pos = 0;
+        for (uint32_t base = 0; base < ns; base += 32) {
+            const uint32_t sc = slot_score32(tab[base + lane], cb);
+            const unsigned m = __ballot_sync(0xffffffffu, sc != 0);
+            if (sc) tab[pos + __popc(m & lt)] = sc;   // every lane read its slot before the ballot
+            pos += __popc(m);
+        }
+        __syncwarp();
+        uint32_t ka = lane < (unsigned)filled ? tab[lane] : 0u;
+        uint32_t kb2 = 32 + lane < (unsigned)filled ? tab[32 + lane] : 0u;
+        if (filled <= 32) {
+            ka = warp_sort32_desc32(ka);
+            kb2 = 0;
+        } else {
+            warp_sort64_desc32(ka, kb2);
+        }
+        t.a = widen_score(ka, cb);
+        t.b = widen_score(kb2, cb);
+    }
+    write_list(t, o, qi);
+    __syncwarp();
+    return true;
+}
+
 struct PersistArgs {
     PathsRef P;
     const int32_t* queries;
@@ -515,6 +679,7 @@ struct PersistArgs {
     OutRef o;
     uint32_t cta_slots;
     uint32_t* status;
+    int narrow_cb;   // > 0: warp tier on 32-bit slots with this many count bits
 };
 
 template <int STRIDE>
@@ -546,7 +711,8 @@ __global__ void __launch_bounds__(1024, 1) persistent_kernel(PersistArgs A) {
         for (int j = it; j < end; ++j) {
             int64_t qi = A.tiers.list[0][j];
             int32_t v = A.queries ? A.queries[qi] : (int32_t)qi;
-            warp_query<STRIDE>(A.P, v, qi, wt, A.o, A.status);
+            if (!A.narrow_cb || !warp_query32<STRIDE>(A.P, v, qi, (uint32_t*)wt, A.o, A.narrow_cb, A.status))
+                warp_query<STRIDE>(A.P, v, qi, wt, A.o, A.status);
         }
     }
 }
@@ -1132,7 +1298,12 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
         lane_kernel<<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(P, queries, lists + 3 * q, counts, 5, o);
         ctx->launches++;
     }
-    PersistArgs A{P, queries, tiers, o, sh.cta_slots, ctx->d_status};
+    // narrow warp tier: ids below 2^(32 - cb) with cb bits for the largest
+    // warp-tier count (a count never exceeds the query's number of paths)
+    int cb = 1;
+    while ((1 << cb) <= WCAP / std::max(1, P.L - 1)) ++cb;
+    const int narrow_cb = (cb <= 16 && ix->n <= (int64_t(1) << (32 - cb))) ? cb : 0;   // ids < 2^(32-cb)
+    PersistArgs A{P, queries, tiers, o, sh.cta_slots, ctx->d_status, narrow_cb};
     unsigned blocks = (unsigned)(ctx->num_sms * sh.blocks_per_sm);
     if (p->stride == 8) persistent_kernel<8><<<blocks, sh.threads, smem, s>>>(A);
     else if (p->stride == 16) persistent_kernel<16><<<blocks, sh.threads, smem, s>>>(A);

@@ -19,6 +19,7 @@
 // from device counters (CTA-tier queries first, then warp-tier queries in
 // chunks), so skewed |P_v| does not leave SMs idle.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -289,15 +290,44 @@ __device__ __forceinline__ bool row_has(const int32_t (&r)[8], int32_t u) {
     return h;
 }
 
-__global__ void __launch_bounds__(256) lane_kernel(PathsRef P, const int32_t* __restrict__ queries,
+// Scores: count high, ascending id low. NARROW packs them in 32 bits (ids
+// below 2^29: counts here are at most LANE_NP < 8), else in 64.
+template <bool NARROW>
+struct LaneScore {
+    using T = typename std::conditional<NARROW, uint32_t, uint64_t>::type;
+    static __device__ __forceinline__ T make(uint32_t c, int32_t u) {
+        if (NARROW) return (T)((c << 29) | ((1u << 29) - 1u - (uint32_t)u));
+        return (T)(((uint64_t)c << 32) | (uint64_t)(0xffffffffu - (uint32_t)u));
+    }
+    static __device__ __forceinline__ int32_t id(T s) {
+        if (NARROW) return (int32_t)((1u << 29) - 1u - ((uint32_t)s & ((1u << 29) - 1u)));
+        return (int32_t)(0xffffffffu - (uint32_t)s);
+    }
+    static __device__ __forceinline__ uint32_t count(T s) { return NARROW ? (uint32_t)s >> 29 : (uint32_t)((uint64_t)s >> 32); }
+};
+
+template <bool NARROW>
+__global__ void __launch_bounds__(256, NARROW ? 3 : 2) lane_kernel(PathsRef P, const int32_t* __restrict__ queries,
                                                    const int32_t* __restrict__ list, const int* __restrict__ count,
                                                    int slot, OutRef o) {
+    using LS = LaneScore<NARROW>;
+    using T = typename LS::T;
     const int n = count[slot];
-    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x) {
+    const int stride = gridDim.x * blockDim.x;
+    int it = blockIdx.x * blockDim.x + threadIdx.x;
+    // the next query's vertex and path range are fetched one query ahead
+    int32_t nv = 0;
+    int64_t na = 0, nb = 0;
+    if (it < n) {
+        nv = queries ? queries[list[it]] : list[it];
+        na = P.off[nv];
+        nb = P.off[nv + 1];
+    }
+    for (; it < n; it += stride) {
         const int64_t qi = list[it];
-        const int32_t v = queries ? queries[qi] : (int32_t)qi;
-        const int64_t a = P.off[v];
-        const int np = (int)(P.off[v + 1] - a);
+        const int32_t v = nv;
+        const int64_t a = na;
+        const int np = (int)(nb - na);
         int32_t row[LANE_NP][8];
 #pragma unroll
         for (int i = 0; i < LANE_NP; ++i) {
@@ -316,7 +346,12 @@ __global__ void __launch_bounds__(256) lane_kernel(PathsRef P, const int32_t* __
             for (int j = 0; j < 8; ++j)
                 if (j >= P.L) row[i][j] = -1;
         }
-        uint64_t best[LANE_K];
+        if (it + stride < n) {
+            nv = queries ? queries[list[it + stride]] : list[it + stride];
+            na = P.off[nv];
+            nb = P.off[nv + 1];
+        }
+        T best[LANE_K];
 #pragma unroll
         for (int t = 0; t < LANE_K; ++t) best[t] = 0;
 #pragma unroll
@@ -333,12 +368,12 @@ __global__ void __launch_bounds__(256) lane_kernel(PathsRef P, const int32_t* __
                     uint32_t c = 1;
 #pragma unroll
                     for (int ii = i + 1; ii < LANE_NP; ++ii) c += row_has(row[ii], u) ? 1u : 0u;
-                    uint64_t sc = ((uint64_t)c << 32) | (uint64_t)(0xffffffffu - (uint32_t)u);
+                    T sc = LS::make(c, u);
                     // sorted insertion (descending)
 #pragma unroll
                     for (int t = 0; t < LANE_K; ++t) {
-                        uint64_t hi = best[t] > sc ? best[t] : sc;
-                        uint64_t lo = best[t] > sc ? sc : best[t];
+                        T hi = best[t] > sc ? best[t] : sc;
+                        T lo = best[t] > sc ? sc : best[t];
                         best[t] = hi;
                         sc = lo;
                     }
@@ -348,9 +383,9 @@ __global__ void __launch_bounds__(256) lane_kernel(PathsRef P, const int32_t* __
 #pragma unroll
         for (int t = 0; t < LANE_K; ++t) {
             if (t < o.k) {
-                uint64_t sc = best[t];
-                if (o.ids) o.ids[qi * o.k + t] = sc ? (int32_t)(0xffffffffu - (uint32_t)sc) : -1;
-                o.cnt[qi * o.k + t] = (uint32_t)(sc >> 32);
+                const T sc = best[t];
+                if (o.ids) o.ids[qi * o.k + t] = sc ? LS::id(sc) : -1;
+                o.cnt[qi * o.k + t] = LS::count(sc);
             }
         }
     }
@@ -1295,7 +1330,10 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
     classify_kernel<<<(unsigned)ceil_div(q, 256), 256, 0, s>>>(queries, q, P, ccap, lane_ok, tiers, o, ctx->d_status);
     ctx->launches++;
     if (lane_ok) {
-        lane_kernel<<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(P, queries, lists + 3 * q, counts, 5, o);
+        if (ix->n <= (int64_t(1) << 29))
+            lane_kernel<true><<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(P, queries, lists + 3 * q, counts, 5, o);
+        else
+            lane_kernel<false><<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(P, queries, lists + 3 * q, counts, 5, o);
         ctx->launches++;
     }
     // narrow warp tier: ids below 2^(32 - cb) with cb bits for the largest

@@ -491,6 +491,84 @@ __global__ void classify_kernel(const int32_t* __restrict__ queries, int64_t q, 
     }
 }
 
+// Top-k of a CTA's shared table (every thread of the CTA calls it; ends with
+// a barrier). The k-th largest count c* comes from a histogram of the counts
+// (counts above 62 share bin 63); only the slots with count >= c* are
+// compacted, and when there are at most 64 of them one warp sorts them.
+// Otherwise every slot is offered to per-warp lists that are then merged.
+__device__ void cta_table_topk(const unsigned long long* tab, uint32_t nslots, unsigned long long* lists,
+                               const OutRef& o, int64_t qi) {
+    __shared__ unsigned hist[64];
+    __shared__ int s_cstar, s_m;
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
+    const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) hist[i] = 0;
+    if (threadIdx.x == 0) s_m = 0;
+    __syncthreads();
+    for (uint32_t base = (uint32_t)w * 32; base < nslots; base += (uint32_t)nw * 32) {   // warp-uniform
+        const uint32_t s = base + lane;
+        const unsigned long long x = s < nslots ? tab[s] : EMPTY;
+        const uint32_t c = x == EMPTY ? 64u : min((uint32_t)x, 63u);
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        if (c < 64 && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&hist[c], (unsigned)__popc(peers));
+    }
+    __syncthreads();
+    if (w == 0) {
+        // S(c) = number of slots with count >= c, for c = lane and 32 + lane
+        uint32_t hi = hist[32 + lane], lo = hist[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t yh = __shfl_down_sync(0xffffffffu, hi, d), yl = __shfl_down_sync(0xffffffffu, lo, d);
+            if (lane + d < 32) {
+                hi += yh;
+                lo += yl;
+            }
+        }
+        lo += __shfl_sync(0xffffffffu, hi, 0);
+        const unsigned mh = __ballot_sync(0xffffffffu, hi >= (uint32_t)o.k);
+        const unsigned ml = __ballot_sync(0xffffffffu, lo >= (uint32_t)o.k);
+        int cstar = 1;   // fewer than k filled slots: take them all
+        if (mh) cstar = 32 + 31 - __clz(mh);
+        else if (ml) cstar = max(1, 31 - __clz(ml));
+        if (lane == 0) s_cstar = cstar;
+    }
+    __syncthreads();
+    const uint32_t cstar = (uint32_t)s_cstar;
+    for (uint32_t base = (uint32_t)w * 32; base < nslots; base += (uint32_t)nw * 32) {   // warp-uniform
+        const uint32_t s = base + lane;
+        const unsigned long long x = s < nslots ? tab[s] : EMPTY;
+        const bool pass = x != EMPTY && (uint32_t)x >= cstar;
+        const unsigned m = __ballot_sync(0xffffffffu, pass);
+        if (!m) continue;
+        int at = 0;
+        if (lane == 0) at = atomicAdd(&s_m, __popc(m));
+        at = __shfl_sync(0xffffffffu, at, 0) + __popc(m & lt);
+        if (pass && at < 64) lists[at] = slot_score(x);
+    }
+    __syncthreads();
+    const int m = s_m;
+    if (m <= 64) {
+        if (w == 0) {
+            WarpTopK t;
+            t.a = lane < (unsigned)m ? lists[lane] : 0;
+            t.b = 32 + lane < (unsigned)m ? lists[32 + lane] : 0;
+            warp_sort64_desc(t.a, t.b);
+            write_list(t, o, qi);
+        }
+        __syncthreads();
+        return;
+    }
+    __syncthreads();   // the list area is reused below
+    WarpTopK t;
+    for (uint32_t base = (uint32_t)w * 32; base < nslots; base += (uint32_t)nw * 32) {
+        uint32_t s = base + lane;
+        t.offer(s < nslots ? slot_score(tab[s]) : 0, o.k);
+    }
+    cta_merge(t, lists);
+    if (w == 0) write_list(t, o, qi);
+    __syncthreads();
+}
+
 // CTA-wide: count one query into the shared table and write its top-k
 template <int STRIDE>
 __device__ void cta_query(const PathsRef& P, int32_t v, int64_t qi, unsigned long long* tab, uint32_t max_slots,
@@ -507,19 +585,7 @@ __device__ void cta_query(const PathsRef& P, int32_t v, int64_t qi, unsigned lon
     }
     if (!ok) flag_status(status, ST_HASH_FULL);
     __syncthreads();
-    WarpTopK t;
-    int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
-    unsigned lane = threadIdx.x & 31;
-    for (uint32_t base = (uint32_t)w * 32; base < nslots; base += (uint32_t)nw * 32) {
-        uint32_t s = base + lane;
-        t.offer(s < nslots ? slot_score(tab[s]) : 0, o.k);
-    }
-    // merge warp lists through shared memory (reuses the list area)
-    cta_merge(t, lists);
-    if (w == 0) {
-        write_list(t, o, qi);
-    }
-    __syncthreads();
+    cta_table_topk(tab, nslots, lists, o, qi);
 }
 
 template <int STRIDE>

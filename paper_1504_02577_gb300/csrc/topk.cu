@@ -450,14 +450,155 @@ __device__ __forceinline__ bool insert_path_conv(const PathsRef& P, int32_t r, i
     return ok;
 }
 
+
+// --------------------------------------------------------- group tiers ---
+// Queries with 7..16 paths (T <= 7, ids below 2^GROUP_UB): a group of G = 8
+// or 16 lanes per query, lane j holding path j of P_v in 8 registers, so a
+// warp serves 32/G queries at once with no table. Each entry u != v becomes
+// the key u << 4 | j; the G*8 keys are bitonic-sorted across the group, the
+// number of distinct rows in each run of equal u is its count (a path that
+// visits u twice gives two equal keys and counts once), and the run ends
+// carry the scores count << GROUP_UB | reversed id, sorted again, descending.
+constexpr int GROUP_UB = 27;
+
+// bitonic sort of the 8*G keys of a group (element gl*8 + r is register r of
+// group lane gl); ascending or descending
+template <int G, bool ASC>
+__device__ __forceinline__ void group_sort(uint32_t (&x)[8], unsigned gl) {
+#pragma unroll
+    for (int kk = 2; kk <= 8 * G; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            if (j >= 8) {
+                const unsigned lj = (unsigned)(j >> 3);
+                const bool lower = (gl & lj) == 0;
+                const bool up = kk == 8 * G || ((gl * 8) & (unsigned)kk) == 0;
+                const bool take_min = (lower == up) == ASC;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const uint32_t p = __shfl_xor_sync(0xffffffffu, x[r], lj);
+                    x[r] = take_min ? min(x[r], p) : max(x[r], p);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    if (r & j) continue;
+                    const unsigned e = gl * 8 + (unsigned)r;
+                    const bool up = kk == 8 * G || (e & (unsigned)kk) == 0;
+                    const uint32_t lo = min(x[r], x[r + j]), hi = max(x[r], x[r + j]);
+                    x[r] = (up == ASC) ? lo : hi;
+                    x[r + j] = (up == ASC) ? hi : lo;
+                }
+            }
+        }
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) group_kernel(PathsRef P, const int32_t* __restrict__ queries,
+                                                    const int32_t* __restrict__ list, const int* __restrict__ count,
+                                                    int slot, OutRef o) {
+    const int n = count[slot];
+    const unsigned lane = threadIdx.x & 31, gl = lane & (G - 1);
+    const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
+    constexpr uint32_t UMASK = (1u << GROUP_UB) - 1u;
+    for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;; it += ngroups) {
+        const bool active = it < n;
+        if (!__any_sync(0xffffffffu, active)) break;   // warp-uniform: the whole warp shuffles together
+        int64_t qi = 0;
+        int32_t v = -1;
+        int np = 0;
+        int64_t a = 0;
+        if (active) {
+            qi = list[it];
+            v = queries ? queries[qi] : (int32_t)qi;
+            a = P.off[v];
+            np = (int)(P.off[v + 1] - a);
+        }
+        uint32_t x[8];
+        {
+            const int32_t r = (int)gl < np ? P.pid[a + gl] : -1;
+            int4 q0 = make_int4(-1, -1, -1, -1), q1 = q0;
+            if (r >= 0 && (int64_t)r < P.R) {
+                const int4* src = (const int4*)(P.rows + (int64_t)r * 8);
+                q0 = __ldg(src);
+                q1 = __ldg(src + 1);
+            }
+            const int32_t y[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                const bool ok = p < P.L && y[p] >= 0 && y[p] != v;
+                x[p] = ok ? ((uint32_t)y[p] << 4) | gl : 0xffffffffu;
+            }
+        }
+        group_sort<G, true>(x, gl);
+        // run ends and the number of distinct rows per run of equal u
+        const uint32_t prev7 = __shfl_up_sync(0xffffffffu, x[7], 1);
+        const uint32_t next0 = __shfl_down_sync(0xffffffffu, x[0], 1);
+        uint32_t c[8];
+        unsigned lane_reset = 0;   // bit r: element r starts a new u
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const uint32_t pk = r ? x[r - 1] : (gl ? prev7 : 0xfffffffeu);
+            const bool new_u = (x[r] >> 4) != (pk >> 4) || (r == 0 && gl == 0);
+            const uint32_t d = (x[r] != pk || (r == 0 && gl == 0)) ? 1u : 0u;
+            c[r] = (r == 0 || new_u) ? d : c[r - 1] + d;
+            if (new_u) lane_reset |= 1u << r;
+        }
+        // carry the running count across lanes until a lane that starts a new u
+        uint32_t carry = 0;   // distinct rows of the run that continues into this lane
+        {
+            // (total after the last reset, whether the lane resets) scanned over the group
+            uint32_t t = c[7];
+            bool f = lane_reset != 0;
+#pragma unroll
+            for (int d = 1; d < G; d <<= 1) {
+                const uint32_t pt = __shfl_up_sync(0xffffffffu, t, d);
+                const bool pf = __shfl_up_sync(0xffffffffu, f ? 1u : 0u, d) != 0;
+                if (gl >= (unsigned)d && !f) {
+                    t += pt;
+                    f = pf;
+                }
+            }
+            // exclusive: the inclusive value of the previous lane
+            const uint32_t pt = __shfl_up_sync(0xffffffffu, t, 1);
+            carry = gl ? pt : 0;
+        }
+        uint32_t sc[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const uint32_t cnt = ((lane_reset & ((2u << r) - 1u)) == 0) ? c[r] + carry : c[r];
+            const uint32_t nk = r < 7 ? x[r + 1] : (gl + 1 < (unsigned)G ? next0 : 0xffffffffu);
+            const bool last = (x[r] >> 4) != (nk >> 4) || (r == 7 && gl + 1 == (unsigned)G);
+            const uint32_t u = x[r] >> 4;
+            sc[r] = (last && x[r] != 0xffffffffu) ? (cnt << GROUP_UB) | (UMASK - u) : 0u;
+        }
+        group_sort<G, false>(sc, gl);
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int e = (int)gl * 8 + r;
+                if (e < o.k) {
+                    if (o.ids) o.ids[qi * o.k + e] = sc[r] ? (int32_t)(UMASK - (sc[r] & UMASK)) : -1;
+                    o.cnt[qi * o.k + e] = sc[r] >> GROUP_UB;
+                }
+            }
+            for (int e = 8 * G + (int)gl; e < o.k; e += G) {   // k beyond the group's 8G ranks: padding
+                if (o.ids) o.ids[qi * o.k + e] = -1;
+                o.cnt[qi * o.k + e] = 0;
+            }
+        }
+    }
+}
+
 struct Tiers {
-    int32_t* list[4];    // query indices per tier: warp, CTA, global, lane
-    int* count;          // [0..2] warp/CTA/global sizes, [3..4] fetch counters (warp, CTA), [5] lane size
+    int32_t* list[6];    // query indices per tier: warp, CTA, global, lane, group of 8, group of 16
+    int* count;          // [0..2] warp/CTA/global sizes, [3..4] fetch counters (warp, CTA), [5..7] lane, g8, g16 sizes
 };
 
 // classification: pads trivially empty queries and sorts the rest into tiers
 __global__ void classify_kernel(const int32_t* __restrict__ queries, int64_t q, PathsRef P, int64_t ccap,
-                                bool lane_ok, Tiers tiers, OutRef o, uint32_t* status) {
+                                bool lane_ok, bool group_ok, Tiers tiers, OutRef o, uint32_t* status) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned lane = threadIdx.x & 31;
     int tier = -1;
@@ -470,7 +611,12 @@ __global__ void classify_kernel(const int32_t* __restrict__ queries, int64_t q, 
             int64_t np = P.off[v + 1] - P.off[v];
             int64_t cap = np * (P.L - 1);
             if (cap > P.n - 1) cap = P.n - 1;
-            if (cap > 0) tier = (lane_ok && np <= LANE_NP) ? 3 : (cap <= WCAP ? 0 : (cap <= ccap ? 1 : 2));
+            if (cap > 0) {
+                if (lane_ok && np <= LANE_NP) tier = 3;
+                else if (group_ok && np <= 8) tier = 4;
+                else if (group_ok && np <= 16) tier = 5;
+                else tier = cap <= WCAP ? 0 : (cap <= ccap ? 1 : 2);
+            }
         }
         if (tier < 0) {
             for (int r = 0; r < o.k; ++r) {
@@ -480,12 +626,12 @@ __global__ void classify_kernel(const int32_t* __restrict__ queries, int64_t q, 
         }
     }
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < 6; ++t) {
         unsigned m = __ballot_sync(0xffffffffu, tier == t);
         if (!m) continue;
         int leader = __ffs(m) - 1;
         int base = 0;
-        if ((int)lane == leader) base = atomicAdd(&tiers.count[t == 3 ? 5 : t], __popc(m));
+        if ((int)lane == leader) base = atomicAdd(&tiers.count[t >= 3 ? t + 2 : t], __popc(m));
         base = __shfl_sync(0xffffffffu, base, leader);
         if (tier == t) tiers.list[t][base + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
     }
@@ -1385,15 +1531,17 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
 
     int32_t* lists = nullptr;
     int* counts = nullptr;
-    if ((st = dev_alloc(ctx, (void**)&lists, sizeof(int32_t) * 4 * (size_t)q)) ||
+    if ((st = dev_alloc(ctx, (void**)&lists, sizeof(int32_t) * 6 * (size_t)q)) ||
         (st = dev_alloc(ctx, (void**)&counts, sizeof(int) * 8))) {
         dev_free(ctx, lists);
         return st;
     }
-    Tiers tiers{{lists, lists + q, lists + 2 * q, lists + 3 * q}, counts};
+    Tiers tiers{{lists, lists + q, lists + 2 * q, lists + 3 * q, lists + 4 * q, lists + 5 * q}, counts};
+    const bool group_ok = p->stride == 8 && ix->n <= (int64_t(1) << GROUP_UB);
     const bool lane_ok = p->stride == 8 && k <= LANE_K;
     PCK(ctx, cudaMemsetAsync(counts, 0, sizeof(int) * 8, s));
-    classify_kernel<<<(unsigned)ceil_div(q, 256), 256, 0, s>>>(queries, q, P, ccap, lane_ok, tiers, o, ctx->d_status);
+    classify_kernel<<<(unsigned)ceil_div(q, 256), 256, 0, s>>>(queries, q, P, ccap, lane_ok, group_ok, tiers, o,
+                                                                ctx->d_status);
     ctx->launches++;
     if (lane_ok) {
         if (ix->n <= (int64_t(1) << 29))
@@ -1401,6 +1549,11 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
         else
             lane_kernel<false><<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(P, queries, lists + 3 * q, counts, 5, o);
         ctx->launches++;
+    }
+    if (group_ok) {
+        group_kernel<8><<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(P, queries, lists + 4 * q, counts, 6, o);
+        group_kernel<16><<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(P, queries, lists + 5 * q, counts, 7, o);
+        ctx->launches += 2;
     }
     // narrow warp tier: ids below 2^(32 - cb) with cb bits for the largest
     // warp-tier count (a count never exceeds the query's number of paths)

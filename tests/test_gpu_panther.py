@@ -263,6 +263,22 @@ def test_topk_global_tier_hubs(pk):
     assert np.array_equal(out["cnt"], rcnt)
 
 
+@pytest.mark.parametrize("k", [1, 10, 40])
+def test_topk_group_tiers(pk, k):
+    # about 12 paths per vertex: most queries have 7..16 paths (the sort-based
+    # tiers of 8 and 16 lanes per query); low-degree cycles make paths revisit
+    # vertices, so equal keys inside one path must count once
+    g = synth.chung_lu(5000, 6, 2.5, ("uniform", 1, 3), seed=11)
+    R, T = 10_000, 5
+    out = _run(pk, g, 12, R, T, pk.MODE_ALIAS, k=k)
+    o = oracle.Oracle(g.n, oracle.sample_paths(g, 12, R, T, oracle.ALIAS))
+    sizes = np.diff(o.off)
+    assert ((sizes > 6) & (sizes <= 8)).sum() > 500 and ((sizes > 8) & (sizes <= 16)).sum() > 1000
+    rid, rcnt = o.topk_many(np.arange(g.n, dtype=np.int32), k)
+    assert np.array_equal(out["ids"], rid)
+    assert np.array_equal(out["cnt"], rcnt)
+
+
 def test_topk_hub_threshold_retry(pk):
     # A 30,000-leaf star whose centre is a hub query: its first-round filter
     # (candidates u with |P_u| >= 255) keeps only the twelve secondary hubs,

@@ -452,14 +452,16 @@ __device__ __forceinline__ bool insert_path_conv(const PathsRef& P, int32_t r, i
 
 
 // --------------------------------------------------------- group tiers ---
-// Queries with 7..16 paths (T <= 7, ids below 2^GROUP_UB): a group of G = 8
-// or 16 lanes per query, lane j holding path j of P_v in 8 registers, so a
-// warp serves 32/G queries at once with no table. Each entry u != v becomes
-// the key u << 4 | j; the G*8 keys are bitonic-sorted across the group, the
-// number of distinct rows in each run of equal u is its count (a path that
-// visits u twice gives two equal keys and counts once), and the run ends
-// carry the scores count << GROUP_UB | reversed id, sorted again, descending.
-constexpr int GROUP_UB = 27;
+// Queries with 7..32 paths (T <= 7, ids below 2^group_ub(G)): a group of
+// G = 8, 16 or 32 lanes per query, lane j holding path j of P_v in 8
+// registers, so a warp serves 32/G queries at once with no table. Each entry
+// u != v becomes the key u << log2(G) | j; the G*8 keys are bitonic-sorted
+// across the group, the number of distinct rows in each run of equal u is its
+// count (a path that visits u twice gives two equal keys and counts once),
+// and the run ends carry the scores count << group_ub(G) | reversed id,
+// sorted again, descending.
+__host__ __device__ constexpr int group_ub(int G) { return G == 32 ? 26 : 27; }   // count <= G fits above
+__host__ __device__ constexpr int group_rb(int G) { return G == 8 ? 3 : (G == 16 ? 4 : 5); }
 
 // bitonic sort of the 8*G keys of a group (element gl*8 + r is register r of
 // group lane gl); ascending or descending
@@ -501,7 +503,8 @@ __global__ void __launch_bounds__(256) group_kernel(PathsRef P, const int32_t* _
     const int n = count[slot];
     const unsigned lane = threadIdx.x & 31, gl = lane & (G - 1);
     const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
-    constexpr uint32_t UMASK = (1u << GROUP_UB) - 1u;
+    constexpr int UB = group_ub(G), RB = group_rb(G);
+    constexpr uint32_t UMASK = (1u << UB) - 1u;
     for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;; it += ngroups) {
         const bool active = it < n;
         if (!__any_sync(0xffffffffu, active)) break;   // warp-uniform: the whole warp shuffles together
@@ -528,7 +531,7 @@ __global__ void __launch_bounds__(256) group_kernel(PathsRef P, const int32_t* _
 #pragma unroll
             for (int p = 0; p < 8; ++p) {
                 const bool ok = p < P.L && y[p] >= 0 && y[p] != v;
-                x[p] = ok ? ((uint32_t)y[p] << 4) | gl : 0xffffffffu;
+                x[p] = ok ? ((uint32_t)y[p] << RB) | gl : 0xffffffffu;
             }
         }
         group_sort<G, true>(x, gl);
@@ -540,7 +543,7 @@ __global__ void __launch_bounds__(256) group_kernel(PathsRef P, const int32_t* _
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const uint32_t pk = r ? x[r - 1] : (gl ? prev7 : 0xfffffffeu);
-            const bool new_u = (x[r] >> 4) != (pk >> 4) || (r == 0 && gl == 0);
+            const bool new_u = (x[r] >> RB) != (pk >> RB) || (r == 0 && gl == 0);
             const uint32_t d = (x[r] != pk || (r == 0 && gl == 0)) ? 1u : 0u;
             c[r] = (r == 0 || new_u) ? d : c[r - 1] + d;
             if (new_u) lane_reset |= 1u << r;
@@ -569,9 +572,9 @@ __global__ void __launch_bounds__(256) group_kernel(PathsRef P, const int32_t* _
         for (int r = 0; r < 8; ++r) {
             const uint32_t cnt = ((lane_reset & ((2u << r) - 1u)) == 0) ? c[r] + carry : c[r];
             const uint32_t nk = r < 7 ? x[r + 1] : (gl + 1 < (unsigned)G ? next0 : 0xffffffffu);
-            const bool last = (x[r] >> 4) != (nk >> 4) || (r == 7 && gl + 1 == (unsigned)G);
-            const uint32_t u = x[r] >> 4;
-            sc[r] = (last && x[r] != 0xffffffffu) ? (cnt << GROUP_UB) | (UMASK - u) : 0u;
+            const bool last = (x[r] >> RB) != (nk >> RB) || (r == 7 && gl + 1 == (unsigned)G);
+            const uint32_t u = x[r] >> RB;
+            sc[r] = (last && x[r] != 0xffffffffu) ? (cnt << UB) | (UMASK - u) : 0u;
         }
         group_sort<G, false>(sc, gl);
         if (active) {
@@ -580,7 +583,7 @@ __global__ void __launch_bounds__(256) group_kernel(PathsRef P, const int32_t* _
                 const int e = (int)gl * 8 + r;
                 if (e < o.k) {
                     if (o.ids) o.ids[qi * o.k + e] = sc[r] ? (int32_t)(UMASK - (sc[r] & UMASK)) : -1;
-                    o.cnt[qi * o.k + e] = sc[r] >> GROUP_UB;
+                    o.cnt[qi * o.k + e] = sc[r] >> UB;
                 }
             }
             for (int e = 8 * G + (int)gl; e < o.k; e += G) {   // k beyond the group's 8G ranks: padding
@@ -592,13 +595,13 @@ __global__ void __launch_bounds__(256) group_kernel(PathsRef P, const int32_t* _
 }
 
 struct Tiers {
-    int32_t* list[6];    // query indices per tier: warp, CTA, global, lane, group of 8, group of 16
-    int* count;          // [0..2] warp/CTA/global sizes, [3..4] fetch counters (warp, CTA), [5..7] lane, g8, g16 sizes
+    int32_t* list[7];    // query indices per tier: warp, CTA, global, lane, groups of 8, 16, 32
+    int* count;          // [0..2] warp/CTA/global sizes, [3..4] fetch counters (warp, CTA), [5..8] lane, g8/16/32 sizes
 };
 
 // classification: pads trivially empty queries and sorts the rest into tiers
 __global__ void classify_kernel(const int32_t* __restrict__ queries, int64_t q, PathsRef P, int64_t ccap,
-                                bool lane_ok, bool group_ok, Tiers tiers, OutRef o, uint32_t* status) {
+                                bool lane_ok, int group_max, Tiers tiers, OutRef o, uint32_t* status) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned lane = threadIdx.x & 31;
     int tier = -1;
@@ -613,8 +616,9 @@ __global__ void classify_kernel(const int32_t* __restrict__ queries, int64_t q, 
             if (cap > P.n - 1) cap = P.n - 1;
             if (cap > 0) {
                 if (lane_ok && np <= LANE_NP) tier = 3;
-                else if (group_ok && np <= 8) tier = 4;
-                else if (group_ok && np <= 16) tier = 5;
+                else if (np <= 8 && np <= group_max) tier = 4;
+                else if (np <= 16 && np <= group_max) tier = 5;
+                else if (np <= 32 && np <= group_max) tier = 6;
                 else tier = cap <= WCAP ? 0 : (cap <= ccap ? 1 : 2);
             }
         }
@@ -626,7 +630,7 @@ __global__ void classify_kernel(const int32_t* __restrict__ queries, int64_t q, 
         }
     }
 #pragma unroll
-    for (int t = 0; t < 6; ++t) {
+    for (int t = 0; t < 7; ++t) {
         unsigned m = __ballot_sync(0xffffffffu, tier == t);
         if (!m) continue;
         int leader = __ffs(m) - 1;
@@ -1531,16 +1535,19 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
 
     int32_t* lists = nullptr;
     int* counts = nullptr;
-    if ((st = dev_alloc(ctx, (void**)&lists, sizeof(int32_t) * 6 * (size_t)q)) ||
-        (st = dev_alloc(ctx, (void**)&counts, sizeof(int) * 8))) {
+    if ((st = dev_alloc(ctx, (void**)&lists, sizeof(int32_t) * 7 * (size_t)q)) ||
+        (st = dev_alloc(ctx, (void**)&counts, sizeof(int) * 16))) {
         dev_free(ctx, lists);
         return st;
     }
-    Tiers tiers{{lists, lists + q, lists + 2 * q, lists + 3 * q, lists + 4 * q, lists + 5 * q}, counts};
-    const bool group_ok = p->stride == 8 && ix->n <= (int64_t(1) << GROUP_UB);
+    Tiers tiers{{lists, lists + q, lists + 2 * q, lists + 3 * q, lists + 4 * q, lists + 5 * q, lists + 6 * q}, counts};
+    // largest |P_v| the group tiers take: ids must fit below 2^group_ub(G)
+    const int group_max = p->stride != 8 ? 0
+                          : ix->n <= (int64_t(1) << group_ub(32)) ? 32
+                          : ix->n <= (int64_t(1) << group_ub(16)) ? 16 : 0;
     const bool lane_ok = p->stride == 8 && k <= LANE_K;
-    PCK(ctx, cudaMemsetAsync(counts, 0, sizeof(int) * 8, s));
-    classify_kernel<<<(unsigned)ceil_div(q, 256), 256, 0, s>>>(queries, q, P, ccap, lane_ok, group_ok, tiers, o,
+    PCK(ctx, cudaMemsetAsync(counts, 0, sizeof(int) * 16, s));
+    classify_kernel<<<(unsigned)ceil_div(q, 256), 256, 0, s>>>(queries, q, P, ccap, lane_ok, group_max, tiers, o,
                                                                 ctx->d_status);
     ctx->launches++;
     if (lane_ok) {
@@ -1550,10 +1557,14 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
             lane_kernel<false><<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(P, queries, lists + 3 * q, counts, 5, o);
         ctx->launches++;
     }
-    if (group_ok) {
+    if (group_max >= 16) {
         group_kernel<8><<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(P, queries, lists + 4 * q, counts, 6, o);
         group_kernel<16><<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(P, queries, lists + 5 * q, counts, 7, o);
         ctx->launches += 2;
+    }
+    if (group_max >= 32) {
+        group_kernel<32><<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(P, queries, lists + 6 * q, counts, 8, o);
+        ctx->launches++;
     }
     // narrow warp tier: ids below 2^(32 - cb) with cb bits for the largest
     // warp-tier count (a count never exceeds the query's number of paths)

@@ -595,13 +595,15 @@ __global__ void __launch_bounds__(256) group_kernel(PathsRef P, const int32_t* _
 }
 
 struct Tiers {
-    int32_t* list[7];    // query indices per tier: warp, CTA, global, lane, groups of 8, 16, 32
-    int* count;          // [0..2] warp/CTA/global sizes, [3..4] fetch counters (warp, CTA), [5..8] lane, g8/16/32 sizes
+    int32_t* list[8];    // query indices per tier: warp, CTA, global, lane, groups of 8, 16, 32, big CTA
+    int* count;          // [0..2] warp/CTA/global sizes, [3..4] fetch counters (warp, CTA), [5..8] lane,
+                         // g8/16/32 sizes; [9..13] the same layout as [0..4] for the big-CTA pass
 };
 
 // classification: pads trivially empty queries and sorts the rest into tiers
 __global__ void classify_kernel(const int32_t* __restrict__ queries, int64_t q, PathsRef P, int64_t ccap,
-                                bool lane_ok, int group_max, Tiers tiers, OutRef o, uint32_t* status) {
+                                int64_t ccap_big, bool lane_ok, int group_max, Tiers tiers, OutRef o,
+                                uint32_t* status) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned lane = threadIdx.x & 31;
     int tier = -1;
@@ -619,7 +621,7 @@ __global__ void classify_kernel(const int32_t* __restrict__ queries, int64_t q, 
                 else if (np <= 8 && np <= group_max) tier = 4;
                 else if (np <= 16 && np <= group_max) tier = 5;
                 else if (np <= 32 && np <= group_max) tier = 6;
-                else tier = cap <= WCAP ? 0 : (cap <= ccap ? 1 : 2);
+                else tier = cap <= WCAP ? 0 : (cap <= ccap ? 1 : (cap <= ccap_big ? 7 : 2));
             }
         }
         if (tier < 0) {
@@ -630,12 +632,12 @@ __global__ void classify_kernel(const int32_t* __restrict__ queries, int64_t q, 
         }
     }
 #pragma unroll
-    for (int t = 0; t < 7; ++t) {
+    for (int t = 0; t < 8; ++t) {
         unsigned m = __ballot_sync(0xffffffffu, tier == t);
         if (!m) continue;
         int leader = __ffs(m) - 1;
         int base = 0;
-        if ((int)lane == leader) base = atomicAdd(&tiers.count[t >= 3 ? t + 2 : t], __popc(m));
+        if ((int)lane == leader) base = atomicAdd(&tiers.count[t < 3 ? t : (t == 7 ? 10 : t + 2)], __popc(m));
         base = __shfl_sync(0xffffffffu, base, leader);
         if (tier == t) tiers.list[t][base + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
     }
@@ -1262,6 +1264,10 @@ uint32_t pow2_at_least(int64_t x) {
 }  // namespace
 
 // ------------------------------------------------------------ host side ---
+constexpr int BIG_T = 1024;
+constexpr uint32_t BIG_SLOTS = 24576;
+constexpr size_t BIG_SMEM = (size_t)BIG_SLOTS * 8 + (size_t)(BIG_T / 32) * KMAX * 8;
+
 struct TopkShape {
     int threads;
     uint32_t cta_slots;
@@ -1504,14 +1510,20 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
     cudaStream_t s = ctx->stream;
     TopkShape sh = topk_shape(ctx);
     const size_t smem = (size_t)sh.cta_slots * 8 + (size_t)(sh.threads / 32) * KMAX * 8;
+    // the attribute is process-wide (contexts of several threads share it):
+    // always the larger of this shape and the big-table pass
+    const size_t attr = std::max(smem, BIG_SMEM);
     panther_status st;
-    if (p->stride == 8) st = set_smem_attr<8>(ctx, smem);
-    else if (p->stride == 16) st = set_smem_attr<16>(ctx, smem);
-    else st = set_smem_attr<32>(ctx, smem);
+    if (p->stride == 8) st = set_smem_attr<8>(ctx, attr);
+    else if (p->stride == 16) st = set_smem_attr<16>(ctx, attr);
+    else st = set_smem_attr<32>(ctx, attr);
     if (st) return st;
     PathsRef P{p->rows, p->R, p->L, ix->off, ix->pid, ix->n, ix->cls};
     OutRef o{ids, cnt, k};
     const int64_t ccap = (int64_t)sh.cta_slots * 7 / 10;
+    // queries above the tuned shape's table but within a 24,576-slot one take a
+    // second persistent pass with one 1,024-thread CTA per SM
+    const int64_t ccap_big = sh.cta_slots < BIG_SLOTS ? (int64_t)BIG_SLOTS * 7 / 10 : ccap;
 
     if (plain) {
         uint32_t gslots = pow2_at_least(2 * ix->n);
@@ -1535,20 +1547,21 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
 
     int32_t* lists = nullptr;
     int* counts = nullptr;
-    if ((st = dev_alloc(ctx, (void**)&lists, sizeof(int32_t) * 7 * (size_t)q)) ||
+    if ((st = dev_alloc(ctx, (void**)&lists, sizeof(int32_t) * 8 * (size_t)q)) ||
         (st = dev_alloc(ctx, (void**)&counts, sizeof(int) * 16))) {
         dev_free(ctx, lists);
         return st;
     }
-    Tiers tiers{{lists, lists + q, lists + 2 * q, lists + 3 * q, lists + 4 * q, lists + 5 * q, lists + 6 * q}, counts};
+    Tiers tiers{{lists, lists + q, lists + 2 * q, lists + 3 * q, lists + 4 * q, lists + 5 * q, lists + 6 * q, lists + 7 * q},
+                counts};
     // largest |P_v| the group tiers take: ids must fit below 2^group_ub(G)
     const int group_max = p->stride != 8 ? 0
                           : ix->n <= (int64_t(1) << group_ub(32)) ? 32
                           : ix->n <= (int64_t(1) << group_ub(16)) ? 16 : 0;
     const bool lane_ok = p->stride == 8 && k <= LANE_K;
     PCK(ctx, cudaMemsetAsync(counts, 0, sizeof(int) * 16, s));
-    classify_kernel<<<(unsigned)ceil_div(q, 256), 256, 0, s>>>(queries, q, P, ccap, lane_ok, group_max, tiers, o,
-                                                                ctx->d_status);
+    classify_kernel<<<(unsigned)ceil_div(q, 256), 256, 0, s>>>(queries, q, P, ccap, ccap_big, lane_ok, group_max,
+                                                                tiers, o, ctx->d_status);
     ctx->launches++;
     if (lane_ok) {
         if (ix->n <= (int64_t(1) << 29))
@@ -1577,6 +1590,16 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
     else if (p->stride == 16) persistent_kernel<16><<<blocks, sh.threads, smem, s>>>(A);
     else persistent_kernel<32><<<blocks, sh.threads, smem, s>>>(A);
     ctx->launches++;
+    if (ccap_big > ccap) {
+        // CTA tier only: its list is tier 7's, its counters start at [9]
+        Tiers big{{lists, lists + 7 * q, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr}, counts + 9};
+        PersistArgs B{P, queries, big, o, BIG_SLOTS, ctx->d_status, 0};
+        const unsigned bb = (unsigned)ctx->num_sms;
+        if (p->stride == 8) persistent_kernel<8><<<bb, BIG_T, BIG_SMEM, s>>>(B);
+        else if (p->stride == 16) persistent_kernel<16><<<bb, BIG_T, BIG_SMEM, s>>>(B);
+        else persistent_kernel<32><<<bb, BIG_T, BIG_SMEM, s>>>(B);
+        ctx->launches++;
+    }
     PCK(ctx, cudaGetLastError());
 
     // global tier: read its size (one synchronisation), then run in rounds

@@ -226,7 +226,7 @@ PANTHER_API panther_status panther_tune_topk(panther_ctx* ctx, const panther_ind
                                              uint32_t* out_counts, int* chosen);
 
 /* Set the batched form's launch shape directly (for example one chosen by
- * panther_tune_topk in an earlier run): threads per CTA in {256, 512, 1024},
+ * panther_tune_topk in an earlier run): threads per CTA in {128, 256, 512, 1024},
  * shared-table slots (a multiple of 32, at least threads/32*512, at most
  * 24,576), CTAs per SM in [1, 8]. Results do not depend on the shape.
  * Errors: EINVAL. */

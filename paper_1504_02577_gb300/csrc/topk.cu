@@ -1719,7 +1719,8 @@ extern "C" panther_status panther_tune_topk(panther_ctx* ctx, const panther_inde
         return set_err(ctx, PANTHER_EINVAL, "bad tuner arguments");
     cudaSetDevice(ctx->device);
     struct Shape { int threads, slots, bps; };
-    const Shape cand[] = {{1024, 24576, 1}, {512, 12288, 2}, {256, 6144, 4}, {256, 4096, 6}, {512, 24576, 1}};
+    const Shape cand[] = {{1024, 24576, 1}, {512, 12288, 2}, {256, 6144, 4}, {256, 4096, 6},
+                          {512, 24576, 1}, {256, 8192, 3}, {128, 3072, 8}, {128, 4096, 6}};
     cudaEvent_t a, b;
     PCK(ctx, cudaEventCreate(&a));
     PCK(ctx, cudaEventCreate(&b));
@@ -1765,7 +1766,7 @@ extern "C" panther_status panther_tune_topk(panther_ctx* ctx, const panther_inde
 
 extern "C" panther_status panther_set_topk_shape(panther_ctx* ctx, int threads, int table_slots, int ctas_per_sm) {
     if (!ctx) return PANTHER_EINVAL;
-    if ((threads != 256 && threads != 512 && threads != 1024) || table_slots % 32 != 0 ||
+    if ((threads != 128 && threads != 256 && threads != 512 && threads != 1024) || table_slots % 32 != 0 ||
         table_slots < threads / 32 * WSLOTS || table_slots > 24576 || ctas_per_sm < 1 || ctas_per_sm > 8)
         return set_err(ctx, PANTHER_EINVAL, "unsupported top-k launch shape");
     ctx->topk_threads = threads;

@@ -116,6 +116,53 @@ struct BlockG {
     }
 };
 
+
+// G lanes of a warp per row (G divides 32), IPT items per lane in blocked
+// order. Every lane of the warp must make the same calls (the shuffles span
+// the warp, each group of G lanes scanning its own row).
+template <int G, int IPT_>
+struct SubG {
+    static constexpr int size = G;
+    static constexpr int IPT = IPT_;
+    __device__ __forceinline__ int rank() const { return threadIdx.x & (G - 1); }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+    __device__ __forceinline__ uint64_t incl_scan(uint64_t v, uint64_t* total) const {
+        const int l = rank();
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) {
+            uint64_t y = __shfl_up_sync(0xffffffffu, v, o, G);
+            if (l >= o) v += y;
+        }
+        *total = __shfl_sync(0xffffffffu, v, G - 1, G);
+        return v;
+    }
+    __device__ __forceinline__ uint64_t sum(uint64_t v) const {
+#pragma unroll
+        for (int o = G / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+        return v;
+    }
+    __device__ __forceinline__ bool any(bool p) const {
+        const unsigned m = __ballot_sync(0xffffffffu, p);
+        const unsigned gbase = (threadIdx.x & 31) & ~(unsigned)(G - 1);
+        return ((G == 32 ? m : (m >> gbase) & ((1u << G) - 1u))) != 0;
+    }
+    // inclusive scan of the group's G*IPT items; returns the total
+    template <int N>
+    __device__ __forceinline__ uint64_t chunk_scan(uint64_t (&v)[N]) const {
+        uint64_t run = 0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            run += v[j];
+            v[j] = run;
+        }
+        uint64_t tot;
+        const uint64_t before = incl_scan(run, &tot) - run;
+#pragma unroll
+        for (int j = 0; j < N; ++j) v[j] += before;
+        return tot;
+    }
+};
+
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z ^= z >> 33;
     z *= 0xff51afd7ed558ccdULL;
@@ -172,22 +219,45 @@ __device__ void row_stats(const G& g, int64_t v, int64_t start, int64_t deg, int
     mx = s > mx ? s : mx;
 }
 
+// rows of SHORT_LO..SHORT_HI entries: 8 lanes per row, 4 entries per lane
+constexpr int64_t SHORT_LO = 17, SHORT_HI = 32;
+
+// Row-pointer checks, and the lists of rows by length: big (above BIG_DEG),
+// short (SHORT_LO..SHORT_HI, at the front of `mid`) and medium (up to
+// BIG_DEG, from the back of `mid`). counts: [0] big, [1] short, [2] medium.
 __global__ void rows_check_kernel(const int64_t* __restrict__ row_ptr, int64_t n, int64_t m,
-                                  int32_t* __restrict__ big, int* __restrict__ nbig, uint32_t* status) {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v > n) return;
-    int64_t a = row_ptr[v];
-    if (v == 0 && a != 0) flag_status(status, ST_GRAPH_BAD);
-    if (v == n) {
-        if (a != m) flag_status(status, ST_GRAPH_BAD);
-        return;
+                                  int32_t* __restrict__ big, int32_t* __restrict__ mid, int* __restrict__ counts,
+                                  uint32_t* status) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    int cls = -1;   // 0 big, 1 short, 2 medium
+    if (v <= n) {
+        const int64_t a = row_ptr[v];
+        if (v == 0 && a != 0) flag_status(status, ST_GRAPH_BAD);
+        if (v == n) {
+            if (a != m) flag_status(status, ST_GRAPH_BAD);
+        } else {
+            const int64_t b = row_ptr[v + 1];
+            if (b < a || a < 0 || b > m) flag_status(status, ST_GRAPH_BAD);
+            else if (b - a > BIG_DEG) cls = 0;
+            else if (b - a >= SHORT_LO && b - a <= SHORT_HI) cls = 1;
+            else if (b - a > SHORT_HI) cls = 2;
+        }
     }
-    int64_t b = row_ptr[v + 1];
-    if (b < a || a < 0 || b > m) {
-        flag_status(status, ST_GRAPH_BAD);
-        return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {   // one atomic per warp and list
+        const unsigned mk = __ballot_sync(0xffffffffu, cls == c);
+        if (!mk) continue;
+        const int leader = __ffs(mk) - 1;
+        int at = 0;
+        if ((int)lane == leader) at = atomicAdd(&counts[c], __popc(mk));
+        at = __shfl_sync(0xffffffffu, at, leader) + __popc(mk & lt);
+        if (cls == c) {
+            if (c == 0) big[at] = (int32_t)v;
+            else if (c == 1) mid[at] = (int32_t)v;
+            else mid[n - 1 - at] = (int32_t)v;
+        }
     }
-    if (b - a > BIG_DEG) big[atomicAdd(nbig, 1)] = (int32_t)v;
 }
 
 // rows of degree <= SMALL_STATS: one thread per row
@@ -310,15 +380,78 @@ __global__ void big_finalize_kernel(const int64_t* __restrict__ row_ptr, const i
     atomicMax(o.acc + 0, (unsigned long long)S);
 }
 
+// short rows (SHORT_LO..SHORT_HI entries, the front of `mid`): 8 lanes per
+// row, four rows per warp; the loop is warp-uniform (idle groups take a row
+// of length 0 and write nothing)
+__global__ void stats_short_kernel(const int64_t* __restrict__ row_ptr, int64_t n, const int32_t* __restrict__ col,
+                                   const uint32_t* __restrict__ w, const int32_t* __restrict__ mid, int64_t nshort,
+                                   StatsOut o) {
+    SubG<8, 4> g;
+    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int64_t ng = ((int64_t)gridDim.x * blockDim.x) >> 3;
+    uint64_t h1 = 0, h2 = 0, mx = 0;
+    for (int64_t it = gid;; it += ng) {
+        const bool act = it < nshort;
+        if (!__any_sync(0xffffffffu, act)) break;
+        const int64_t v = act ? mid[it] : 0;
+        const int64_t a = act ? row_ptr[v] : 0, deg = act ? row_ptr[v + 1] - a : 0;
+        uint64_t sum = 0, a1 = 0, a2 = 0;
+        bool bad = false;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t i = (int64_t)g.rank() * 4 + j;
+            if (i < deg) {
+                const int32_t u = col[a + i];
+                const uint32_t ww = w[a + i];
+                bad |= (u < 0) || ((int64_t)u >= n) || ((int64_t)u == v) || (ww == 0) ||
+                       (i > 0 && col[a + i - 1] >= u);
+                sum += ww;
+                if (u >= 0) {
+                    a1 += edge_hash((uint64_t)v, (uint64_t)u, ww);
+                    a2 += edge_hash((uint64_t)u, (uint64_t)v, ww);
+                }
+            }
+        }
+        h1 += a1;
+        h2 += a2;
+        sum = g.sum(sum);
+        bad = g.any(bad);
+        if (act && g.rank() == 0) {
+            o.vrec[v] = make_uint4((uint32_t)a, (uint32_t)deg, (uint32_t)sum, (uint32_t)(sum >> 32));
+            if (__umul64hi(sum, (uint64_t)deg) != 0 || sum * (uint64_t)deg >= (1ull << 63))
+                flag_status(o.status, ST_OVERFLOW);
+            if (bad) {
+                flag_status(o.status, ST_GRAPH_BAD);
+                atomicMin(o.status + 1, (uint32_t)v);
+            }
+        }
+        mx = sum > mx ? sum : mx;
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+        h1 += __shfl_xor_sync(0xffffffffu, h1, d);
+        h2 += __shfl_xor_sync(0xffffffffu, h2, d);
+        const uint64_t m2 = __shfl_xor_sync(0xffffffffu, mx, d);
+        mx = m2 > mx ? m2 : mx;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(o.acc + 0, (unsigned long long)mx);
+        atomicAdd(o.acc + 1, (unsigned long long)h1);
+        atomicAdd(o.acc + 2, (unsigned long long)h2);
+    }
+}
+
+// medium rows (listed from the back of `mid`): one warp per row
 __global__ void stats_warp_kernel(const int64_t* __restrict__ row_ptr, int64_t n, const int32_t* __restrict__ col,
-                                  const uint32_t* __restrict__ w, StatsOut o) {
+                                  const uint32_t* __restrict__ w, const int32_t* __restrict__ mid, int64_t nmed,
+                                  StatsOut o) {
     WarpG g;
     int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint64_t h1 = 0, h2 = 0, mx = 0;
-    for (int64_t v = wid; v < n; v += nw) {
-        int64_t a = row_ptr[v], b = row_ptr[v + 1];
-        if (b < a || b - a > BIG_DEG || b - a <= SMALL_STATS) continue;
+    for (int64_t i = wid; i < nmed; i += nw) {
+        const int64_t v = mid[n - 1 - i];
+        const int64_t a = row_ptr[v], b = row_ptr[v + 1];
         row_stats(g, v, a, b - a, n, col, w, o, h1, h2, mx);
     }
     if (g.rank() == 0) {
@@ -567,14 +700,81 @@ __global__ void __launch_bounds__(256) alias_thread_kernel(const uint4* __restri
 }
 
 __global__ void alias_warp_kernel(const uint4* __restrict__ vrec, int64_t n, const int32_t* __restrict__ col,
-                                  const uint32_t* __restrict__ w, uint4* tab, int32_t* sidx, uint64_t* scum) {
+                                  const uint32_t* __restrict__ w, const int32_t* __restrict__ mid, int64_t nmed,
+                                  uint4* tab, int32_t* sidx, uint64_t* scum) {
     WarpG g;
     int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t v = wid; v < n; v += nw) {
-        uint4 r = vrec[v];
-        if ((int64_t)r.y > BIG_DEG || (int64_t)r.y <= SMALL_DEG) continue;
+    for (int64_t i = wid; i < nmed; i += nw) {
+        const uint4 r = vrec[mid[n - 1 - i]];
         row_alias(g, (int64_t)r.x, (int64_t)r.y, (uint64_t)r.z | ((uint64_t)r.w << 32), col, w, tab, sidx, scum);
+    }
+}
+
+// Short rows: 8 lanes per row, 4 entries per lane, so every pass is one
+// chunk and every group of the warp makes the same shuffles (idle groups run
+// on a row of length 0).
+__global__ void alias_short_kernel(const uint4* __restrict__ vrec, int64_t n, const int32_t* __restrict__ col,
+                                   const uint32_t* __restrict__ w, const int32_t* __restrict__ mid, int64_t nshort,
+                                   uint4* tab, int32_t* sidx, uint64_t* scum) {
+    SubG<8, 4> g;
+    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int64_t ng = ((int64_t)gridDim.x * blockDim.x) >> 3;
+    for (int64_t it = gid;; it += ng) {
+        const bool act = it < nshort;
+        if (!__any_sync(0xffffffffu, act)) break;
+        uint4 r = make_uint4(0, 0, 0, 0);
+        if (act) r = vrec[mid[it]];
+        const int64_t start = (int64_t)r.x, deg = (int64_t)r.y;
+        const uint64_t S = (uint64_t)r.z | ((uint64_t)r.w << 32), d = (uint64_t)deg;
+        const int rk = g.rank();
+        // A+B: smalls (q < S) and their pop positions
+        uint64_t f[4];
+        uint32_t wv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t i = (int64_t)rk * 4 + j;
+            wv[j] = i < deg ? w[start + i] : 0u;
+            f[j] = (i < deg && (uint64_t)wv[j] * d < S) ? 1 : 0;
+        }
+        const int64_t nsm = (int64_t)g.chunk_scan(f), nl = deg - nsm;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t i = (int64_t)rk * 4 + j;
+            if (i < deg) {
+                const bool sm = (uint64_t)wv[j] * d < S;
+                const int64_t rs = (int64_t)f[j] - (sm ? 1 : 0);   // smalls before i
+                sidx[start + (sm ? nsm - 1 - rs : deg - 1 - (i - rs))] = (int32_t)i;
+            }
+        }
+        g.sync();
+        // C: inclusive prefixes of deficits (smalls) and excesses (larges) in pop order
+        uint64_t x[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t p = (int64_t)rk * 4 + j;
+            x[j] = p < nsm ? S - (uint64_t)w[start + sidx[start + p]] * d : 0;
+        }
+        g.chunk_scan(x);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t p = (int64_t)rk * 4 + j;
+            if (p < nsm) scum[start + p] = x[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t p = (int64_t)rk * 4 + j;
+            x[j] = p < nl ? (uint64_t)w[start + sidx[start + nsm + p]] * d - S : 0;
+        }
+        g.chunk_scan(x);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t p = (int64_t)rk * 4 + j;
+            if (p < nl) scum[start + nsm + p] = x[j];
+        }
+        g.sync();
+        if (deg > 0) alias_assign(start, deg, S, nsm, col, w, tab, sidx, scum, rk, 8);
+        g.sync();
     }
 }
 
@@ -768,6 +968,7 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
     int32_t* t_col = nullptr;
     uint32_t* t_w = nullptr;
     int32_t* big = nullptr;
+    int32_t* mid = nullptr;
     int* nbig = nullptr;
     unsigned long long* acc = nullptr;
     panther_status st = PANTHER_OK;
@@ -776,6 +977,7 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
         dev_free(ctx, t_col);
         dev_free(ctx, t_w);
         dev_free(ctx, big);
+        dev_free(ctx, mid);
         dev_free(ctx, nbig);
         dev_free(ctx, acc);
         cudaStreamSynchronize(s);
@@ -784,7 +986,8 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
     };
     if ((st = dev_alloc(ctx, (void**)&g->vrec, sizeof(uint4) * n)) ||
         (st = dev_alloc(ctx, (void**)&big, sizeof(int32_t) * (n + 1))) ||
-        (st = dev_alloc(ctx, (void**)&nbig, sizeof(int) * 2)) ||
+        (st = dev_alloc(ctx, (void**)&mid, sizeof(int32_t) * n)) ||
+        (st = dev_alloc(ctx, (void**)&nbig, sizeof(int) * 4)) ||
         (st = dev_alloc(ctx, (void**)&acc, sizeof(unsigned long long) * 4)))
         return fail(st);
     cudaError_t e;
@@ -801,21 +1004,27 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
     const int64_t* d_rp = mem == PANTHER_MEM_HOST ? t_rp : row_ptr;
     const int32_t* d_col = mem == PANTHER_MEM_HOST ? t_col : col;
     const uint32_t* d_w = mem == PANTHER_MEM_HOST ? t_w : w;
-    if ((e = cudaMemsetAsync(nbig, 0, sizeof(int) * 2, s)) ||
+    if ((e = cudaMemsetAsync(nbig, 0, sizeof(int) * 4, s)) ||
         (e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 4, s)) ||
         (e = cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s)) ||
         (e = cudaMemsetAsync(ctx->d_status + 1, 0xff, sizeof(uint32_t), s)))
         return fail(cuda_err(ctx, e, "graph upload"));
 
-    rows_check_kernel<<<(unsigned)ceil_div(n + 1, 256), 256, 0, s>>>(d_rp, n, m, big, nbig, ctx->d_status);
+    rows_check_kernel<<<(unsigned)ceil_div(n + 1, 256), 256, 0, s>>>(d_rp, n, m, big, mid, nbig, ctx->d_status);
     ctx->launches++;
-    int h_nbig = 0;
+    int h_lists[4] = {0, 0, 0, 0};
     uint32_t h_st[2];
-    if ((e = cudaMemcpyAsync(&h_nbig, nbig, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+    if ((e = cudaMemcpyAsync(h_lists, nbig, sizeof(int) * 4, cudaMemcpyDeviceToHost, s)) ||
         (e = cudaMemcpyAsync(h_st, ctx->d_status, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) ||
         (e = cudaStreamSynchronize(s)))
         return fail(cuda_err(ctx, e, "row check"));
     if (h_st[0]) return fail(set_err(ctx, PANTHER_EINVAL, "row_ptr is not a valid CSR offset array"));
+    const int h_nbig = h_lists[0];
+    const int64_t nshort = h_lists[1], nmed = h_lists[2];
+    auto rows_grid = [&](int64_t rows, int lanes_per_row) {
+        return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows * lanes_per_row, 256),
+                                                                (int64_t)ctx->num_sms * 16));
+    };
 
     // segment plan of the rows above BIG_DEG
     int64_t* bdeg = nullptr;
@@ -853,8 +1062,15 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
     unsigned gw = grid_for(ctx, 64, n, 256);
     stats_thread_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->num_sms * 16), 256, 0, s>>>(
         d_rp, n, d_col, d_w, so);
-    stats_warp_kernel<<<gw, 256, 0, s>>>(d_rp, n, d_col, d_w, so);
-    ctx->launches += 2;
+    ctx->launches++;
+    if (nshort) {
+        stats_short_kernel<<<rows_grid(nshort, 8), 256, 0, s>>>(d_rp, n, d_col, d_w, mid, nshort, so);
+        ctx->launches++;
+    }
+    if (nmed) {
+        stats_warp_kernel<<<rows_grid(nmed, 32), 256, 0, s>>>(d_rp, n, d_col, d_w, mid, nmed, so);
+        ctx->launches++;
+    }
     if (h_nbig) {
         stats_seg_kernel<<<(unsigned)nseg, BLK, 0, s>>>(d_rp, n, d_col, d_w, big, seg_off, h_nbig, bigS, so);
         big_finalize_kernel<<<(unsigned)ceil_div(h_nbig, 256), 256, 0, s>>>(d_rp, big, h_nbig, bigS, so);
@@ -903,8 +1119,17 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
         }
         alias_thread_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->num_sms * 16), 256, 0, s>>>(
             g->vrec, n, d_col, d_w, g->alias);
-        alias_warp_kernel<<<gw, 256, 0, s>>>(g->vrec, n, d_col, d_w, g->alias, sidx, scum);
-        ctx->launches += 2;
+        ctx->launches++;
+        if (nshort) {
+            alias_short_kernel<<<rows_grid(nshort, 8), 256, 0, s>>>(g->vrec, n, d_col, d_w, mid, nshort, g->alias,
+                                                                    sidx, scum);
+            ctx->launches++;
+        }
+        if (nmed) {
+            alias_warp_kernel<<<rows_grid(nmed, 32), 256, 0, s>>>(g->vrec, n, d_col, d_w, mid, nmed, g->alias, sidx,
+                                                                  scum);
+            ctx->launches++;
+        }
         if (h_nbig) {
             int64_t* bign = nullptr;
             if ((st = dev_alloc(ctx, (void**)&bign, sizeof(int64_t) * h_nbig))) {
@@ -939,10 +1164,11 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
     dev_free(ctx, t_col);
     dev_free(ctx, t_w);
     dev_free(ctx, big);
+    dev_free(ctx, mid);
     dev_free(ctx, nbig);
     dev_free(ctx, acc);
     if ((e = cudaStreamSynchronize(s))) {
-        t_rp = nullptr; t_col = nullptr; t_w = nullptr; big = nullptr; nbig = nullptr; acc = nullptr;
+        t_rp = nullptr; t_col = nullptr; t_w = nullptr; big = nullptr; mid = nullptr; nbig = nullptr; acc = nullptr;
         return fail(cuda_err(ctx, e, "graph tables"));
     }
     *out = g;

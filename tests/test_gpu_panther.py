@@ -123,7 +123,30 @@ def _hub_rows_graph():
     return synth.graph_from_edges(n, edges, ws)
 
 
-@pytest.mark.parametrize("which", ["small", "bigrow", "hubrows", "wide"])
+def _short_rows_graph():
+    # rows of 17..33 entries (8 lanes per row up to 32, a warp beyond) with
+    # equal, random, one dominant, and log-uniform weights
+    n = 3000
+    rng = np.random.default_rng(13)
+    edges, ws = [], []
+    for r in range(68):
+        deg = 17 + (r % 17)
+        nb = rng.choice(np.arange(100, n), size=deg, replace=False)
+        for j, u in enumerate(nb):
+            edges.append((r, int(u)))
+            kind = (r // 17) % 4
+            if kind == 0:
+                ws.append(5)
+            elif kind == 1:
+                ws.append(int(rng.integers(1, 2**16)))
+            elif kind == 2:
+                ws.append(2**20 if j == 3 else 1)
+            else:
+                ws.append(int(np.exp(rng.uniform(0, np.log(2**12)))))
+    return synth.graph_from_edges(n, edges, ws)
+
+
+@pytest.mark.parametrize("which", ["small", "bigrow", "hubrows", "shortrows", "wide"])
 def test_transition_tables_match_oracle(pk, small, which):
     if which == "small":
         g = small
@@ -131,6 +154,10 @@ def test_transition_tables_match_oracle(pk, small, which):
         g = _big_row_graph()
     elif which == "hubrows":
         g = _hub_rows_graph()
+    elif which == "shortrows":
+        g = _short_rows_graph()
+        deg = np.diff(g.row_ptr)
+        assert ((deg >= 17) & (deg <= 32)).sum() >= 60 and (deg == 33).sum() >= 1
     else:
         # row sums beyond 2^32 switch the prefix table to 64-bit entries
         g = synth.graph_from_edges(40, [(0, i) for i in range(1, 40)] + [(1, 2)],

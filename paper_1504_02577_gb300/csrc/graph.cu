@@ -219,33 +219,37 @@ __device__ void row_stats(const G& g, int64_t v, int64_t start, int64_t deg, int
     mx = s > mx ? s : mx;
 }
 
-// rows of SHORT_LO..SHORT_HI entries: 8 lanes per row, 4 entries per lane
-constexpr int64_t SHORT_LO = 17, SHORT_HI = 32;
+// Rows of 17..4G entries are built by G lanes each (G = 8, 16, 32; four
+// entries per lane, one chunk per pass), longer ones up to BIG_DEG by a warp
+// in chunks of 32.
+constexpr int64_t SHORT_LO = 17, SHORT_HI = 128;
 
-// Row-pointer checks, and the lists of rows by length: big (above BIG_DEG),
-// short (SHORT_LO..SHORT_HI, at the front of `mid`) and medium (up to
-// BIG_DEG, from the back of `mid`). counts: [0] big, [1] short, [2] medium.
+// Row-pointer checks, and the lists of rows by length. counts: [0] rows above
+// BIG_DEG (`big`), [1] 17..32 entries (front of `mid`), [2] 129..BIG_DEG
+// (back of `mid`), [3] 33..64 (front of `mid2`), [4] 65..128 (back of `mid2`).
 __global__ void rows_check_kernel(const int64_t* __restrict__ row_ptr, int64_t n, int64_t m,
-                                  int32_t* __restrict__ big, int32_t* __restrict__ mid, int* __restrict__ counts,
-                                  uint32_t* status) {
+                                  int32_t* __restrict__ big, int32_t* __restrict__ mid, int32_t* __restrict__ mid2,
+                                  int* __restrict__ counts, uint32_t* status) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
-    int cls = -1;   // 0 big, 1 short, 2 medium
+    int cls = -1;
     if (v <= n) {
         const int64_t a = row_ptr[v];
         if (v == 0 && a != 0) flag_status(status, ST_GRAPH_BAD);
         if (v == n) {
             if (a != m) flag_status(status, ST_GRAPH_BAD);
         } else {
-            const int64_t b = row_ptr[v + 1];
+            const int64_t b = row_ptr[v + 1], d = b - a;
             if (b < a || a < 0 || b > m) flag_status(status, ST_GRAPH_BAD);
-            else if (b - a > BIG_DEG) cls = 0;
-            else if (b - a >= SHORT_LO && b - a <= SHORT_HI) cls = 1;
-            else if (b - a > SHORT_HI) cls = 2;
+            else if (d > BIG_DEG) cls = 0;
+            else if (d > SHORT_HI) cls = 2;
+            else if (d > 64) cls = 4;
+            else if (d > 32) cls = 3;
+            else if (d >= SHORT_LO) cls = 1;
         }
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {   // one atomic per warp and list
+    for (int c = 0; c < 5; ++c) {   // one atomic per warp and list
         const unsigned mk = __ballot_sync(0xffffffffu, cls == c);
         if (!mk) continue;
         const int leader = __ffs(mk) - 1;
@@ -255,9 +259,16 @@ __global__ void rows_check_kernel(const int64_t* __restrict__ row_ptr, int64_t n
         if (cls == c) {
             if (c == 0) big[at] = (int32_t)v;
             else if (c == 1) mid[at] = (int32_t)v;
-            else mid[n - 1 - at] = (int32_t)v;
+            else if (c == 2) mid[n - 1 - at] = (int32_t)v;
+            else if (c == 3) mid2[at] = (int32_t)v;
+            else mid2[n - 1 - at] = (int32_t)v;
         }
     }
+}
+
+// list i of a short class: `rows[i]` (front) or `rows[n - 1 - i]` (back)
+__device__ __forceinline__ int64_t list_at(const int32_t* rows, int64_t n, bool back, int64_t i) {
+    return rows[back ? n - 1 - i : i];
 }
 
 // rows of degree <= SMALL_STATS: one thread per row
@@ -380,20 +391,20 @@ __global__ void big_finalize_kernel(const int64_t* __restrict__ row_ptr, const i
     atomicMax(o.acc + 0, (unsigned long long)S);
 }
 
-// short rows (SHORT_LO..SHORT_HI entries, the front of `mid`): 8 lanes per
-// row, four rows per warp; the loop is warp-uniform (idle groups take a row
-// of length 0 and write nothing)
+// short rows (at most 4G entries): G lanes per row, 32/G rows per warp; the
+// loop is warp-uniform (idle groups take a row of length 0 and write nothing)
+template <int G>
 __global__ void stats_short_kernel(const int64_t* __restrict__ row_ptr, int64_t n, const int32_t* __restrict__ col,
-                                   const uint32_t* __restrict__ w, const int32_t* __restrict__ mid, int64_t nshort,
-                                   StatsOut o) {
-    SubG<8, 4> g;
-    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-    const int64_t ng = ((int64_t)gridDim.x * blockDim.x) >> 3;
+                                   const uint32_t* __restrict__ w, const int32_t* __restrict__ rows, bool back,
+                                   int64_t nrows, StatsOut o) {
+    SubG<G, 4> g;
+    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / G;
     uint64_t h1 = 0, h2 = 0, mx = 0;
     for (int64_t it = gid;; it += ng) {
-        const bool act = it < nshort;
+        const bool act = it < nrows;
         if (!__any_sync(0xffffffffu, act)) break;
-        const int64_t v = act ? mid[it] : 0;
+        const int64_t v = act ? list_at(rows, n, back, it) : 0;
         const int64_t a = act ? row_ptr[v] : 0, deg = act ? row_ptr[v + 1] - a : 0;
         uint64_t sum = 0, a1 = 0, a2 = 0;
         bool bad = false;
@@ -711,20 +722,21 @@ __global__ void alias_warp_kernel(const uint4* __restrict__ vrec, int64_t n, con
     }
 }
 
-// Short rows: 8 lanes per row, 4 entries per lane, so every pass is one
+// Short rows: G lanes per row, 4 entries per lane, so every pass is one
 // chunk and every group of the warp makes the same shuffles (idle groups run
 // on a row of length 0).
+template <int G>
 __global__ void alias_short_kernel(const uint4* __restrict__ vrec, int64_t n, const int32_t* __restrict__ col,
-                                   const uint32_t* __restrict__ w, const int32_t* __restrict__ mid, int64_t nshort,
-                                   uint4* tab, int32_t* sidx, uint64_t* scum) {
-    SubG<8, 4> g;
-    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-    const int64_t ng = ((int64_t)gridDim.x * blockDim.x) >> 3;
+                                   const uint32_t* __restrict__ w, const int32_t* __restrict__ rows, bool back,
+                                   int64_t nrows, uint4* tab, int32_t* sidx, uint64_t* scum) {
+    SubG<G, 4> g;
+    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / G;
     for (int64_t it = gid;; it += ng) {
-        const bool act = it < nshort;
+        const bool act = it < nrows;
         if (!__any_sync(0xffffffffu, act)) break;
         uint4 r = make_uint4(0, 0, 0, 0);
-        if (act) r = vrec[mid[it]];
+        if (act) r = vrec[list_at(rows, n, back, it)];
         const int64_t start = (int64_t)r.x, deg = (int64_t)r.y;
         const uint64_t S = (uint64_t)r.z | ((uint64_t)r.w << 32), d = (uint64_t)deg;
         const int rk = g.rank();
@@ -773,7 +785,7 @@ __global__ void alias_short_kernel(const uint4* __restrict__ vrec, int64_t n, co
             if (p < nl) scum[start + nsm + p] = x[j];
         }
         g.sync();
-        if (deg > 0) alias_assign(start, deg, S, nsm, col, w, tab, sidx, scum, rk, 8);
+        if (deg > 0) alias_assign(start, deg, S, nsm, col, w, tab, sidx, scum, rk, G);
         g.sync();
     }
 }
@@ -969,6 +981,7 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
     uint32_t* t_w = nullptr;
     int32_t* big = nullptr;
     int32_t* mid = nullptr;
+    int32_t* mid2 = nullptr;
     int* nbig = nullptr;
     unsigned long long* acc = nullptr;
     panther_status st = PANTHER_OK;
@@ -978,6 +991,7 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
         dev_free(ctx, t_w);
         dev_free(ctx, big);
         dev_free(ctx, mid);
+        dev_free(ctx, mid2);
         dev_free(ctx, nbig);
         dev_free(ctx, acc);
         cudaStreamSynchronize(s);
@@ -987,7 +1001,8 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
     if ((st = dev_alloc(ctx, (void**)&g->vrec, sizeof(uint4) * n)) ||
         (st = dev_alloc(ctx, (void**)&big, sizeof(int32_t) * (n + 1))) ||
         (st = dev_alloc(ctx, (void**)&mid, sizeof(int32_t) * n)) ||
-        (st = dev_alloc(ctx, (void**)&nbig, sizeof(int) * 4)) ||
+        (st = dev_alloc(ctx, (void**)&mid2, sizeof(int32_t) * n)) ||
+        (st = dev_alloc(ctx, (void**)&nbig, sizeof(int) * 8)) ||
         (st = dev_alloc(ctx, (void**)&acc, sizeof(unsigned long long) * 4)))
         return fail(st);
     cudaError_t e;
@@ -1004,23 +1019,24 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
     const int64_t* d_rp = mem == PANTHER_MEM_HOST ? t_rp : row_ptr;
     const int32_t* d_col = mem == PANTHER_MEM_HOST ? t_col : col;
     const uint32_t* d_w = mem == PANTHER_MEM_HOST ? t_w : w;
-    if ((e = cudaMemsetAsync(nbig, 0, sizeof(int) * 4, s)) ||
+    if ((e = cudaMemsetAsync(nbig, 0, sizeof(int) * 8, s)) ||
         (e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 4, s)) ||
         (e = cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s)) ||
         (e = cudaMemsetAsync(ctx->d_status + 1, 0xff, sizeof(uint32_t), s)))
         return fail(cuda_err(ctx, e, "graph upload"));
 
-    rows_check_kernel<<<(unsigned)ceil_div(n + 1, 256), 256, 0, s>>>(d_rp, n, m, big, mid, nbig, ctx->d_status);
+    rows_check_kernel<<<(unsigned)ceil_div(n + 1, 256), 256, 0, s>>>(d_rp, n, m, big, mid, mid2, nbig,
+                                                                     ctx->d_status);
     ctx->launches++;
-    int h_lists[4] = {0, 0, 0, 0};
+    int h_lists[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint32_t h_st[2];
-    if ((e = cudaMemcpyAsync(h_lists, nbig, sizeof(int) * 4, cudaMemcpyDeviceToHost, s)) ||
+    if ((e = cudaMemcpyAsync(h_lists, nbig, sizeof(int) * 8, cudaMemcpyDeviceToHost, s)) ||
         (e = cudaMemcpyAsync(h_st, ctx->d_status, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) ||
         (e = cudaStreamSynchronize(s)))
         return fail(cuda_err(ctx, e, "row check"));
     if (h_st[0]) return fail(set_err(ctx, PANTHER_EINVAL, "row_ptr is not a valid CSR offset array"));
     const int h_nbig = h_lists[0];
-    const int64_t nshort = h_lists[1], nmed = h_lists[2];
+    const int64_t nshort = h_lists[1], nmed = h_lists[2], n16 = h_lists[3], n32 = h_lists[4];
     auto rows_grid = [&](int64_t rows, int lanes_per_row) {
         return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows * lanes_per_row, 256),
                                                                 (int64_t)ctx->num_sms * 16));
@@ -1064,7 +1080,15 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
         d_rp, n, d_col, d_w, so);
     ctx->launches++;
     if (nshort) {
-        stats_short_kernel<<<rows_grid(nshort, 8), 256, 0, s>>>(d_rp, n, d_col, d_w, mid, nshort, so);
+        stats_short_kernel<8><<<rows_grid(nshort, 8), 256, 0, s>>>(d_rp, n, d_col, d_w, mid, false, nshort, so);
+        ctx->launches++;
+    }
+    if (n16) {
+        stats_short_kernel<16><<<rows_grid(n16, 16), 256, 0, s>>>(d_rp, n, d_col, d_w, mid2, false, n16, so);
+        ctx->launches++;
+    }
+    if (n32) {
+        stats_short_kernel<32><<<rows_grid(n32, 32), 256, 0, s>>>(d_rp, n, d_col, d_w, mid2, true, n32, so);
         ctx->launches++;
     }
     if (nmed) {
@@ -1121,8 +1145,18 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
             g->vrec, n, d_col, d_w, g->alias);
         ctx->launches++;
         if (nshort) {
-            alias_short_kernel<<<rows_grid(nshort, 8), 256, 0, s>>>(g->vrec, n, d_col, d_w, mid, nshort, g->alias,
-                                                                    sidx, scum);
+            alias_short_kernel<8><<<rows_grid(nshort, 8), 256, 0, s>>>(g->vrec, n, d_col, d_w, mid, false, nshort,
+                                                                       g->alias, sidx, scum);
+            ctx->launches++;
+        }
+        if (n16) {
+            alias_short_kernel<16><<<rows_grid(n16, 16), 256, 0, s>>>(g->vrec, n, d_col, d_w, mid2, false, n16,
+                                                                      g->alias, sidx, scum);
+            ctx->launches++;
+        }
+        if (n32) {
+            alias_short_kernel<32><<<rows_grid(n32, 32), 256, 0, s>>>(g->vrec, n, d_col, d_w, mid2, true, n32,
+                                                                      g->alias, sidx, scum);
             ctx->launches++;
         }
         if (nmed) {
@@ -1165,10 +1199,12 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
     dev_free(ctx, t_w);
     dev_free(ctx, big);
     dev_free(ctx, mid);
+    dev_free(ctx, mid2);
     dev_free(ctx, nbig);
     dev_free(ctx, acc);
     if ((e = cudaStreamSynchronize(s))) {
-        t_rp = nullptr; t_col = nullptr; t_w = nullptr; big = nullptr; mid = nullptr; nbig = nullptr; acc = nullptr;
+        t_rp = nullptr; t_col = nullptr; t_w = nullptr; big = nullptr; mid = nullptr; mid2 = nullptr; nbig = nullptr;
+        acc = nullptr;
         return fail(cuda_err(ctx, e, "graph tables"));
     }
     *out = g;

@@ -123,18 +123,21 @@ def _hub_rows_graph():
     return synth.graph_from_edges(n, edges, ws)
 
 
+_SHORT_DEGS = [17, 24, 32, 33, 50, 64, 65, 100, 128, 129]
+
+
 def _short_rows_graph():
-    # rows of 17..33 entries (8 lanes per row up to 32, a warp beyond) with
-    # equal, random, one dominant, and log-uniform weights
+    # rows on both sides of the 8/16/32-lane and warp boundaries (32, 64, 128)
+    # with equal, random, one dominant, and log-uniform weights
     n = 3000
     rng = np.random.default_rng(13)
     edges, ws = [], []
-    for r in range(68):
-        deg = 17 + (r % 17)
+    for r in range(4 * len(_SHORT_DEGS)):
+        deg = _SHORT_DEGS[r % len(_SHORT_DEGS)]
         nb = rng.choice(np.arange(100, n), size=deg, replace=False)
         for j, u in enumerate(nb):
             edges.append((r, int(u)))
-            kind = (r // 17) % 4
+            kind = r // len(_SHORT_DEGS)
             if kind == 0:
                 ws.append(5)
             elif kind == 1:
@@ -157,7 +160,7 @@ def test_transition_tables_match_oracle(pk, small, which):
     elif which == "shortrows":
         g = _short_rows_graph()
         deg = np.diff(g.row_ptr)
-        assert ((deg >= 17) & (deg <= 32)).sum() >= 60 and (deg == 33).sum() >= 1
+        assert all((deg == d).sum() >= 4 for d in _SHORT_DEGS)
     else:
         # row sums beyond 2^32 switch the prefix table to 64-bit entries
         g = synth.graph_from_edges(40, [(0, i) for i in range(1, 40)] + [(1, 2)],

@@ -183,7 +183,7 @@ PANTHER_API panther_status panther_build_index(panther_ctx* ctx, const panther_p
  * Same result as panther_build_index: P_v = pid[off[v] .. off[v+1]),
  * ascending. The caller passes dev_off (int64[n+1]) and dev_pid (int32,
  * pid_capacity >= R*(T+1) entries); *nnz receives the number of pairs.
- * Temporary buffers come from one static device array of about 72 MiB that
+ * Temporary buffers come from one static device array of about 86 MiB that
  * every GPU loading the library reserves until the process exits; R*(T+1)
  * may be at most 4,194,304 (EOVERFLOW beyond, before any launch). The first
  * call on a device looks up that array's device address, so make it before

@@ -18,8 +18,8 @@ namespace {
 
 constexpr int IX_T = 512;                  // threads per tile CTA
 constexpr int IX_WARPS = IX_T / 32;
-constexpr int IX_ROUNDS = 16;              // 32-item rounds per warp
-constexpr int IX_TILE = IX_T * IX_ROUNDS;  // 8192 items per tile
+constexpr int IX_ROUNDS = 12;              // 32-item rounds per warp
+constexpr int IX_TILE = IX_T * IX_ROUNDS;  // 6144 items per tile
 constexpr int MAX_RADIX = 512;
 
 struct Src {
@@ -338,7 +338,7 @@ extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_pa
 // process exits; the caller passes the outputs.
 namespace {
 constexpr int64_t NA_MAX_PAIRS = int64_t(1) << 22;           // R * (T+1) at most 4,194,304
-constexpr int64_t NA_MAX_TILES = 2048;                        // >= ceil(R * stride / 8192) for the limit above
+constexpr int64_t NA_MAX_TILES = 2816;                        // >= ceil(R * stride / IX_TILE) for the limit above
 constexpr size_t NA_KV_BYTES = (size_t)NA_MAX_PAIRS * 4;      // one key or value array
 constexpr size_t NA_CNT_BYTES = (size_t)MAX_RADIX * NA_MAX_TILES * 8;
 constexpr size_t NA_SCRATCH_BYTES = 4 * NA_KV_BYTES + 2 * NA_CNT_BYTES + 256;

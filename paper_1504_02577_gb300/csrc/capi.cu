@@ -72,6 +72,22 @@ panther_status panther_create(panther_ctx** out, int device, void* cuda_stream) 
         delete ctx;
         return PANTHER_ECUDA;
     }
+    // side streams and their events (optional: without them everything runs on `stream`)
+    bool side_ok = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < 2 && side_ok; ++i)
+        side_ok = cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&ctx->join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!side_ok) {
+        cudaGetLastError();
+        for (int i = 0; i < 2; ++i) {
+            if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);
+            if (ctx->join[i]) cudaEventDestroy(ctx->join[i]);
+            ctx->side[i] = nullptr;
+            ctx->join[i] = nullptr;
+        }
+        if (ctx->fork) cudaEventDestroy(ctx->fork);
+        ctx->fork = nullptr;
+    }
     // keep freed stream-ordered memory in the pool between calls
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
@@ -86,6 +102,11 @@ void panther_destroy(panther_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    for (int i = 0; i < 2; ++i) {
+        if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);
+        if (ctx->join[i]) cudaEventDestroy(ctx->join[i]);
+    }
+    if (ctx->fork) cudaEventDestroy(ctx->fork);
     cudaFree(ctx->d_status);
     cudaFreeHost(ctx->h_status);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);

@@ -34,6 +34,10 @@ struct panther_ctx {
     int64_t knn_stats[4] = {0, 0, 0, 0};
     // autotuned top-k launch shape (0 = not tuned yet)
     int topk_threads = 0, topk_cta_slots = 0, topk_blocks_per_sm = 0;
+    // side streams for independent kernels of one call (fork/join by events
+    // on `stream`); null when they could not be created
+    cudaStream_t side[2] = {nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
 };
 
 struct panther_graph {

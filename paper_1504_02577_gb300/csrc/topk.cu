@@ -1563,21 +1563,34 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
     classify_kernel<<<(unsigned)ceil_div(q, 256), 256, 0, s>>>(queries, q, P, ccap, ccap_big, lane_ok, group_max,
                                                                 tiers, o, ctx->d_status);
     ctx->launches++;
+    // the lane and group tiers are independent of the persistent passes: they
+    // run on the side streams (joined back into `s` below)
+    const bool side = ctx->side[0] != nullptr;
+    cudaStream_t s0 = side ? ctx->side[0] : s, s1 = side ? ctx->side[1] : s;
+    if (side) {
+        PCK(ctx, cudaEventRecord(ctx->fork, s));
+        PCK(ctx, cudaStreamWaitEvent(s0, ctx->fork, 0));
+        PCK(ctx, cudaStreamWaitEvent(s1, ctx->fork, 0));
+    }
     if (lane_ok) {
         if (ix->n <= (int64_t(1) << 29))
-            lane_kernel<true><<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(P, queries, lists + 3 * q, counts, 5, o);
+            lane_kernel<true><<<(unsigned)(ctx->num_sms * 8), 256, 0, s0>>>(P, queries, lists + 3 * q, counts, 5, o);
         else
-            lane_kernel<false><<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(P, queries, lists + 3 * q, counts, 5, o);
+            lane_kernel<false><<<(unsigned)(ctx->num_sms * 8), 256, 0, s0>>>(P, queries, lists + 3 * q, counts, 5, o);
         ctx->launches++;
     }
     if (group_max >= 16) {
-        group_kernel<8><<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(P, queries, lists + 4 * q, counts, 6, o);
-        group_kernel<16><<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(P, queries, lists + 5 * q, counts, 7, o);
+        group_kernel<8><<<(unsigned)(ctx->num_sms * 8), 256, 0, s0>>>(P, queries, lists + 4 * q, counts, 6, o);
+        group_kernel<16><<<(unsigned)(ctx->num_sms * 8), 256, 0, s1>>>(P, queries, lists + 5 * q, counts, 7, o);
         ctx->launches += 2;
     }
     if (group_max >= 32) {
-        group_kernel<32><<<(unsigned)(ctx->num_sms * 8), 256, 0, s>>>(P, queries, lists + 6 * q, counts, 8, o);
+        group_kernel<32><<<(unsigned)(ctx->num_sms * 8), 256, 0, s1>>>(P, queries, lists + 6 * q, counts, 8, o);
         ctx->launches++;
+    }
+    if (side) {
+        PCK(ctx, cudaEventRecord(ctx->join[0], s0));
+        PCK(ctx, cudaEventRecord(ctx->join[1], s1));
     }
     // narrow warp tier: ids below 2^(32 - cb) with cb bits for the largest
     // warp-tier count (a count never exceeds the query's number of paths)
@@ -1599,6 +1612,10 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
         else if (p->stride == 16) persistent_kernel<16><<<bb, BIG_T, BIG_SMEM, s>>>(B);
         else persistent_kernel<32><<<bb, BIG_T, BIG_SMEM, s>>>(B);
         ctx->launches++;
+    }
+    if (side) {
+        PCK(ctx, cudaStreamWaitEvent(s, ctx->join[0], 0));
+        PCK(ctx, cudaStreamWaitEvent(s, ctx->join[1], 0));
     }
     PCK(ctx, cudaGetLastError());
 

@@ -643,19 +643,21 @@ __global__ void classify_kernel(const int32_t* __restrict__ queries, int64_t q, 
     }
 }
 
-// Top-k of a CTA's shared table (every thread of the CTA calls it; ends with
-// a barrier). The k-th largest count c* comes from a histogram of the counts
-// (counts above 62 share bin 63); only the slots with count >= c* are
-// compacted, and when there are at most 64 of them one warp sorts them.
-// Otherwise every slot is offered to per-warp lists that are then merged.
-__device__ void cta_table_topk(const unsigned long long* tab, uint32_t nslots, unsigned long long* lists,
-                               const OutRef& o, int64_t qi) {
+// Top-k of a table of nslots slots, by a whole CTA (every thread calls it;
+// ends with a barrier). The k-th largest count c* comes from a histogram of
+// the counts (counts above 62 share bin 63), which also gives m = the slots
+// with count >= c*. With m <= 64 only those slots are compacted and one warp
+// sorts them; otherwise every slot is offered to per-warp lists, then merged.
+// CLEAR empties each filled slot once read (tables that are reused). The
+// list (ranks l and 32+l in lane l) goes to sink(t) in warp 0.
+template <bool CLEAR, class Sink>
+__device__ void cta_select(unsigned long long* tab, uint32_t nslots, unsigned long long* lists, int k, Sink sink) {
     __shared__ unsigned hist[64];
-    __shared__ int s_cstar, s_m;
+    __shared__ int s_cstar, s_m, s_at;
     const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
     const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     for (int i = threadIdx.x; i < 64; i += blockDim.x) hist[i] = 0;
-    if (threadIdx.x == 0) s_m = 0;
+    if (threadIdx.x == 0) s_at = 0;
     __syncthreads();
     for (uint32_t base = (uint32_t)w * 32; base < nslots; base += (uint32_t)nw * 32) {   // warp-uniform
         const uint32_t s = base + lane;
@@ -677,47 +679,56 @@ __device__ void cta_table_topk(const unsigned long long* tab, uint32_t nslots, u
             }
         }
         lo += __shfl_sync(0xffffffffu, hi, 0);
-        const unsigned mh = __ballot_sync(0xffffffffu, hi >= (uint32_t)o.k);
-        const unsigned ml = __ballot_sync(0xffffffffu, lo >= (uint32_t)o.k);
+        const unsigned mh = __ballot_sync(0xffffffffu, hi >= (uint32_t)k);
+        const unsigned ml = __ballot_sync(0xffffffffu, lo >= (uint32_t)k);
         int cstar = 1;   // fewer than k filled slots: take them all
         if (mh) cstar = 32 + 31 - __clz(mh);
         else if (ml) cstar = max(1, 31 - __clz(ml));
-        if (lane == 0) s_cstar = cstar;
+        const uint32_t m = cstar >= 32 ? __shfl_sync(0xffffffffu, hi, cstar - 32) : __shfl_sync(0xffffffffu, lo, cstar);
+        if (lane == 0) {
+            s_cstar = cstar;
+            s_m = (int)m;
+        }
     }
     __syncthreads();
     const uint32_t cstar = (uint32_t)s_cstar;
-    for (uint32_t base = (uint32_t)w * 32; base < nslots; base += (uint32_t)nw * 32) {   // warp-uniform
-        const uint32_t s = base + lane;
-        const unsigned long long x = s < nslots ? tab[s] : EMPTY;
-        const bool pass = x != EMPTY && (uint32_t)x >= cstar;
-        const unsigned m = __ballot_sync(0xffffffffu, pass);
-        if (!m) continue;
-        int at = 0;
-        if (lane == 0) at = atomicAdd(&s_m, __popc(m));
-        at = __shfl_sync(0xffffffffu, at, 0) + __popc(m & lt);
-        if (pass && at < 64) lists[at] = slot_score(x);
-    }
-    __syncthreads();
     const int m = s_m;
     if (m <= 64) {
+        for (uint32_t base = (uint32_t)w * 32; base < nslots; base += (uint32_t)nw * 32) {   // warp-uniform
+            const uint32_t s = base + lane;
+            const unsigned long long x = s < nslots ? tab[s] : EMPTY;
+            if (CLEAR && x != EMPTY) tab[s] = EMPTY;
+            const bool pass = x != EMPTY && (uint32_t)x >= cstar;
+            const unsigned mk = __ballot_sync(0xffffffffu, pass);
+            if (!mk) continue;
+            int at = 0;
+            if (lane == 0) at = atomicAdd(&s_at, __popc(mk));
+            at = __shfl_sync(0xffffffffu, at, 0) + __popc(mk & lt);
+            if (pass) lists[at] = slot_score(x);
+        }
+        __syncthreads();
         if (w == 0) {
             WarpTopK t;
             t.a = lane < (unsigned)m ? lists[lane] : 0;
             t.b = 32 + lane < (unsigned)m ? lists[32 + lane] : 0;
             warp_sort64_desc(t.a, t.b);
-            write_list(t, o, qi);
+            sink(t);
         }
         __syncthreads();
         return;
     }
-    __syncthreads();   // the list area is reused below
     WarpTopK t;
     for (uint32_t base = (uint32_t)w * 32; base < nslots; base += (uint32_t)nw * 32) {
-        uint32_t s = base + lane;
-        t.offer(s < nslots ? slot_score(tab[s]) : 0, o.k);
+        const uint32_t s = base + lane;
+        uint64_t sc = 0;
+        if (s < nslots) {
+            sc = slot_score(tab[s]);
+            if (CLEAR && sc) tab[s] = EMPTY;
+        }
+        t.offer(sc, k);
     }
     cta_merge(t, lists);
-    if (w == 0) write_list(t, o, qi);
+    if (w == 0) sink(t);
     __syncthreads();
 }
 
@@ -737,7 +748,7 @@ __device__ void cta_query(const PathsRef& P, int32_t v, int64_t qi, unsigned lon
     }
     if (!ok) flag_status(status, ST_HASH_FULL);
     __syncthreads();
-    cta_table_topk(tab, nslots, lists, o, qi);
+    cta_select<false>(tab, nslots, lists, o.k, [&](const WarpTopK& t) { write_list(t, o, qi); });
 }
 
 template <int STRIDE>
@@ -1059,31 +1070,19 @@ __global__ void g_count_kernel(PathsRef P, const int32_t* __restrict__ queries, 
 }
 
 // partial top-k of one chunk of one table; empties the slots it read
-__global__ void g_select_kernel(GPlan G, unsigned long long* arena, int k, unsigned long long* partial) {
-    __shared__ unsigned long long lists[32 * KMAX];
-    int64_t item = blockIdx.x;
-    int g = find_owner(G.sel_off, G.ng, item);
-    int64_t c0 = (item - G.sel_off[g]) * G_SLOTS;
-    uint32_t ns = G.tab_n[g];
-    unsigned long long* tab = arena + G.tab_off[g];
-    int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
-    unsigned lane = threadIdx.x & 31;
-    WarpTopK t;
-    int64_t end = c0 + G_SLOTS < (int64_t)ns ? c0 + G_SLOTS : (int64_t)ns;
-    for (int64_t base = c0 + w * 32; base < end; base += nw * 32) {
-        int64_t s = base + lane;
-        uint64_t sc = 0;
-        if (s < end) {
-            sc = slot_score(tab[s]);
-            if (sc) tab[s] = EMPTY;
-        }
-        t.offer(sc, k);
-    }
-    cta_merge(t, lists);
-    if (w == 0) {
+__global__ void __launch_bounds__(512) g_select_kernel(GPlan G, unsigned long long* arena, int k,
+                                                       unsigned long long* partial) {
+    __shared__ unsigned long long lists[16 * KMAX];
+    const int64_t item = blockIdx.x;
+    const int g = find_owner(G.sel_off, G.ng, item);
+    const int64_t c0 = (item - G.sel_off[g]) * G_SLOTS;
+    const int64_t ns = G.tab_n[g];
+    const uint32_t len = (uint32_t)(c0 + G_SLOTS < ns ? G_SLOTS : ns - c0);
+    const unsigned lane = threadIdx.x & 31;
+    cta_select<true>(arena + G.tab_off[g] + c0, len, lists, k, [&](const WarpTopK& t) {
         partial[item * KMAX + lane] = t.a;
         partial[item * KMAX + 32 + lane] = t.b;
-    }
+    });
 }
 
 // merge the partial lists of one query with a whole CTA (warps take lists

@@ -67,10 +67,28 @@ def _src_hash(*files):
     return h.hexdigest()[:12]
 
 
-# DRAM traffic per launch of the dominant kernel from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
-# source is unchanged; the capture and its command are in profiles/.
+# DRAM traffic of a stage per step (dram__bytes_read.sum + dram__bytes_write.sum
+# summed over the stage's launches) from one ncu capture of the 5M-vertex case,
+# scaled by the units processed (x10 for the 50M-vertex workload: vertices,
+# paths and pairs all grow tenfold); valid only while the stage's sources are
+# unchanged (SHA-256 of the files), else reported as null. The capture and its
+# command are in profiles/.
 NCU_TRAFFIC = {}
+
+
+def _traffic(stage, scale):
+    t = NCU_TRAFFIC.get(stage)
+    if not t:
+        return None
+    import hashlib
+    for f, digest in t["sources"].items():
+        try:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                if hashlib.sha256(fh.read()).hexdigest() != digest:
+                    return None
+        except OSError:
+            return None
+    return int(t["bytes_5M"] * scale)
 
 
 class Clocks:
@@ -145,17 +163,10 @@ def _max_over_ranks(x: float, ws: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
-
-
-def _workload(name):
-    import synth
-    p = dict(synth.WORKLOADS[name])
-    if name == "batched":
-        import oracle  # only for the closed-form R of Sec. 3.2? no: the library computes it
-    return p
 
 
 def _sample_size(p):
@@ -255,11 +266,12 @@ def run_ours(args, ws, rank, local):
     for s in stages:
         gbs = algo[s] / (stage_ms[s] * 1e-3) / 1e9
         stage_obj[s] = {"ms": round(stage_ms[s], 4), "algo_bytes": int(algo[s]), "achieved_gbs": round(gbs, 1),
-                        "frac": round(gbs / peak, 4)}
+                        "frac": round(gbs / peak, 4), "traffic": _traffic(s, g.n / 5_000_000)}
     dom = max(stages, key=lambda s: stage_ms[s])
-    kernel_name = {"sample": "sample_kernel", "index": "radix index passes", "topk": "topk (persistent)",
-                   "tables": "graph tables"}[dom]
-    traffic = NCU_TRAFFIC.get(dom)
+    kernel_name = {"sample": "sample_kernel (one launch)", "index": "index stage (radix passes)",
+                   "topk": "top-k stage (lane, group, persistent, hub kernels)",
+                   "tables": "tables stage (stats and alias kernels)"}[dom]
+    traffic = _traffic(dom, g.n / 5_000_000)
     roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": stage_obj[dom]["achieved_gbs"], "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": stage_obj[dom]["frac"],
                 "traffic": traffic}
@@ -715,6 +727,8 @@ def main():
         args.warmup = 3
     ws, rank, local = _dist()
     if args.impl == "reference":
+        # the oracle runs on the host: rank 0 alone works and prints, the
+        # other ranks exit without work
         out = run_reference(args, ws, rank)
         if out is not None:
             print(json.dumps(out), flush=True)

@@ -283,6 +283,21 @@ PANTHER_API panther_status panther_debug_philox(panther_ctx* ctx, uint32_t k0, u
                                                 uint32_t c2, uint32_t c3, int64_t count, uint32_t* dev_out,
                                                 uint32_t* dev_ref);
 
+/* Fault injection (test-only; no counterpart in the paper). The nth device
+ * allocation of this context from now on (0-based) fails once with ENOMEM,
+ * as if the device were out of memory; nth < 0 cancels. The call that meets
+ * it returns ENOMEM, frees what it had allocated and leaves the context
+ * usable. Errors: EINVAL (null ctx). */
+PANTHER_API panther_status panther_debug_fail_alloc(panther_ctx* ctx, int64_t nth);
+
+/* Bounded device wait (test-only; no counterpart in the paper): one warp
+ * waits for a device flag that nothing sets, gives up after limit_cycles
+ * SM clock cycles (1 <= limit_cycles <= 2^31), records a timeout in the
+ * context's status word and returns; the synchronisation at the end reports
+ * it. Returns ETIMEOUT when the wait ran out (always, by construction); the
+ * context stays usable. Errors: EINVAL. */
+PANTHER_API panther_status panther_debug_wait_timeout(panther_ctx* ctx, int64_t limit_cycles);
+
 /* --------------------------------------------------------- free calls --- */
 PANTHER_API void panther_free_graph(panther_graph* g);
 PANTHER_API void panther_free_paths(panther_paths* p);

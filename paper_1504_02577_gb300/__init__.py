@@ -58,6 +58,8 @@ SIGNATURES = {
     "pantherpp_knn_stats": ([_vp, _P(_i64)], _int),
     "panther_debug_graph_tables": ([_vp, _vp, _vp, _P(_int)], _int),
     "panther_debug_philox": ([_vp, _u32, _u32, _u64, _u32, _u32, _i64, _vp, _vp], _int),
+    "panther_debug_fail_alloc": ([_vp, _i64], _int),
+    "panther_debug_wait_timeout": ([_vp, _i64], _int),
     "panther_free_graph": ([_vp], None),
     "panther_free_paths": ([_vp], None),
     "panther_free_index": ([_vp], None),
@@ -237,6 +239,16 @@ def panther_debug_graph_tables(g: int, dev_alias16, dev_prefix):
 
 def panther_debug_philox(ctx: int, k0: int, k1: int, r0: int, c2: int, c3: int, count: int, dev_out, dev_ref):
     _check(ctx, load_library().panther_debug_philox(ctx, k0, k1, r0, c2, c3, count, _ptr(dev_out), _ptr(dev_ref)))
+
+
+def panther_debug_fail_alloc(ctx: int, nth: int) -> None:
+    """Test-only: the nth device allocation of ctx from now on fails once (ENOMEM); nth < 0 cancels."""
+    _check(ctx, load_library().panther_debug_fail_alloc(ctx, nth))
+
+
+def panther_debug_wait_timeout(ctx: int, limit_cycles: int) -> None:
+    """Test-only: a bounded device wait on a flag nothing sets; raises PantherError(ETIMEOUT)."""
+    _check(ctx, load_library().panther_debug_wait_timeout(ctx, limit_cycles))
 
 
 def panther_free_graph(g: int) -> None:

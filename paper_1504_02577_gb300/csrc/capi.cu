@@ -26,6 +26,10 @@ panther_status cuda_err(panther_ctx* ctx, cudaError_t e, const char* what) {
 panther_status dev_alloc(panther_ctx* ctx, void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (ctx->fail_alloc_at >= 0 && ctx->alloc_seen++ == ctx->fail_alloc_at) {
+        ctx->fail_alloc_at = -1;
+        return set_err(ctx, PANTHER_ENOMEM, "injected allocation failure (%zu bytes)", bytes);
+    }
     cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
     if (e != cudaSuccess) {
         *p = nullptr;

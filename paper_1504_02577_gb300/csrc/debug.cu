@@ -33,3 +33,39 @@ extern "C" panther_status panther_debug_philox(panther_ctx* ctx, uint32_t k0, ui
     PCK(ctx, cudaStreamSynchronize(ctx->stream));
     return PANTHER_OK;
 }
+
+namespace {
+// waits for *flag (never set) at most limit cycles, then records a timeout
+__global__ void wait_flag_kernel(const volatile uint32_t* flag, long long limit, uint32_t* status) {
+    const long long t0 = clock64();
+    while (*flag == 0) {
+        if (clock64() - t0 > limit) {
+            if (threadIdx.x == 0) flag_status(status, ST_TIMEOUT);
+            return;
+        }
+    }
+}
+}  // namespace
+
+extern "C" panther_status panther_debug_fail_alloc(panther_ctx* ctx, int64_t nth) {
+    if (!ctx) return PANTHER_EINVAL;
+    ctx->fail_alloc_at = nth < 0 ? -1 : nth;
+    ctx->alloc_seen = 0;
+    return PANTHER_OK;
+}
+
+extern "C" panther_status panther_debug_wait_timeout(panther_ctx* ctx, int64_t limit_cycles) {
+    if (!ctx) return PANTHER_EINVAL;
+    if (limit_cycles < 1 || limit_cycles > (int64_t(1) << 31))
+        return set_err(ctx, PANTHER_EINVAL, "limit_cycles must be in [1, 2^31]");
+    cudaSetDevice(ctx->device);
+    uint32_t* flag = nullptr;
+    panther_status st = dev_alloc(ctx, (void**)&flag, sizeof(uint32_t));
+    if (st) return st;
+    PCK(ctx, cudaMemsetAsync(flag, 0, sizeof(uint32_t), ctx->stream));
+    wait_flag_kernel<<<1, 32, 0, ctx->stream>>>(flag, (long long)limit_cycles, ctx->d_status);
+    ctx->launches++;
+    dev_free(ctx, flag);
+    PCK(ctx, cudaGetLastError());
+    return panther_sync(ctx);
+}

@@ -38,6 +38,8 @@ struct panther_ctx {
     // on `stream`); null when they could not be created
     cudaStream_t side[2] = {nullptr, nullptr};
     cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+    // fault injection: the allocation numbered fail_alloc_at fails once (-1: off)
+    int64_t fail_alloc_at = -1, alloc_seen = 0;
 };
 
 struct panther_graph {

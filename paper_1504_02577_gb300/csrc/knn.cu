@@ -190,6 +190,13 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// wait for a phase that is certain to complete (copies or MMAs already in
+// flight), bounded all the same; used only to drain after an abort
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity) && clock64() - t0 < (1ll << 31)) {
+    }
+}
 // bounded wait: about one second of SM clocks, then report and give up
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t* status, volatile int* abort_flag) {
     if (mbar_try(bar, parity)) return true;
@@ -403,6 +410,7 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
     auto TFULL = [&](int b) { return bar0 + 8 * (2 * KN_STAGES + b); };
     auto TEMPTY = [&](int b) { return bar0 + 8 * (2 * KN_STAGES + 2 + b); };
     const uint32_t AFULL = bar0 + 8 * (2 * KN_STAGES + 4), AEMPTY = AFULL + 8;
+    const uint32_t DRAIN = bar0 + 8 * (2 * KN_STAGES + 8);   // completion of this CTA's MMAs after an abort
     volatile int* abort_flag = (volatile int*)(gbase + SM_BAR + 8 * (2 * KN_STAGES + 6));
     uint32_t* tmem_slot = (uint32_t*)(gbase + SM_BAR + 8 * (2 * KN_STAGES + 7));
 
@@ -418,6 +426,7 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
         }
         mbar_init(AFULL, 1);
         mbar_init(AEMPTY, 1);
+        mbar_init(DRAIN, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -430,18 +439,28 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
+    // what was issued, for the drain after an abort: the parity of the last A
+    // load and of the last B load per stage (-1: none), and whether MMAs ran
+    int last_a = -1;
+    int last_b[KN_STAGES];
+    for (int st = 0; st < KN_STAGES; ++st) last_b[st] = -1;
+    bool mma_issued = false;
     if (warp == 0) {
         // ------------------------------------------------ TMA producer ---
         if (lane == 0) {
             int64_t it = 0;
             int j = 0;
-            for (int64_t wi = blockIdx.x; wi < S.nqt * S.nchunk; wi += gridDim.x, ++j) {
+            bool ok = true;
+            for (int64_t wi = blockIdx.x; wi < S.nqt * S.nchunk && ok; wi += gridDim.x, ++j) {
                 const int64_t qt = wi / S.nchunk, ch = wi % S.nchunk;
                 const int64_t ct0 = ch * S.nct / S.nchunk, ct1 = (ch + 1) * S.nct / S.nchunk;
-                if (!mbar_wait(AEMPTY, (j & 1) ^ 1, S.status, abort_flag)) break;
+                if (!mbar_wait(AEMPTY, (j & 1) ^ 1, S.status, abort_flag)) {
+                    ok = false;
+                    break;
+                }
                 mbar_expect_tx(AFULL, KN_M * KN_K * 2);
                 tma_load_2d(base + SM_A, &tmA, 0, (int)(qt * KN_M), AFULL);
-                bool ok = true;
+                last_a = j & 1;
                 for (int64_t ct = ct0; ct < ct1; ++ct, ++it) {
                     int s = (int)(it % KN_STAGES);
                     uint32_t ph = (uint32_t)((it / KN_STAGES) & 1);
@@ -452,8 +471,8 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
                     bulk_load(info, S.cid + ct * KN_N, KN_N * 4, FULL(s));
                     bulk_load(info + KN_N * 4, S.cnrm + ct * KN_N, KN_N * 4, FULL(s));
                     bulk_load(info + KN_N * 8, S.cncf + ct * KN_N, KN_N * 4, FULL(s));
+                    last_b[s] = (int)ph;
                 }
-                if (!ok) break;
             }
         }
     } else if (warp == 1) {
@@ -483,6 +502,7 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
                         umma_bf16(tmem + b * KN_N, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), kk > 0);
                     umma_commit(EMPTY(s));
                     umma_commit(TFULL(b));
+                    mma_issued = true;
                 }
                 umma_commit(AEMPTY);
                 if (!ok) break;
@@ -562,6 +582,22 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
+    if (*abort_flag) {
+        // a wait ran out somewhere in the CTA: the copies issued into shared
+        // memory land and the MMAs issued complete before the CTA releases
+        // TMEM and exits (each drain is bounded too)
+        if (warp == 0 && lane == 0) {
+            if (last_a >= 0) mbar_drain(AFULL, (uint32_t)last_a);
+            for (int st = 0; st < KN_STAGES; ++st)
+                if (last_b[st] >= 0) mbar_drain(FULL(st), (uint32_t)last_b[st]);
+        }
+        if (warp == 1 && lane == 0 && mma_issued) {
+            umma_commit(DRAIN);
+            mbar_drain(DRAIN, 0);
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
     tc_fence_after();
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
 }

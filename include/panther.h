@@ -163,6 +163,15 @@ PANTHER_API panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int6
 PANTHER_API panther_status panther_sample_paths(panther_ctx* ctx, const panther_graph* g, uint64_t seed,
                                     int64_t R, int T, int mode, panther_paths** out);
 
+/* Paths r0 .. r0+R-1 of the same sequence (no counterpart in the paper): row
+ * i holds path r0 + i, drawn with counter r0 + i, so a range is bit-identical
+ * to the same rows of a run from 0. Use it to resume sampling from any path
+ * id or to split the paths between GPUs. Path ids in an index built from this
+ * handle are local (i = r - r0). r0 >= 0, r0 + R < 2^63; otherwise as
+ * panther_sample_paths. */
+PANTHER_API panther_status panther_sample_paths_range(panther_ctx* ctx, const panther_graph* g, uint64_t seed,
+                                                      int64_t r0, int64_t R, int T, int mode, panther_paths** out);
+
 /* Device view of the path rows (library-owned; valid until freed). */
 PANTHER_API panther_status panther_paths_view(const panther_paths* p, const int32_t** dev_rows,
                                   int64_t* R, int* L, int* stride);
@@ -303,6 +312,21 @@ PANTHER_API void panther_free_graph(panther_graph* g);
 PANTHER_API void panther_free_paths(panther_paths* p);
 PANTHER_API void panther_free_index(panther_index* ix);
 PANTHER_API void pantherpp_free_vecs(pantherpp_vecs* v);
+
+/* ---------------------------------------------------------- checkpoint --- */
+/* (No counterpart in the paper.) Write sampled paths or an index to a file
+ * and read them back, for example to serve from a saved index after a
+ * restart. File: a 64-byte header (magic "PNTHPATH"/"PNTHINDX", version 1,
+ * T, L, stride, mode, n, R, r0 or nnz, seed), then the device arrays as they
+ * are laid out in memory (little-endian). Loading validates the header and,
+ * for an index, the offsets (monotone from 0 to nnz) and path ids (< R) on
+ * the device before returning the handle. Synchronous.
+ * Errors: EINVAL (null arguments, unreadable or inconsistent file), ENOMEM,
+ * ECUDA. */
+PANTHER_API panther_status panther_save_paths(const panther_paths* p, const char* path);
+PANTHER_API panther_status panther_load_paths(panther_ctx* ctx, const char* path, panther_paths** out);
+PANTHER_API panther_status panther_save_index(const panther_index* ix, const char* path);
+PANTHER_API panther_status panther_load_index(panther_ctx* ctx, const char* path, panther_index** out);
 
 /* ------------------------------------------------------------ serving --- */
 /* (No counterpart in the paper.) A request loop over resident paths, index

@@ -59,6 +59,11 @@ SIGNATURES = {
     "panther_debug_graph_tables": ([_vp, _vp, _vp, _P(_int)], _int),
     "panther_debug_philox": ([_vp, _u32, _u32, _u64, _u32, _u32, _i64, _vp, _vp], _int),
     "panther_debug_fail_alloc": ([_vp, _i64], _int),
+    "panther_sample_paths_range": ([_vp, _vp, _u64, _i64, _i64, _int, _int, _P(_vp)], _int),
+    "panther_save_paths": ([_vp, ctypes.c_char_p], _int),
+    "panther_load_paths": ([_vp, ctypes.c_char_p, _P(_vp)], _int),
+    "panther_save_index": ([_vp, ctypes.c_char_p], _int),
+    "panther_load_index": ([_vp, ctypes.c_char_p, _P(_vp)], _int),
     "panther_debug_wait_timeout": ([_vp, _i64], _int),
     "panther_free_graph": ([_vp], None),
     "panther_free_paths": ([_vp], None),
@@ -239,6 +244,33 @@ def panther_debug_graph_tables(g: int, dev_alias16, dev_prefix):
 
 def panther_debug_philox(ctx: int, k0: int, k1: int, r0: int, c2: int, c3: int, count: int, dev_out, dev_ref):
     _check(ctx, load_library().panther_debug_philox(ctx, k0, k1, r0, c2, c3, count, _ptr(dev_out), _ptr(dev_ref)))
+
+
+def panther_sample_paths_range(ctx: int, g: int, seed: int, r0: int, R: int, T: int, mode: int) -> int:
+    """Paths r0 .. r0+R-1 of the sequence of `seed` (row i = path r0 + i)."""
+    out = _vp()
+    _check(ctx, load_library().panther_sample_paths_range(ctx, g, seed, r0, R, T, mode, ctypes.byref(out)))
+    return out.value
+
+
+def panther_save_paths(p: int, path: str) -> None:
+    _check(None, load_library().panther_save_paths(p, os.fsencode(path)))
+
+
+def panther_load_paths(ctx: int, path: str) -> int:
+    out = _vp()
+    _check(ctx, load_library().panther_load_paths(ctx, os.fsencode(path), ctypes.byref(out)))
+    return out.value
+
+
+def panther_save_index(ix: int, path: str) -> None:
+    _check(None, load_library().panther_save_index(ix, os.fsencode(path)))
+
+
+def panther_load_index(ctx: int, path: str) -> int:
+    out = _vp()
+    _check(ctx, load_library().panther_load_index(ctx, os.fsencode(path), ctypes.byref(out)))
+    return out.value
 
 
 def panther_debug_fail_alloc(ctx: int, nth: int) -> None:

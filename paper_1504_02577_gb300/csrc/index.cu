@@ -230,6 +230,17 @@ static void radix_plan(int64_t n, int* passes, int* rbits) {
     *rbits = (bits + np - 1) / np;
 }
 
+// cls and its histogram from ix->off (ix->cls, ix->cls_hist allocated)
+panther_status index_classes(panther_ctx* ctx, panther_index* ix) {
+    cudaStream_t s = ctx->stream;
+    PCK(ctx, cudaMemsetAsync(ix->cls_hist, 0, sizeof(int64_t) * 256, s));
+    cls_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ix->n, 256), (int64_t)ctx->num_sms * 8)),
+                 256, 0, s>>>(ix->off, ix->n, ix->cls, (unsigned long long*)ix->cls_hist);
+    ctx->launches++;
+    PCK(ctx, cudaGetLastError());
+    return PANTHER_OK;
+}
+
 extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_paths* p, panther_index** out) {
     if (!ctx || !p || !out) return PANTHER_EINVAL;
     *out = nullptr;
@@ -244,6 +255,7 @@ extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_pa
     panther_index* ix = new panther_index();
     ix->ctx = ctx;
     ix->n = n;
+    ix->R = p->R;
     int32_t *kA = nullptr, *vA = nullptr, *kB = nullptr, *vB = nullptr;
     int64_t *counts = nullptr, *offs = nullptr, *tot = nullptr;
     panther_status st;
@@ -310,14 +322,12 @@ extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_pa
     }
     ix->nnz = count;
     offsets_kernel<<<(unsigned)ceil_div(count + 1, 256), 256, 0, s>>>(ik, count, n, ix->off, ctx->d_status);
-    if (cudaError_t e = cudaMemsetAsync(ix->cls_hist, 0, sizeof(int64_t) * 256, s)) {
+    ctx->launches++;
+    if ((st = index_classes(ctx, ix))) {
         cleanup();
         panther_free_index(ix);
-        return cuda_err(ctx, e, "index classes");
+        return st;
     }
-    cls_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->num_sms * 8), 256, 0, s>>>(
-        ix->off, n, ix->cls, (unsigned long long*)ix->cls_hist);
-    ctx->launches += 2;
     // keep the final value array as pid; release everything else
     ix->pid = iv;
     if (iv == vA) vA = nullptr; else vB = nullptr;

@@ -58,12 +58,14 @@ struct panther_paths {
     int64_t n = 0, R = 0;
     int T = 0, L = 0, stride = 0, mode = 0;
     uint64_t seed = 0;
+    int64_t r0 = 0;                  // global id of local row 0 (draw counters use r0 + row)
     int32_t* rows = nullptr;         // [R][stride]
 };
 
 struct panther_index {
     panther_ctx* ctx = nullptr;
     int64_t n = 0, nnz = 0;
+    int64_t R = 0;                   // rows of the paths its ids refer to
     int64_t* off = nullptr;          // [n+1]
     int32_t* pid = nullptr;          // [nnz]
     uint8_t* cls = nullptr;          // [n] min(|P_v|, 255): an upper bound of any count with v
@@ -116,6 +118,9 @@ static inline int path_stride(int L) { return L <= 8 ? 8 : (L <= 16 ? 16 : 32); 
 
 // device-wide exclusive scan of int64 values (in place), n >= 1; uses scratch
 panther_status scan_exclusive_i64(panther_ctx* ctx, int64_t* data, int64_t n);
+
+// the index's per-vertex path-count classes (cls, cls_hist) from its offsets
+panther_status index_classes(panther_ctx* ctx, panther_index* ix);
 
 // ---------------------------------------------------------- device helpers ---
 #ifdef __CUDACC__

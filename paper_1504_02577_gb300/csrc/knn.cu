@@ -973,7 +973,8 @@ extern "C" panther_status pantherpp_vectors(panther_ctx* ctx, const panther_inde
     if (!ctx || !ix || !p || !out) return PANTHER_EINVAL;
     *out = nullptr;
     if (D < 1 || D > 64) return set_err(ctx, PANTHER_EINVAL, "D must be in [1, 64]");
-    if (ix->n != p->n) return set_err(ctx, PANTHER_EINVAL, "index and paths belong to different graphs");
+    if (ix->n != p->n || ix->R != p->R)
+        return set_err(ctx, PANTHER_EINVAL, "index and paths do not belong together");
     cudaSetDevice(ctx->device);
     cudaStream_t s = ctx->stream;
     const int64_t n = ix->n;

@@ -50,14 +50,14 @@ __device__ __forceinline__ uint32_t pick_prefix64(const uint4* __restrict__ e, u
 // MODE 1 = prefix, 2 = alias
 template <int MODE, bool WIDE, int STRIDE>
 __global__ void __launch_bounds__(256) sample_kernel(const uint4* __restrict__ vrec, const void* __restrict__ tab,
-                                                     int64_t n, uint64_t seed, int64_t R, int T,
+                                                     int64_t n, uint64_t seed, int64_t r0, int64_t R, int T,
                                                      int32_t* __restrict__ rows, uint32_t* status) {
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += nthreads) {
         int32_t p[STRIDE];
         uint64_t v = 0;
         for (uint32_t att = 0;; ++att) {
-            pword4 x = path_draw(seed, (uint64_t)r, 0, att);
+            pword4 x = path_draw(seed, (uint64_t)(r0 + r), 0, att);
             if (lemire64((uint64_t)x.x | ((uint64_t)x.y << 32), (uint64_t)n, &v)) break;
         }
         p[0] = (int32_t)v;
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256) sample_kernel(const uint4* __restrict__ v
                     if (MODE == 1) {
                         uint64_t x = 0;
                         for (uint32_t att = 0;; ++att) {
-                            pword4 w = path_draw(seed, (uint64_t)r, (uint32_t)t, att);
+                            pword4 w = path_draw(seed, (uint64_t)(r0 + r), (uint32_t)t, att);
                             if (lemire64((uint64_t)w.x | ((uint64_t)w.y << 32), S, &x)) break;
                         }
                         if (WIDE)
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256) sample_kernel(const uint4* __restrict__ v
                     } else {
                         uint64_t c = 0, u = 0;
                         for (uint32_t att = 0;; ++att) {
-                            pword4 w = path_draw(seed, (uint64_t)r, (uint32_t)t, att);
+                            pword4 w = path_draw(seed, (uint64_t)(r0 + r), (uint32_t)t, att);
                             bool ok0 = lemire64((uint64_t)w.x | ((uint64_t)w.y << 32), (uint64_t)rec.y, &c);
                             bool ok1 = lemire64((uint64_t)w.z | ((uint64_t)w.w << 32), S, &u);
                             if (ok0 && ok1) break;
@@ -106,24 +106,25 @@ __global__ void __launch_bounds__(256) sample_kernel(const uint4* __restrict__ v
 }
 
 template <int MODE, bool WIDE>
-void launch_sample(panther_ctx* ctx, const panther_graph* g, const void* tab, uint64_t seed, int64_t R, int T,
-                   int stride, int32_t* rows, unsigned blocks) {
+void launch_sample(panther_ctx* ctx, const panther_graph* g, const void* tab, uint64_t seed, int64_t r0, int64_t R,
+                   int T, int stride, int32_t* rows, unsigned blocks) {
     cudaStream_t s = ctx->stream;
     if (stride == 8)
-        sample_kernel<MODE, WIDE, 8><<<blocks, 256, 0, s>>>(g->vrec, tab, g->n, seed, R, T, rows, ctx->d_status);
+        sample_kernel<MODE, WIDE, 8><<<blocks, 256, 0, s>>>(g->vrec, tab, g->n, seed, r0, R, T, rows, ctx->d_status);
     else if (stride == 16)
-        sample_kernel<MODE, WIDE, 16><<<blocks, 256, 0, s>>>(g->vrec, tab, g->n, seed, R, T, rows, ctx->d_status);
+        sample_kernel<MODE, WIDE, 16><<<blocks, 256, 0, s>>>(g->vrec, tab, g->n, seed, r0, R, T, rows, ctx->d_status);
     else
-        sample_kernel<MODE, WIDE, 32><<<blocks, 256, 0, s>>>(g->vrec, tab, g->n, seed, R, T, rows, ctx->d_status);
+        sample_kernel<MODE, WIDE, 32><<<blocks, 256, 0, s>>>(g->vrec, tab, g->n, seed, r0, R, T, rows, ctx->d_status);
 }
 
 }  // namespace
 
-extern "C" panther_status panther_sample_paths(panther_ctx* ctx, const panther_graph* g, uint64_t seed, int64_t R,
-                                               int T, int mode, panther_paths** out) {
+extern "C" panther_status panther_sample_paths_range(panther_ctx* ctx, const panther_graph* g, uint64_t seed,
+                                                     int64_t r0, int64_t R, int T, int mode, panther_paths** out) {
     if (!ctx || !g || !out) return PANTHER_EINVAL;
     *out = nullptr;
     if (R < 1 || R > 0x7fffffffLL) return set_err(ctx, PANTHER_EINVAL, "R must be in [1, 2^31-1]");
+    if (r0 < 0 || r0 > INT64_MAX - R) return set_err(ctx, PANTHER_EINVAL, "r0 must be >= 0 and r0 + R < 2^63");
     if (T < 1 || T > 31) return set_err(ctx, PANTHER_EINVAL, "T must be in [1, 31]");
     if (mode != PANTHER_MODE_PREFIX && mode != PANTHER_MODE_ALIAS)
         return set_err(ctx, PANTHER_EINVAL, "mode must be PREFIX or ALIAS");
@@ -138,6 +139,7 @@ extern "C" panther_status panther_sample_paths(panther_ctx* ctx, const panther_g
     p->stride = path_stride(p->L);
     p->mode = mode;
     p->seed = seed;
+    p->r0 = r0;
     panther_status st = dev_alloc(ctx, (void**)&p->rows, sizeof(int32_t) * (size_t)R * p->stride);
     if (st) {
         delete p;
@@ -148,11 +150,11 @@ extern "C" panther_status panther_sample_paths(panther_ctx* ctx, const panther_g
     unsigned blocks = (unsigned)(want < cap ? want : cap);
     if (mode == PANTHER_MODE_PREFIX) {
         if (g->prefix_wide)
-            launch_sample<1, true>(ctx, g, g->prefix, seed, R, T, p->stride, p->rows, blocks);
+            launch_sample<1, true>(ctx, g, g->prefix, seed, r0, R, T, p->stride, p->rows, blocks);
         else
-            launch_sample<1, false>(ctx, g, g->prefix, seed, R, T, p->stride, p->rows, blocks);
+            launch_sample<1, false>(ctx, g, g->prefix, seed, r0, R, T, p->stride, p->rows, blocks);
     } else {
-        launch_sample<2, false>(ctx, g, g->alias, seed, R, T, p->stride, p->rows, blocks);
+        launch_sample<2, false>(ctx, g, g->alias, seed, r0, R, T, p->stride, p->rows, blocks);
     }
     ctx->launches++;
     cudaError_t e = cudaGetLastError();
@@ -162,4 +164,9 @@ extern "C" panther_status panther_sample_paths(panther_ctx* ctx, const panther_g
     }
     *out = p;
     return PANTHER_OK;
+}
+
+extern "C" panther_status panther_sample_paths(panther_ctx* ctx, const panther_graph* g, uint64_t seed, int64_t R,
+                                               int T, int mode, panther_paths** out) {
+    return panther_sample_paths_range(ctx, g, seed, 0, R, T, mode, out);
 }

@@ -167,6 +167,7 @@ panther_status panther_serve_create(int device, const panther_index* ix, const p
                                     int streams, panther_server** out) {
     if (!out || !ix || !p) return PANTHER_EINVAL;
     *out = nullptr;
+    if (ix->n != p->n || ix->R != p->R || (v && v->n != ix->n)) return PANTHER_EINVAL;
     if (streams < 1 || streams > 16 || max_inflight_requests < 1 || mem_budget_bytes < (1 << 20))
         return PANTHER_EINVAL;
     auto* s = new panther_server();

@@ -1686,7 +1686,8 @@ extern "C" panther_status panther_topk(panther_ctx* ctx, const panther_index* ix
     if (!ctx || !ix || !p) return PANTHER_EINVAL;
     if (q < 0 || q > 0x7fffffffLL) return set_err(ctx, PANTHER_EINVAL, "q must be in [0, 2^31)");
     if (k < 1 || k > KMAX) return set_err(ctx, PANTHER_EINVAL, "k must be in [1, 64]");
-    if (ix->n != p->n) return set_err(ctx, PANTHER_EINVAL, "index and paths belong to different graphs");
+    if (ix->n != p->n || ix->R != p->R)
+        return set_err(ctx, PANTHER_EINVAL, "index and paths do not belong together");
     if (q == 0) return PANTHER_OK;
     if (!queries || !out_ids || !out_counts) return set_err(ctx, PANTHER_EINVAL, "null query or output array");
     int mode = flags & 0xff;
@@ -1733,6 +1734,7 @@ extern "C" panther_status panther_tune_topk(panther_ctx* ctx, const panther_inde
                                             uint32_t* out_counts, int* chosen) {
     if (!ctx || !ix || !p || !queries || !out_ids || !out_counts || q < 1 || k < 1 || k > KMAX)
         return set_err(ctx, PANTHER_EINVAL, "bad tuner arguments");
+    if (ix->n != p->n || ix->R != p->R) return set_err(ctx, PANTHER_EINVAL, "index and paths do not belong together");
     cudaSetDevice(ctx->device);
     struct Shape { int threads, slots, bps; };
     const Shape cand[] = {{1024, 24576, 1}, {512, 12288, 2}, {256, 6144, 4}, {256, 4096, 6},

@@ -269,6 +269,15 @@ PANTHER_API panther_status pantherpp_vecs_view(const pantherpp_vecs* v, const ui
 PANTHER_API panther_status pantherpp_knn(panther_ctx* ctx, const pantherpp_vecs* v, const int32_t* queries,
                              int64_t q, int k, int32_t* out_ids, uint64_t* out_dist2, int flags);
 
+/* Panther++ across two networks (the paper's identity-resolution use of
+ * S_RP++ between vertices of different graphs, Sec. 3.3 / Fig. 1a): queries
+ * are vertices of vq, candidates every vertex of vc, none excluded; both
+ * vector sets have the same D. Output ids are vertices of vc. Otherwise as
+ * pantherpp_knn. Errors: EINVAL (also different D), ENOMEM, ECUDA. */
+PANTHER_API panther_status pantherpp_knn_cross(panther_ctx* ctx, const pantherpp_vecs* vq, const pantherpp_vecs* vc,
+                                               const int32_t* queries, int64_t q, int k, int32_t* out_ids,
+                                               uint64_t* out_dist2, int flags);
+
 /* Screening statistics of the last pantherpp_knn call on this context:
  * [0] pairs screened, [1] pairs sent to exact rerank, [2] max |d_hat - d|
  * observed over reranked pairs, [3] pairs whose bound was zero (exact). */

@@ -206,6 +206,22 @@ def dist2(a: np.ndarray, b: np.ndarray) -> int:
     return int(out[0])
 
 
+def knn_cross(theta_q: np.ndarray, theta_c: np.ndarray, v: int, k: int):
+    """Panther++ across two graphs (Sec. 3.3's S_RP++ between theta(v) of one
+    network and every theta(u) of another): the k vertices u of the second by
+    (squared L2 asc, id asc); no vertex is excluded. Plain definition in
+    integers (numpy), padded with (-1, UINT64_MAX)."""
+    a = np.asarray(theta_q, dtype=np.int64)[v]
+    b = np.asarray(theta_c, dtype=np.int64)
+    d2 = ((b - a) ** 2).astype(np.uint64).sum(axis=1, dtype=np.uint64)
+    order = np.lexsort((np.arange(b.shape[0]), d2))[:k]
+    ids = np.full(k, -1, dtype=np.int32)
+    dist = np.full(k, np.iinfo(np.uint64).max, dtype=np.uint64)
+    ids[:order.size] = order
+    dist[:order.size] = d2[order]
+    return ids, dist
+
+
 def knn(theta: np.ndarray, v: int, k: int):
     """Sec. 3.3 / Algorithm 2: k nearest u != v by (squared L2 asc, id asc)."""
     theta = np.ascontiguousarray(theta, dtype=np.uint32)

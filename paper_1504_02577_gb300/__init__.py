@@ -55,6 +55,7 @@ SIGNATURES = {
     "pantherpp_vectors": ([_vp, _vp, _vp, _int, _P(_vp)], _int),
     "pantherpp_vecs_view": ([_vp, _P(_vp), _P(_i64), _P(_int)], _int),
     "pantherpp_knn": ([_vp, _vp, _vp, _i64, _int, _vp, _vp, _int], _int),
+    "pantherpp_knn_cross": ([_vp, _vp, _vp, _vp, _i64, _int, _vp, _vp, _int], _int),
     "pantherpp_knn_stats": ([_vp, _P(_i64)], _int),
     "panther_debug_graph_tables": ([_vp, _vp, _vp, _P(_int)], _int),
     "panther_debug_philox": ([_vp, _u32, _u32, _u64, _u32, _u32, _i64, _vp, _vp], _int),
@@ -227,6 +228,13 @@ def pantherpp_vecs_view(v: int):
 
 def pantherpp_knn(ctx: int, v: int, queries, q: int, k: int, out_ids, out_dist2, flags: int = KNN_BF16_SCREEN):
     _check(ctx, load_library().pantherpp_knn(ctx, v, _ptr(queries), q, k, _ptr(out_ids), _ptr(out_dist2), flags))
+
+
+def pantherpp_knn_cross(ctx: int, vq: int, vc: int, queries, q: int, k: int, out_ids, out_dist2,
+                        flags: int = KNN_BF16_SCREEN):
+    """Queries are vertices of vq's graph, answers vertices of vc's graph (none excluded)."""
+    _check(ctx, load_library().pantherpp_knn_cross(ctx, vq, vc, _ptr(queries), q, k, _ptr(out_ids),
+                                                   _ptr(out_dist2), flags))
 
 
 def pantherpp_knn_stats(ctx: int):

@@ -289,6 +289,7 @@ struct Row {
 
 struct RowConst {
     int qid;         // query vertex (-1: padding row)
+    int self;        // candidate id excluded from the answer (the query itself; -2 across graphs)
     bool exact;
     float anrm;      // KN_ALPHA * |a| (BF16) or 2 eps |a| (FP32)
     float2* list;    // k entries {key, id bits}
@@ -318,14 +319,14 @@ __device__ __noinline__ Row row_insert(Row r, const RowConst& c, float key, int 
 }
 
 __device__ __forceinline__ Row take_exact(Row r, const RowConst& c, float y, int cid) {
-    if (cid < 0 || cid == c.qid) return r;
+    if (cid < 0 || cid == c.self) return r;
     if (y < r.thr || (y == r.thr && cid < r.thr_id)) r = row_insert(r, c, y, cid);
     return r;
 }
 
 // a pair whose screened value carries an error bound E
 __device__ __noinline__ Row take_bounded(Row r, const RowConst& c, float y, float E, int cid, bool cexact) {
-    if (cid < 0 || cid == c.qid) return r;
+    if (cid < 0 || cid == c.self) return r;
     if (c.exact && cexact) return take_exact(r, c, y, cid);
     if (__fsub_rd(y, E) > r.thr) return r;
     if (r.scount < KN_SCAP) c.sl[r.scount] = cid; else *c.overflow = 1;
@@ -386,6 +387,7 @@ struct ScreenArgs {
     int32_t* scount;         // [qpad][nchunk][KN_SPLIT]
     int* overflow;           // [qpad]
     uint32_t* status;
+    bool exclude_self;       // queries and candidates are the same vertices
 };
 
 // shared memory map (offsets from a 1024-aligned base)
@@ -521,8 +523,8 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
             const int64_t slot = qt * KN_M + row;
             Row r{__int_as_float(0x7f800000), 0x7fffffff, 0, 0};
             const int64_t state = (slot * S.nchunk + ch) * KN_SPLIT + half;
-            const RowConst rc{S.qv[slot], S.qexact[slot] != 0, KN_ALPHA * S.qnrm[slot], mylist,
-                              S.shortlist + state * KN_SCAP, S.overflow + slot, S.k};
+            const RowConst rc{S.qv[slot], S.exclude_self ? S.qv[slot] : -2, S.qexact[slot] != 0,
+                              KN_ALPHA * S.qnrm[slot], mylist, S.shortlist + state * KN_SCAP, S.overflow + slot, S.k};
             const bool qtile_exact = S.qtile[qt] != 0;
             bool ok = true;
             for (int64_t ct = ct0; ct < ct1; ++ct, ++it) {
@@ -608,7 +610,9 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
 // |y_hat - y| <= (D+3) 2^-23 (2|a||b| + |b|^2) + 1.
 constexpr int F_T = 128, F_TILE = 32;
 
-__global__ void __launch_bounds__(F_T) fp32_kernel(const uint32_t* __restrict__ theta, int D, const int32_t* __restrict__ qv,
+__global__ void __launch_bounds__(F_T) fp32_kernel(const uint32_t* __restrict__ theta_q,
+                                                   const uint32_t* __restrict__ theta_c, bool exclude_self, int D,
+                                                   const int32_t* __restrict__ qv,
                                                    const uint8_t* __restrict__ qexact, const float* __restrict__ qnrm,
                                                    int64_t qpad, int64_t nexact,
                                                    const int32_t* __restrict__ cidv, const float* __restrict__ cnrmv,
@@ -625,18 +629,19 @@ __global__ void __launch_bounds__(F_T) fp32_kernel(const uint32_t* __restrict__ 
     // rows with every entry <= 256 give exact FP32 products and partial sums
     // (all integers below 2^24); other pairs carry the bound
     const bool qex = slot < qpad && qexact[slot] != 0;
-    const RowConst rc{qid, qex, 2.0f * epsD * (slot < qpad ? qnrm[slot] : 0.f), lst + threadIdx.x * KN_KMAX,
-                      shortlist + (slot < qpad ? slot : 0) * KN_SPLIT * KN_SCAP, overflow + (slot < qpad ? slot : 0), k};
+    const RowConst rc{qid, exclude_self ? qid : -2, qex, 2.0f * epsD * (slot < qpad ? qnrm[slot] : 0.f),
+                      lst + threadIdx.x * KN_KMAX, shortlist + (slot < qpad ? slot : 0) * KN_SPLIT * KN_SCAP,
+                      overflow + (slot < qpad ? slot : 0), k};
     Row r{__int_as_float(0x7f800000), 0x7fffffff, 0, 0};
     float a[KN_K];
 #pragma unroll
-    for (int d = 0; d < KN_K; ++d) a[d] = (qid >= 0 && d < D) ? (float)theta[(int64_t)qid * D + d] : 0.f;
+    for (int d = 0; d < KN_K; ++d) a[d] = (qid >= 0 && d < D) ? (float)theta_q[(int64_t)qid * D + d] : 0.f;
     for (int64_t c0 = 0; c0 < npad; c0 += F_TILE) {
         __syncthreads();
         for (int i = threadIdx.x; i < F_TILE * KN_K; i += F_T) {
             int c = i / KN_K, d = i % KN_K;
             int32_t v = cidv[c0 + c];
-            cb[c][d] = (v >= 0 && d < D) ? (float)theta[(int64_t)v * D + d] : 0.f;
+            cb[c][d] = (v >= 0 && d < D) ? (float)theta_c[(int64_t)v * D + d] : 0.f;
         }
         if (threadIdx.x < F_TILE) {
             cidx[threadIdx.x] = cidv[c0 + threadIdx.x];
@@ -665,10 +670,12 @@ __global__ void __launch_bounds__(F_T) fp32_kernel(const uint32_t* __restrict__ 
 }
 
 // ------------------------------------------------------------- rerank ---
-__device__ __forceinline__ uint64_t exact_d2(const uint32_t* __restrict__ theta, int D, int32_t a, int32_t b) {
+// exact squared distance between row a of theta_q and row b of theta_c
+__device__ __forceinline__ uint64_t exact_d2(const uint32_t* __restrict__ theta_q, const uint32_t* __restrict__ theta_c,
+                                             int D, int32_t a, int32_t b) {
     uint64_t s = 0;
-    const uint32_t* x = theta + (int64_t)a * D;
-    const uint32_t* y = theta + (int64_t)b * D;
+    const uint32_t* x = theta_q + (int64_t)a * D;
+    const uint32_t* y = theta_c + (int64_t)b * D;
     for (int d = 0; d < D; ++d) {
         int64_t t = (int64_t)x[d] - (int64_t)y[d];
         s += (uint64_t)(t * t);
@@ -683,7 +690,8 @@ __device__ __forceinline__ bool pair_less(uint64_t d1, int i1, uint64_t d2, int 
 // One warp per (query slot, candidate range): exact distances of every kept
 // candidate, top-k of the range. With one range per query the rows go to the
 // output; otherwise to part_d2 / part_id ([qpad][nchunk][k]) for chunk_merge.
-__global__ void rerank_kernel(const uint32_t* __restrict__ theta, int D, const int32_t* __restrict__ qv,
+__global__ void rerank_kernel(const uint32_t* __restrict__ theta_q, const uint32_t* __restrict__ theta_c, int D,
+                              const int32_t* __restrict__ qv,
                               const int32_t* __restrict__ qidx, int64_t qpad, int64_t nchunk, int k,
                               const float2* __restrict__ lists, const int32_t* __restrict__ shortlist,
                               const int32_t* __restrict__ scount, const int* __restrict__ overflow,
@@ -727,7 +735,7 @@ __global__ void rerank_kernel(const uint32_t* __restrict__ theta, int D, const i
             }
             if (c >= 0) {
                 id[t] = c;
-                dd[t] = exact_d2(theta, D, v, c);
+                dd[t] = exact_d2(theta_q, theta_c, D, v, c);
             }
         }
     }
@@ -844,7 +852,9 @@ __global__ void __launch_bounds__(256) chunk_merge_kernel(const int32_t* __restr
 // A warp keeps its k best (d2, id) sorted across its lanes (lane l holds rank
 // l); a batch of 32 candidates costs one compare and a ballot unless one of
 // them beats the k-th entry. The nparts lists go through chunk_merge_kernel.
-__global__ void __launch_bounds__(256) brute_warp_kernel(const uint32_t* __restrict__ theta, int D, int64_t n,
+__global__ void __launch_bounds__(256) brute_warp_kernel(const uint32_t* __restrict__ theta_q,
+                                                         const uint32_t* __restrict__ theta_c, bool exclude_self,
+                                                         int D, int64_t n,
                                                          const int32_t* __restrict__ qv,
                                                          const int32_t* __restrict__ ovslots, int64_t nov,
                                                          int64_t nparts, int k, int32_t* __restrict__ part_id,
@@ -860,10 +870,11 @@ __global__ void __launch_bounds__(256) brute_warp_kernel(const uint32_t* __restr
     for (int64_t base = u0; base < u1; base += 32) {
         const int64_t u = base + lane;
         uint64_t d = ~0ull;
-        if (u < u1 && u != v) d = exact_d2(theta, D, v, (int32_t)u);
+        const bool cand = u < u1 && (!exclude_self || u != v);
+        if (cand) d = exact_d2(theta_q, theta_c, D, v, (int32_t)u);
         const uint64_t td = __shfl_sync(0xffffffffu, ld, k - 1);
         const int ti = __shfl_sync(0xffffffffu, li, k - 1);
-        unsigned pass = __ballot_sync(0xffffffffu, u < u1 && u != v && pair_less(d, (int)u, td, ti));
+        unsigned pass = __ballot_sync(0xffffffffu, cand && pair_less(d, (int)u, td, ti));
         while (pass) {
             const int src = __ffs(pass) - 1;
             pass &= pass - 1;
@@ -1068,11 +1079,14 @@ static int64_t knn_ranges(int64_t nqt, int64_t nct, int num_sms, bool fp32) {
     return best;
 }
 
-static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* v, const int32_t* queries, int64_t q, int k,
-                              int32_t* ids, uint64_t* d2, bool fp32) {
-    const pantherpp_vecs& x = *v;
+// queries are vertices of vq, candidates every vertex of vc; `same` excludes
+// the candidate with the query's id (one graph: the query itself)
+static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* vq, const pantherpp_vecs* vc, bool same,
+                              const int32_t* queries, int64_t q, int k, int32_t* ids, uint64_t* d2, bool fp32) {
+    const pantherpp_vecs& x = *vc;
+    const pantherpp_vecs* v = vq;
     cudaStream_t s = ctx->stream;
-    const int64_t n = v->n;
+    const int64_t n = vq->n;
     const int64_t qpad = ceil_div(q, KN_M) * KN_M;
     const int64_t nch = knn_ranges(qpad / KN_M, x.npad / KN_N, ctx->num_sms, fp32);
     panther_status st;
@@ -1137,18 +1151,20 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* v, const i
             return PANTHER_ECUDA;
         }
         ScreenArgs S{x.cid, x.cnrm, x.cncf, x.ctile, x.npad / KN_N, x.nexact, qv, qn, qex, qtile, qpad / KN_M,
-                     nch, k, lists, sl, sc, ovf, ctx->d_status};
+                     nch, k, lists, sl, sc, ovf, ctx->d_status, same};
         PCK(ctx, cudaFuncSetAttribute(screen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KN_SMEM_BYTES));
         int64_t grid = std::min<int64_t>(qpad / KN_M * nch, ctx->num_sms);
         screen_kernel<<<(unsigned)grid, KN_THREADS, KN_SMEM_BYTES, s>>>(tmA, tmB, S);
         ctx->launches++;
     } else {
-        fp32_kernel<<<(unsigned)(qpad / F_T), F_T, 0, s>>>(v->theta, v->D, qv, qex, qn, qpad, x.nexact, x.cid,
+        fp32_kernel<<<(unsigned)(qpad / F_T), F_T, 0, s>>>(vq->theta, vc->theta, same, v->D, qv, qex, qn, qpad,
+                                                            x.nexact, x.cid,
                                                             x.cnrm, x.cncf, x.npad, k, lists, sl, sc, ovf);
         ctx->launches++;
     }
     PCK(ctx, cudaGetLastError());
-    rerank_kernel<<<(unsigned)ceil_div(qpad * nch * 32, 256), 256, 0, s>>>(v->theta, v->D, qv, qidx, qpad, nch, k,
+    rerank_kernel<<<(unsigned)ceil_div(qpad * nch * 32, 256), 256, 0, s>>>(vq->theta, vc->theta, v->D, qv, qidx,
+                                                                            qpad, nch, k,
                                                                             lists, sl, sc, ovf, ids, d2, pid, pd);
     ctx->launches++;
     if (nch > 1) {
@@ -1171,7 +1187,7 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* v, const i
     over = (int64_t)hslots.size();
     if (over) {
         // the overflowed queries: exact brute force over all vertices, spread over the GPU
-        const int64_t nparts = std::max<int64_t>(1, std::min<int64_t>(1024, ceil_div(n, 4096)));
+        const int64_t nparts = std::max<int64_t>(1, std::min<int64_t>(1024, ceil_div(vc->n, 4096)));
         int32_t* dsl = nullptr;
         int32_t* bid = nullptr;
         uint64_t* bd = nullptr;
@@ -1186,7 +1202,7 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* v, const i
         cudaError_t ce = cudaMemcpyAsync(dsl, hslots.data(), sizeof(int32_t) * over, cudaMemcpyHostToDevice, s);
         if (!ce) {
             brute_warp_kernel<<<(unsigned)ceil_div(over * nparts * 32, 256), 256, 0, s>>>(
-                v->theta, v->D, n, qv, dsl, over, nparts, k, bid, bd);
+                vq->theta, vc->theta, same, v->D, vc->n, qv, dsl, over, nparts, k, bid, bd);
             chunk_merge_kernel<<<(unsigned)std::min<int64_t>(over, 8 * ctx->num_sms), 256, 0, s>>>(
                 qv, qidx, ovf, dsl, over, nparts, k, bid, bd, ids, d2);
             ctx->launches += 2;
@@ -1199,7 +1215,7 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* v, const i
             return cuda_err(ctx, ce, "k-NN brute-force fallback");
         }
     }
-    ctx->knn_stats[0] = q * n;
+    ctx->knn_stats[0] = q * vc->n;
     ctx->knn_stats[1] = kept;
     ctx->knn_stats[2] = over;
     ctx->knn_stats[3] = x.nexact;
@@ -1207,9 +1223,11 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* v, const i
     return PANTHER_OK;
 }
 
-extern "C" panther_status pantherpp_knn(panther_ctx* ctx, const pantherpp_vecs* v, const int32_t* queries, int64_t q,
-                                        int k, int32_t* out_ids, uint64_t* out_dist2, int flags) {
-    if (!ctx || !v) return PANTHER_EINVAL;
+static panther_status knn_entry(panther_ctx* ctx, const pantherpp_vecs* v, const pantherpp_vecs* vc, bool same,
+                                const int32_t* queries, int64_t q, int k, int32_t* out_ids, uint64_t* out_dist2,
+                                int flags) {
+    if (!ctx || !v || !vc) return PANTHER_EINVAL;
+    if (vc->D != v->D) return set_err(ctx, PANTHER_EINVAL, "query and candidate vectors differ in D");
     if (q < 0 || q > 0x7fffffffLL) return set_err(ctx, PANTHER_EINVAL, "q must be in [0, 2^31)");
     if (k < 1 || k > KN_KMAX) return set_err(ctx, PANTHER_EINVAL, "k must be in [1, 32]");
     int mode = flags & 0xff;
@@ -1228,7 +1246,7 @@ extern "C" panther_status pantherpp_knn(panther_ctx* ctx, const pantherpp_vecs* 
         uint64_t* dd = (uint64_t*)((char*)buf + qb + ((ib + 15) / 16) * 16);
         int32_t* di = (int32_t*)((char*)buf + qb);
         PCK(ctx, cudaMemcpyAsync(buf, queries, sizeof(int32_t) * q, cudaMemcpyHostToDevice, s));
-        st = knn_run(ctx, v, buf, q, k, di, dd, mode == PANTHER_KNN_FP32);
+        st = knn_run(ctx, v, vc, same, buf, q, k, di, dd, mode == PANTHER_KNN_FP32);
         if (!st) {
             PCK(ctx, cudaMemcpyAsync(out_ids, di, ib, cudaMemcpyDeviceToHost, s));
             PCK(ctx, cudaMemcpyAsync(out_dist2, dd, db, cudaMemcpyDeviceToHost, s));
@@ -1237,7 +1255,18 @@ extern "C" panther_status pantherpp_knn(panther_ctx* ctx, const pantherpp_vecs* 
         dev_free(ctx, buf);
         return st;
     }
-    return knn_run(ctx, v, queries, q, k, out_ids, out_dist2, mode == PANTHER_KNN_FP32);
+    return knn_run(ctx, v, vc, same, queries, q, k, out_ids, out_dist2, mode == PANTHER_KNN_FP32);
+}
+
+extern "C" panther_status pantherpp_knn(panther_ctx* ctx, const pantherpp_vecs* v, const int32_t* queries, int64_t q,
+                                        int k, int32_t* out_ids, uint64_t* out_dist2, int flags) {
+    return knn_entry(ctx, v, v, true, queries, q, k, out_ids, out_dist2, flags);
+}
+
+extern "C" panther_status pantherpp_knn_cross(panther_ctx* ctx, const pantherpp_vecs* vq, const pantherpp_vecs* vc,
+                                              const int32_t* queries, int64_t q, int k, int32_t* out_ids,
+                                              uint64_t* out_dist2, int flags) {
+    return knn_entry(ctx, vq, vc, false, queries, q, k, out_ids, out_dist2, flags);
 }
 
 extern "C" panther_status pantherpp_knn_stats(panther_ctx* ctx, int64_t stats[4]) {

@@ -170,3 +170,49 @@ def test_knn_workload_shape_sampled(pk):
         for i, v in enumerate(q):
             rid, rd = oracle.knn(th, int(v), kk)
             assert ids[i].tolist() == rid.tolist() and d2[i].tolist() == rd.tolist(), (key, i)
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_knn_cross_graph(pk, fp32):
+    # two different networks (a dense one with inexact rows, a sparser one),
+    # queries from the first, answers from the second, both forms exact; and
+    # the same vector set on both sides keeps the query itself at distance 0
+    ga = synth.chung_lu(900, 10, 2.4, ("uniform", 1, 20), seed=31)
+    gb = synth.chung_lu(1300, 8, 2.2, ("loguniform", 1, 64), seed=32)
+    R, T, D, k = 120_000, 5, 24, 12
+    tha = _oracle_theta(ga, 7, R, T, D)
+    thb = _oracle_theta(gb, 8, R, T, D)
+    assert tha.max() > 256                       # some rows of the first graph are inexact in BF16
+    rng = np.random.default_rng(4)
+    q = rng.integers(0, ga.n, size=333).astype(np.int32)
+    flag = pk.KNN_FP32 if fp32 else pk.KNN_BF16_SCREEN
+    handles = []
+    ctx = pk.panther_create(0)
+    try:
+        vh = []
+        for g, seed in ((ga, 7), (gb, 8)):
+            gh = pk.panther_build_graph(ctx, g.n, g.m, g.row_ptr, g.col, g.w, pk.MEM_HOST, pk.MODE_ALIAS)
+            ph = pk.panther_sample_paths(ctx, gh, seed, R, T, pk.MODE_ALIAS)
+            ih = pk.panther_build_index(ctx, ph)
+            vh.append(pk.pantherpp_vectors(ctx, ih, ph, D))
+            handles += [(pk.panther_free_index, ih), (pk.panther_free_paths, ph), (pk.panther_free_graph, gh)]
+        ids = np.empty((q.size, k), np.int32)
+        d2 = np.empty((q.size, k), np.uint64)
+        pk.pantherpp_knn_cross(ctx, vh[0], vh[1], q, q.size, k, ids, d2, flag | pk.IO_HOST)
+        for i, v in enumerate(q):
+            rid, rd = oracle.knn_cross(tha, thb, int(v), k)
+            assert ids[i].tolist() == rid.tolist() and d2[i].tolist() == rd.tolist(), i
+        pk.pantherpp_knn_cross(ctx, vh[0], vh[0], q, q.size, k, ids, d2, flag | pk.IO_HOST)
+        for i, v in enumerate(q):
+            rid, rd = oracle.knn_cross(tha, tha, int(v), k)
+            assert ids[i].tolist() == rid.tolist() and d2[i].tolist() == rd.tolist(), i
+        bad = pk.pantherpp_vectors(ctx, handles[0][1], handles[1][1], D - 1)
+        with pytest.raises(pk.PantherError):
+            pk.pantherpp_knn_cross(ctx, vh[0], bad, q, q.size, k, ids, d2, flag | pk.IO_HOST)   # D differs
+        pk.pantherpp_free_vecs(bad)
+        for v_ in vh:
+            pk.pantherpp_free_vecs(v_)
+        for free, h in handles:
+            free(h)
+    finally:
+        pk.panther_destroy(ctx)

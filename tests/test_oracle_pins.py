@@ -391,3 +391,24 @@ def test_revisited_vertex_counted_once_per_path():
     ids, cnt = o.topk(0, 1)
     assert ids.tolist() == [1] and cnt.tolist() == [10]
     assert (np.diff(o.off) == 10).all()
+
+
+def test_knn_cross_pins():
+    # across "two graphs" that are the same one, the cross list is the
+    # self-excluded list with the query itself (distance 0) merged in; and a
+    # brute-force loop over a tiny pair of networks with ties
+    rng = np.random.default_rng(3)
+    th = rng.integers(0, 6, size=(40, 5)).astype(np.uint32)
+    for v in range(40):
+        ids, d2 = oracle.knn_cross(th, th, v, 9)
+        sid, sd2 = oracle.knn(th, v, 8)
+        keep = ids != v
+        assert ids.tolist().count(v) == 1 and d2[ids.tolist().index(v)] == 0
+        assert ids[keep].tolist() == sid.tolist() and d2[keep].tolist() == sd2.tolist()
+    a = rng.integers(0, 4, size=(7, 3)).astype(np.uint32)
+    b = rng.integers(0, 4, size=(5, 3)).astype(np.uint32)
+    for v in range(7):
+        brute = sorted((sum((int(x) - int(y)) ** 2 for x, y in zip(a[v], b[u])), u) for u in range(5))
+        ids, d2 = oracle.knn_cross(a, b, v, 7)
+        assert ids[:5].tolist() == [u for _, u in brute] and d2[:5].tolist() == [d for d, _ in brute]
+        assert ids[5:].tolist() == [-1, -1] and d2[5:].tolist() == [2**64 - 1] * 2

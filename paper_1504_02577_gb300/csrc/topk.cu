@@ -600,46 +600,74 @@ struct Tiers {
                          // g8/16/32 sizes; [9..13] the same layout as [0..4] for the big-CTA pass
 };
 
-// classification: pads trivially empty queries and sorts the rest into tiers
-__global__ void classify_kernel(const int32_t* __restrict__ queries, int64_t q, PathsRef P, int64_t ccap,
-                                int64_t ccap_big, bool lane_ok, int group_max, Tiers tiers, OutRef o,
-                                uint32_t* status) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned lane = threadIdx.x & 31;
-    int tier = -1;
-    if (i < q) {
-        int64_t v = queries ? (int64_t)queries[i] : i;
-        if (v < 0 || v >= P.n) {
-            flag_status(status, ST_BAD_QUERY);
-            atomicMin(status + 1, (uint32_t)i);
-        } else {
-            int64_t np = P.off[v + 1] - P.off[v];
-            int64_t cap = np * (P.L - 1);
-            if (cap > P.n - 1) cap = P.n - 1;
-            if (cap > 0) {
-                if (lane_ok && np <= LANE_NP) tier = 3;
-                else if (np <= 8 && np <= group_max) tier = 4;
-                else if (np <= 16 && np <= group_max) tier = 5;
-                else if (np <= 32 && np <= group_max) tier = 6;
-                else tier = cap <= WCAP ? 0 : (cap <= ccap ? 1 : (cap <= ccap_big ? 7 : 2));
-            }
-        }
-        if (tier < 0) {
-            for (int r = 0; r < o.k; ++r) {
-                if (o.ids) o.ids[i * o.k + r] = -1;
-                o.cnt[i * o.k + r] = 0;
-            }
-        }
-    }
+// classification: pads trivially empty queries and sorts the rest into tiers.
+// A CTA classifies CL_PER queries per thread (strided by the block size, so
+// loads and stores are coalesced) and reserves space in each tier list with
+// one global atomic per tier, after counting in shared memory.
+constexpr int CL_PER = 16;
+
+__global__ void __launch_bounds__(256) classify_kernel(const int32_t* __restrict__ queries, int64_t q, PathsRef P,
+                                                       int64_t ccap, int64_t ccap_big, bool lane_ok, int group_max,
+                                                       Tiers tiers, OutRef o, uint32_t* status) {
+    __shared__ unsigned tot[8];
+    __shared__ int base[8];
+    const int64_t c0 = (int64_t)blockIdx.x * blockDim.x * CL_PER;
+    int8_t tier[CL_PER];
+    if (threadIdx.x < 8) tot[threadIdx.x] = 0;
+    __syncthreads();
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-        unsigned m = __ballot_sync(0xffffffffu, tier == t);
-        if (!m) continue;
-        int leader = __ffs(m) - 1;
-        int base = 0;
-        if ((int)lane == leader) base = atomicAdd(&tiers.count[t < 3 ? t : (t == 7 ? 10 : t + 2)], __popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (tier == t) tiers.list[t][base + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
+    for (int j = 0; j < CL_PER; ++j) {
+        const int64_t i = c0 + (int64_t)j * blockDim.x + threadIdx.x;
+        int t = -1;
+        if (i < q) {
+            const int64_t v = queries ? (int64_t)queries[i] : i;
+            if (v < 0 || v >= P.n) {
+                flag_status(status, ST_BAD_QUERY);
+                atomicMin(status + 1, (uint32_t)i);
+            } else {
+                const int64_t np = P.off[v + 1] - P.off[v];
+                int64_t cap = np * (P.L - 1);
+                if (cap > P.n - 1) cap = P.n - 1;
+                if (cap > 0) {
+                    if (lane_ok && np <= LANE_NP) t = 3;
+                    else if (np <= 8 && np <= group_max) t = 4;
+                    else if (np <= 16 && np <= group_max) t = 5;
+                    else if (np <= 32 && np <= group_max) t = 6;
+                    else t = cap <= WCAP ? 0 : (cap <= ccap ? 1 : (cap <= ccap_big ? 7 : 2));
+                }
+            }
+            if (t < 0) {
+                for (int r = 0; r < o.k; ++r) {
+                    if (o.ids) o.ids[i * o.k + r] = -1;
+                    o.cnt[i * o.k + r] = 0;
+                }
+            }
+        }
+        tier[j] = (int8_t)t;
+    }
+    // this thread's entries per tier, its offset within the CTA's share
+    unsigned mine[8], off[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) mine[t] = 0;
+#pragma unroll
+    for (int j = 0; j < CL_PER; ++j)
+#pragma unroll
+        for (int t = 0; t < 8; ++t) mine[t] += tier[j] == t ? 1u : 0u;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) off[t] = mine[t] ? atomicAdd(&tot[t], mine[t]) : 0u;
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int t = threadIdx.x;
+        base[t] = tot[t] ? atomicAdd(&tiers.count[t < 3 ? t : (t == 7 ? 10 : t + 2)], (int)tot[t]) : 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < CL_PER; ++j) {
+        const int t = tier[j];
+        if (t >= 0) {
+            const int64_t i = c0 + (int64_t)j * blockDim.x + threadIdx.x;
+            tiers.list[t][base[t] + off[t]++] = (int32_t)i;
+        }
     }
 }
 
@@ -1559,8 +1587,8 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
                           : ix->n <= (int64_t(1) << group_ub(16)) ? 16 : 0;
     const bool lane_ok = p->stride == 8 && k <= LANE_K;
     PCK(ctx, cudaMemsetAsync(counts, 0, sizeof(int) * 16, s));
-    classify_kernel<<<(unsigned)ceil_div(q, 256), 256, 0, s>>>(queries, q, P, ccap, ccap_big, lane_ok, group_max,
-                                                                tiers, o, ctx->d_status);
+    classify_kernel<<<(unsigned)ceil_div(q, 256 * CL_PER), 256, 0, s>>>(queries, q, P, ccap, ccap_big, lane_ok,
+                                                                         group_max, tiers, o, ctx->d_status);
     ctx->launches++;
     // the lane and group tiers are independent of the persistent passes: they
     // run on the side streams (joined back into `s` below)

@@ -203,6 +203,7 @@ def run_ours(args, ws, rank, local):
     import paper_1504_02577_gb300 as pk
 
     torch.cuda.set_device(local)
+    MODE = pk.MODE_ALIAS if args.mode == "alias" else pk.MODE_PREFIX
     p = dict(synth.WORKLOADS[args.workload])
     if args.n:
         if "R" in p:
@@ -231,9 +232,9 @@ def run_ours(args, ws, rank, local):
         s = P.stream
         e = [ev() for _ in range(5)] if record is not None else None
         if e: e[0].record(s)
-        P.build_graph(d_rp, d_col, d_w, pk.MODE_ALIAS)
+        P.build_graph(d_rp, d_col, d_w, MODE)
         if e: e[1].record(s)
-        P.sample_paths(1, R, T, pk.MODE_ALIAS)
+        P.sample_paths(args.seed, R, T, MODE)
         if e: e[2].record(s)
         P.build_index()
         if e: e[3].record(s)
@@ -301,7 +302,7 @@ def run_ours(args, ws, rank, local):
         "vs_baseline": None, "dtype": "int32/u64 (integer counts)", "data": "synthetic",
         "config": {"workload": args.workload, "graph": f"Chung-Lu n={g.n} m={g.m} mean_deg={p['mean_deg']} "
                    f"gamma={p['gamma']} weights={p['weights'][0]}[{p['weights'][1]},{p['weights'][2]}] seed=1",
-                   "R": R, "T": T, "k": k, "queries": nq, "mode": "alias",
+                   "R": R, "T": T, "k": k, "queries": nq, "mode": args.mode, "seed": args.seed,
                    "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (graph and paths)"},
         "paths_sampled_per_s": round(ws * R / (stage_ms["sample"] * 1e-3), 1),
         "stages": stage_obj,
@@ -377,8 +378,9 @@ def e2e(pk, torch, P, g, R, T, k, q_host, args, ws):
     ctx = P.h.ctx
 
     def step():
-        gh = pk.panther_build_graph(ctx, g.n, g.m, rp, col, w, pk.MEM_HOST, pk.MODE_ALIAS)
-        ph = pk.panther_sample_paths(ctx, gh, 1, R, T, pk.MODE_ALIAS)
+        mode = pk.MODE_ALIAS if args.mode == "alias" else pk.MODE_PREFIX
+        gh = pk.panther_build_graph(ctx, g.n, g.m, rp, col, w, pk.MEM_HOST, mode)
+        ph = pk.panther_sample_paths(ctx, gh, args.seed, R, T, mode)
         ih = pk.panther_build_index(ctx, ph)
         pk.panther_topk(ctx, ih, ph, qh, nq, k, ids, cnt, pk.TOPK_BATCHED | pk.IO_HOST)
         pk.panther_free_index(ih)
@@ -740,7 +742,14 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and batched-vs-plain")
     ap.add_argument("--n", type=int, default=None,
                     help="vertices (smaller case of the same shape: R scales with n; profiling only)")
+    ap.add_argument("--config", type=int, choices=[1, 2, 3, 4, 5], default=None,
+                    help="workload by number: 1 small, 2 batched, 3 scale, 4 knn, 5 serve")
+    ap.add_argument("--mode", default="alias", choices=["alias", "prefix"],
+                    help="neighbour selection of Eq. 3 for the sampler (scale/batched/small workloads)")
+    ap.add_argument("--seed", type=int, default=1, help="path seed (scale/batched/small workloads)")
     args = ap.parse_args()
+    if args.config:
+        args.workload = {1: "small", 2: "batched", 3: "scale", 4: "knn", 5: "serve"}[args.config]
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = _dist()

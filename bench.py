@@ -578,6 +578,74 @@ def run_knn(args, ws, rank, local):
     }
 
 
+# ------------------------------------------------------ parameter sweep ---
+def run_sweep(args, ws, rank, local):
+    """Throughput against the method's parameters on a 5M-vertex graph of the
+    scale workload's shape (the performance side of the paper's T, k and D
+    studies): sampler and index against T, top-k against T and k, Panther++
+    vectors and k-NN against D. Each point: one warm-up and the median of 3."""
+    import torch
+    import synth
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_02577_gb300 as pk
+
+    torch.cuda.set_device(local)
+    n = args.n or 5_000_000
+    p = dict(synth.WORKLOADS["scale"])
+    R = max(1, p["R"] * n // p["n"])
+    g = synth.workload_graph("scale", n=n)
+    dev = f"cuda:{local}"
+    P = pk.Panther(local)
+    P.build_graph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev),
+                  torch.from_numpy(g.w.view(np.int32)).to(dev), pk.MODE_ALIAS)
+    allq = torch.arange(g.n, dtype=torch.int32, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=3):
+        fn()
+        P.sync()
+        ts = []
+        for _ in range(reps):
+            a, b = ev(), ev()
+            a.record(P.stream)
+            fn()
+            b.record(P.stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    by_T = []
+    for T in (2, 3, 5, 10, 20, 31):
+        ms_s = timed(lambda: P.sample_paths(args.seed, R, T, pk.MODE_ALIAS))
+        ms_i = timed(lambda: P.build_index())
+        ms_k = timed(lambda: P.topk(allq, 10))
+        by_T.append({"T": T, "sample_ms": round(ms_s, 3), "paths_per_s": round(R / ms_s * 1e3, 1),
+                     "index_ms": round(ms_i, 3), "topk_ms": round(ms_k, 3),
+                     "topk_queries_per_s": round(g.n / ms_k * 1e3, 1)})
+    P.sample_paths(args.seed, R, 5, pk.MODE_ALIAS)
+    P.build_index()
+    by_k = []
+    for k in (5, 10, 20, 50):
+        ms_k = timed(lambda: P.topk(allq, k))
+        by_k.append({"k": k, "topk_ms": round(ms_k, 3), "topk_queries_per_s": round(g.n / ms_k * 1e3, 1)})
+    by_D = []
+    q = torch.randint(0, g.n, (4096,), generator=torch.Generator().manual_seed(3), dtype=torch.int32).to(dev)
+    for D in (10, 25, 50):
+        ms_v = timed(lambda: P.vectors(D), reps=1)
+        ms_n = timed(lambda: P.knn(q, 10))
+        by_D.append({"D": D, "vectors_ms": round(ms_v, 3), "knn_ms_4096q": round(ms_n, 3),
+                     "knn_queries_per_s": round(4096 / ms_n * 1e3, 1)})
+    P.close()
+    best = max(r["topk_queries_per_s"] for r in by_T)
+    return {"metric": METRIC, "value": best, "unit": "queries/s (best top-k point)", "n_gpus": ws, "steps": 3,
+            "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32/u64 (integer counts)", "data": "synthetic",
+            "config": {"workload": "sweep", "graph": f"Chung-Lu n={g.n} m={g.m} (scale workload shape)", "R": R,
+                       "mode": "alias"},
+            "by_T": by_T, "by_k": by_k, "by_D": by_D}
+
+
 # --------------------------------------------------------- serving arm ---
 def _requests(n, count, rng):
     """Mixed requests: 75% top-k (k in {5,10,50}, 1-4,096 vertices, log-uniform
@@ -737,7 +805,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="scale", choices=["scale", "batched", "small", "knn", "serve"])
+    ap.add_argument("--workload", default="scale", choices=["scale", "batched", "small", "knn", "serve", "sweep"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and batched-vs-plain")
     ap.add_argument("--n", type=int, default=None,
@@ -769,6 +837,8 @@ def main():
         out = run_knn(args, ws, rank, local)
     elif args.workload == "serve":
         out = run_serve(args, ws, rank, local)
+    elif args.workload == "sweep":
+        out = run_sweep(args, ws, rank, local)
     else:
         out = run_ours(args, ws, rank, local)
     if rank == 0:

@@ -1067,7 +1067,7 @@ struct GPlan {
     const uint32_t* thr;      // [ng] count only the u with cls[u] >= thr (0: every u), or null
 };
 
-constexpr int G_PATHS = 2048;     // paths per count item
+constexpr int G_PATHS = 512;      // paths per count item (small: the tables of the queries in flight stay in L2)
 constexpr int G_SLOTS = 16384;    // slots per select item
 
 __device__ __forceinline__ int find_owner(const int64_t* pre, int ng, int64_t item) {

@@ -609,29 +609,38 @@ __device__ int64_t row_alias_prep(const G& g, int64_t start, int64_t deg, uint64
 // Pass D of the alias construction: thread `tid` of `nthreads` takes a
 // contiguous run of the smalls and of the larges (in pop order) and walks the
 // other sorted sequence forward from one binary search.
-__device__ void alias_assign(int64_t start, int64_t deg, uint64_t S, int64_t nsm, const int32_t* col,
-                             const uint32_t* w, uint4* tab, const int32_t* sidx, const uint64_t* scum, int64_t tid,
+__device__ void alias_assign(int64_t start, int64_t deg, uint64_t S, int64_t nsm, const int32_t* __restrict__ col,
+                             const uint32_t* __restrict__ w, uint4* __restrict__ tab,
+                             const int32_t* __restrict__ sidx, const uint64_t* __restrict__ scum, int64_t tid,
                              int64_t nthreads) {
     const uint64_t d = (uint64_t)deg;
     const int64_t nl = deg - nsm;
-    const uint64_t* D = scum + start;
-    const uint64_t* E = scum + start + nsm;
-    const int32_t* SI = sidx + start;
-    const int32_t* LI = sidx + start + nsm;
+    const uint64_t* __restrict__ D = scum + start;
+    const uint64_t* __restrict__ E = scum + start + nsm;
+    const int32_t* __restrict__ SI = sidx + start;
+    const int32_t* __restrict__ LI = sidx + start + nsm;
     const uint64_t Dtot = nsm ? D[nsm - 1] : 0;
     // D: table entries. Each lane takes a contiguous run and walks the other
     // sequence forward from one binary search (both sequences are sorted).
+    // The next position's index and prefix are loaded one step ahead.
     {
         int64_t per = (nsm + nthreads - 1) / nthreads;
         int64_t p0 = tid * per, p1 = p0 + per < nsm ? p0 + per : nsm;
         if (p0 < p1) {
             int64_t i = nl ? lower_bound_u64(E, nl, p0 ? D[p0 - 1] : 0) : 0;
+            int32_t jn = SI[p0];
+            uint64_t dn = p0 ? D[p0 - 1] : 0;
             for (int64_t p = p0; p < p1; ++p) {
-                uint64_t dprev = p ? D[p - 1] : 0;
+                const int32_t j = jn;
+                const uint64_t dprev = dn;
+                if (p + 1 < p1) {
+                    jn = SI[p + 1];
+                    dn = D[p];
+                }
+                const uint32_t wj = w[start + j];
+                const int32_t self = col[start + j];
                 while (i < nl && E[i] < dprev) ++i;
-                int32_t j = SI[p];
-                uint64_t q = (uint64_t)w[start + j] * d;
-                int32_t self = col[start + j];
+                const uint64_t q = (uint64_t)wj * d;
                 if (nl == 0 || i >= nl)   // cannot happen for consistent integer weights
                     tab[start + j] = make_uint4((uint32_t)S, (uint32_t)(S >> 32), (uint32_t)self, (uint32_t)self);
                 else
@@ -645,15 +654,23 @@ __device__ void alias_assign(int64_t start, int64_t deg, uint64_t S, int64_t nsm
         int64_t i0 = tid * per, i1 = i0 + per < nl ? i0 + per : nl;
         if (i0 < i1) {
             int64_t js = upper_bound_u64(D, nsm, E[i0]);
+            int32_t jn = LI[i0];
+            uint64_t en = E[i0];
             for (int64_t i = i0; i < i1; ++i) {
-                uint64_t Ei = E[i];
+                const int32_t j = jn;
+                const uint64_t Ei = en;
+                int32_t jnext = -1;
+                if (i + 1 < nl) jnext = LI[i + 1];
+                if (i + 1 < i1) {
+                    jn = jnext;
+                    en = E[i + 1];
+                }
+                const int32_t self = col[start + j];
                 while (js < nsm && D[js] <= Ei) ++js;
-                int32_t j = LI[i];
-                int32_t self = col[start + j];
                 if (Dtot > Ei && i + 1 < nl) {
                     uint64_t thr = S - (D[js] - Ei);
                     tab[start + j] = make_uint4((uint32_t)thr, (uint32_t)(thr >> 32), (uint32_t)self,
-                                                (uint32_t)col[start + LI[i + 1]]);
+                                                (uint32_t)col[start + jnext]);
                 } else {
                     tab[start + j] = make_uint4((uint32_t)S, (uint32_t)(S >> 32), (uint32_t)self, (uint32_t)self);
                 }

@@ -49,7 +49,7 @@ __device__ __forceinline__ uint32_t pick_prefix64(const uint4* __restrict__ e, u
 
 // MODE 1 = prefix, 2 = alias
 template <int MODE, bool WIDE, int STRIDE>
-__global__ void __launch_bounds__(256) sample_kernel(const uint4* __restrict__ vrec, const void* __restrict__ tab,
+__global__ void __launch_bounds__(256, 5) sample_kernel(const uint4* __restrict__ vrec, const void* __restrict__ tab,
                                                      int64_t n, uint64_t seed, int64_t r0, int64_t R, int T,
                                                      int32_t* __restrict__ rows, uint32_t* status) {
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;

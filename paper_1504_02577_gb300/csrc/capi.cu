@@ -105,6 +105,7 @@ panther_status panther_create(panther_ctx** out, int device, void* cuda_stream) 
 void panther_destroy(panther_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
+    if (ctx->hub_arena) cudaFreeAsync(ctx->hub_arena, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
     for (int i = 0; i < 2; ++i) {
         if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);

@@ -38,6 +38,11 @@ struct panther_ctx {
     // on `stream`); null when they could not be created
     cudaStream_t side[2] = {nullptr, nullptr};
     cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+    // slot arena of the hub device tables, kept between calls: all slots are
+    // EMPTY whenever hub_arena_clean (the select pass empties what it reads)
+    unsigned long long* hub_arena = nullptr;
+    int64_t hub_arena_slots = 0;
+    bool hub_arena_clean = true;
     // fault injection: the allocation numbered fail_alloc_at fails once (-1: off)
     int64_t fail_alloc_at = -1, alloc_seen = 0;
 };

@@ -1457,8 +1457,8 @@ static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int3
     const int64_t budget_slots = std::max<int64_t>(ctx->scratch_budget / 8 / 2, 1 << 20);
     const int stride = P.L <= 8 ? 8 : (P.L <= 16 ? 16 : 32);
     size_t pos = 0;
-    unsigned long long* arena = nullptr;
-    int64_t arena_slots = 0;
+    unsigned long long*& arena = ctx->hub_arena;
+    int64_t& arena_slots = ctx->hub_arena_slots;
     panther_status st;
     while (pos < hubs.size()) {
         std::vector<int32_t> rq;
@@ -1483,10 +1483,15 @@ static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int3
         if (used > arena_slots) {
             dev_free(ctx, arena);
             arena = nullptr;
+            arena_slots = 0;
             if ((st = dev_alloc(ctx, (void**)&arena, 8ull * used))) return st;
             arena_slots = used;
-            fill_empty_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(arena, used);
+            ctx->hub_arena_clean = false;
+        }
+        if (!ctx->hub_arena_clean) {   // new, or left dirty by a call that failed midway
+            fill_empty_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(arena, arena_slots);
             ctx->launches++;
+            ctx->hub_arena_clean = true;
         }
         const int rng = (int)rq.size();
         std::vector<char> hp;
@@ -1500,9 +1505,9 @@ static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int3
             (st = dev_alloc(ctx, (void**)&dredo, sizeof(int32_t) * rng))) {
             dev_free(ctx, dplan);
             dev_free(ctx, partial);
-            dev_free(ctx, arena);
             return st;
         }
+        ctx->hub_arena_clean = false;   // until the select pass of this round has run
         GPlan G{(const int32_t*)(dplan + o_q), (const int64_t*)(dplan + o_o), (const uint32_t*)(dplan + o_n),
                 (const int64_t*)(dplan + o_i), (const int64_t*)(dplan + o_s), rng, (const uint32_t*)(dplan + o_t)};
         if (stride == 8) g_count_kernel<8><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
@@ -1516,6 +1521,7 @@ static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int3
         std::vector<int32_t> hredo(rng);
         PCK(ctx, cudaMemcpyAsync(hredo.data(), dredo, sizeof(int32_t) * rng, cudaMemcpyDeviceToHost, s));
         PCK(ctx, cudaStreamSynchronize(s));   // the host plan must outlive the copy
+        ctx->hub_arena_clean = true;
         for (int i = 0; i < rng; ++i)
             if (hredo[i] >= 0) {
                 HubQuery h = rh[i];
@@ -1526,7 +1532,6 @@ static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int3
         dev_free(ctx, partial);
         dev_free(ctx, dredo);
     }
-    dev_free(ctx, arena);
     return PANTHER_OK;
 }
 

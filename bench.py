@@ -323,6 +323,7 @@ def run_ours(args, ws, rank, local):
     P.close()
 
     if rank == 0 and ws == 1 and not args.no_extras:
+        cpu_baseline(args.workload, g, R, T, k, nq)          # warm-up run (first touch of the oracle's memory)
         out["cpu_baseline"] = cpu_baseline(args.workload, g, R, T, k, nq)
     return out
 

@@ -74,22 +74,22 @@ def _src_hash(*files):
 # unchanged (SHA-256 of the files), else reported as null. The capture and its
 # command are in profiles/.
 NCU_TRAFFIC = {
-    "tables": {"bytes_5M": 5805000000, "sources": {
-        "paper_1504_02577_gb300/csrc/graph.cu": "233cfe4f2e904aa90891753f38c996dce3c9640eda0d3dc27e3d92f882ca4d0d",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "aca4f0d06be460f45980d05d27831df13bb5bff8b7fac64a642df532442ec7bb",
+    "tables": {"bytes_5M": 4892681216, "sources": {
+        "paper_1504_02577_gb300/csrc/graph.cu": "473448dff53c3cb47de34a2f40391bcc71edf6d32d9263230f88c357b91e2511",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "9cbbaed30a1574e88d850980f52d73918a6952bd11a54d3a20929c540a6a5ba4",
     }},
-    "sample": {"bytes_5M": 8110000000, "sources": {
-        "paper_1504_02577_gb300/csrc/sample.cu": "43976c4bc9502aaddf15f6ddf7661f96d906800382ada2aa31a6334152ec2d0f",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "aca4f0d06be460f45980d05d27831df13bb5bff8b7fac64a642df532442ec7bb",
+    "sample": {"bytes_5M": 8118935808, "sources": {
+        "paper_1504_02577_gb300/csrc/sample.cu": "bb26fa79f1b96c3cd0b604f4973e3a516a52c41b1659bf03f4eecd0249193d27",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "9cbbaed30a1574e88d850980f52d73918a6952bd11a54d3a20929c540a6a5ba4",
     }},
-    "index": {"bytes_5M": 3670000000, "sources": {
+    "index": {"bytes_5M": 3669294592, "sources": {
         "paper_1504_02577_gb300/csrc/index.cu": "a8c54eb31744e4cdb2ce6c05eb6ad73d3811190257dc19e34947a7cf604e8c37",
-        "paper_1504_02577_gb300/csrc/capi.cu": "8b8a4bb35b729babc0e71e778ef4151967c3e40f19dfc725de043909e564d431",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "aca4f0d06be460f45980d05d27831df13bb5bff8b7fac64a642df532442ec7bb",
+        "paper_1504_02577_gb300/csrc/capi.cu": "02fa30a2121c3c8dca2f5c7d29513b8191b1ec93498ab936e54f7efe39b61e81",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "9cbbaed30a1574e88d850980f52d73918a6952bd11a54d3a20929c540a6a5ba4",
     }},
-    "topk": {"bytes_5M": 9091000000, "sources": {
-        "paper_1504_02577_gb300/csrc/topk.cu": "bb611ad8a4cf20cb2d75b54a87a4cb51d59f830d72b5b5aebf9321ff0e1198d4",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "aca4f0d06be460f45980d05d27831df13bb5bff8b7fac64a642df532442ec7bb",
+    "topk": {"bytes_5M": 8260066304, "sources": {
+        "paper_1504_02577_gb300/csrc/topk.cu": "41237261f4440288475d15fc43b65929da69b0943c867ae76bf0f09944221e0b",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "9cbbaed30a1574e88d850980f52d73918a6952bd11a54d3a20929c540a6a5ba4",
     }},
 }
 

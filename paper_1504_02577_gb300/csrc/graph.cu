@@ -620,23 +620,21 @@ __device__ void alias_assign(int64_t start, int64_t deg, uint64_t S, int64_t nsm
     const int32_t* __restrict__ SI = sidx + start;
     const int32_t* __restrict__ LI = sidx + start + nsm;
     const uint64_t Dtot = nsm ? D[nsm - 1] : 0;
-    // D: table entries. Each lane takes a contiguous run and walks the other
-    // sequence forward from one binary search (both sequences are sorted).
-    // The next position's index and prefix are loaded one step ahead.
+    // D: table entries. Each thread takes a contiguous run and walks the
+    // other sorted sequence forward from one binary search; the run is split
+    // in two halves walked in lockstep, so two independent chains of loads
+    // are in flight.
     {
-        int64_t per = (nsm + nthreads - 1) / nthreads;
-        int64_t p0 = tid * per, p1 = p0 + per < nsm ? p0 + per : nsm;
+        const int64_t per = (nsm + nthreads - 1) / nthreads;
+        const int64_t p0 = tid * per, p1 = p0 + per < nsm ? p0 + per : nsm;
         if (p0 < p1) {
-            int64_t i = nl ? lower_bound_u64(E, nl, p0 ? D[p0 - 1] : 0) : 0;
-            int32_t jn = SI[p0];
-            uint64_t dn = p0 ? D[p0 - 1] : 0;
-            for (int64_t p = p0; p < p1; ++p) {
-                const int32_t j = jn;
-                const uint64_t dprev = dn;
-                if (p + 1 < p1) {
-                    jn = SI[p + 1];
-                    dn = D[p];
-                }
+            const int64_t pm = p0 + (p1 - p0 + 1) / 2;
+            int64_t pa = p0, pb = pm;
+            int64_t ia = nl ? lower_bound_u64(E, nl, pa ? D[pa - 1] : 0) : 0;
+            int64_t ib = (nl && pb < p1) ? lower_bound_u64(E, nl, D[pb - 1]) : 0;
+            auto small_step = [&](int64_t p, int64_t& i) {
+                const int32_t j = SI[p];
+                const uint64_t dprev = p ? D[p - 1] : 0;
                 const uint32_t wj = w[start + j];
                 const int32_t self = col[start + j];
                 while (i < nl && E[i] < dprev) ++i;
@@ -646,25 +644,25 @@ __device__ void alias_assign(int64_t start, int64_t deg, uint64_t S, int64_t nsm
                 else
                     tab[start + j] = make_uint4((uint32_t)q, (uint32_t)(q >> 32), (uint32_t)self,
                                                 (uint32_t)col[start + LI[i]]);
+            };
+            for (; pa < pm || pb < p1; ++pa, ++pb) {
+                if (pa < pm) small_step(pa, ia);
+                if (pb < p1) small_step(pb, ib);
             }
         }
     }
     {
-        int64_t per = (nl + nthreads - 1) / nthreads;
-        int64_t i0 = tid * per, i1 = i0 + per < nl ? i0 + per : nl;
+        const int64_t per = (nl + nthreads - 1) / nthreads;
+        const int64_t i0 = tid * per, i1 = i0 + per < nl ? i0 + per : nl;
         if (i0 < i1) {
-            int64_t js = upper_bound_u64(D, nsm, E[i0]);
-            int32_t jn = LI[i0];
-            uint64_t en = E[i0];
-            for (int64_t i = i0; i < i1; ++i) {
-                const int32_t j = jn;
-                const uint64_t Ei = en;
-                int32_t jnext = -1;
-                if (i + 1 < nl) jnext = LI[i + 1];
-                if (i + 1 < i1) {
-                    jn = jnext;
-                    en = E[i + 1];
-                }
+            const int64_t im = i0 + (i1 - i0 + 1) / 2;
+            int64_t xa = i0, xb = im;
+            int64_t ja = upper_bound_u64(D, nsm, E[xa]);
+            int64_t jb = xb < i1 ? upper_bound_u64(D, nsm, E[xb]) : 0;
+            auto large_step = [&](int64_t i, int64_t& js) {
+                const uint64_t Ei = E[i];
+                const int32_t j = LI[i];
+                const int32_t jnext = i + 1 < nl ? LI[i + 1] : -1;
                 const int32_t self = col[start + j];
                 while (js < nsm && D[js] <= Ei) ++js;
                 if (Dtot > Ei && i + 1 < nl) {
@@ -674,6 +672,10 @@ __device__ void alias_assign(int64_t start, int64_t deg, uint64_t S, int64_t nsm
                 } else {
                     tab[start + j] = make_uint4((uint32_t)S, (uint32_t)(S >> 32), (uint32_t)self, (uint32_t)self);
                 }
+            };
+            for (; xa < im || xb < i1; ++xa, ++xb) {
+                if (xa < im) large_step(xa, ja);
+                if (xb < i1) large_step(xb, jb);
             }
         }
     }

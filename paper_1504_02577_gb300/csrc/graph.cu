@@ -609,6 +609,8 @@ __device__ int64_t row_alias_prep(const G& g, int64_t start, int64_t deg, uint64
 // Pass D of the alias construction: thread `tid` of `nthreads` takes a
 // contiguous run of the smalls and of the larges (in pop order) and walks the
 // other sorted sequence forward from one binary search.
+constexpr int ASSIGN_WAYS = 4;
+
 __device__ void alias_assign(int64_t start, int64_t deg, uint64_t S, int64_t nsm, const int32_t* __restrict__ col,
                              const uint32_t* __restrict__ w, uint4* __restrict__ tab,
                              const int32_t* __restrict__ sidx, const uint64_t* __restrict__ scum, int64_t tid,
@@ -622,16 +624,21 @@ __device__ void alias_assign(int64_t start, int64_t deg, uint64_t S, int64_t nsm
     const uint64_t Dtot = nsm ? D[nsm - 1] : 0;
     // D: table entries. Each thread takes a contiguous run and walks the
     // other sorted sequence forward from one binary search; the run is split
-    // in two halves walked in lockstep, so two independent chains of loads
-    // are in flight.
+    // in ASSIGN_WAYS parts walked in lockstep, so as many independent chains
+    // of loads are in flight.
     {
         const int64_t per = (nsm + nthreads - 1) / nthreads;
         const int64_t p0 = tid * per, p1 = p0 + per < nsm ? p0 + per : nsm;
         if (p0 < p1) {
-            const int64_t pm = p0 + (p1 - p0 + 1) / 2;
-            int64_t pa = p0, pb = pm;
-            int64_t ia = nl ? lower_bound_u64(E, nl, pa ? D[pa - 1] : 0) : 0;
-            int64_t ib = (nl && pb < p1) ? lower_bound_u64(E, nl, D[pb - 1]) : 0;
+            constexpr int W = ASSIGN_WAYS;
+            const int64_t len = (p1 - p0 + W - 1) / W;
+            int64_t pp[W], pe[W], ii[W];
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                pp[u] = p0 + u * len < p1 ? p0 + u * len : p1;
+                pe[u] = pp[u] + len < p1 ? pp[u] + len : p1;
+                ii[u] = (nl && pp[u] < pe[u]) ? lower_bound_u64(E, nl, pp[u] ? D[pp[u] - 1] : 0) : 0;
+            }
             auto small_step = [&](int64_t p, int64_t& i) {
                 const int32_t j = SI[p];
                 const uint64_t dprev = p ? D[p - 1] : 0;
@@ -645,20 +652,25 @@ __device__ void alias_assign(int64_t start, int64_t deg, uint64_t S, int64_t nsm
                     tab[start + j] = make_uint4((uint32_t)q, (uint32_t)(q >> 32), (uint32_t)self,
                                                 (uint32_t)col[start + LI[i]]);
             };
-            for (; pa < pm || pb < p1; ++pa, ++pb) {
-                if (pa < pm) small_step(pa, ia);
-                if (pb < p1) small_step(pb, ib);
-            }
+            for (int64_t s2 = 0; s2 < len; ++s2)
+#pragma unroll
+                for (int u = 0; u < W; ++u)
+                    if (pp[u] + s2 < pe[u]) small_step(pp[u] + s2, ii[u]);
         }
     }
     {
         const int64_t per = (nl + nthreads - 1) / nthreads;
         const int64_t i0 = tid * per, i1 = i0 + per < nl ? i0 + per : nl;
         if (i0 < i1) {
-            const int64_t im = i0 + (i1 - i0 + 1) / 2;
-            int64_t xa = i0, xb = im;
-            int64_t ja = upper_bound_u64(D, nsm, E[xa]);
-            int64_t jb = xb < i1 ? upper_bound_u64(D, nsm, E[xb]) : 0;
+            constexpr int W = ASSIGN_WAYS;
+            const int64_t len = (i1 - i0 + W - 1) / W;
+            int64_t xx[W], xe[W], jj[W];
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                xx[u] = i0 + u * len < i1 ? i0 + u * len : i1;
+                xe[u] = xx[u] + len < i1 ? xx[u] + len : i1;
+                jj[u] = xx[u] < xe[u] ? upper_bound_u64(D, nsm, E[xx[u]]) : 0;
+            }
             auto large_step = [&](int64_t i, int64_t& js) {
                 const uint64_t Ei = E[i];
                 const int32_t j = LI[i];
@@ -673,10 +685,10 @@ __device__ void alias_assign(int64_t start, int64_t deg, uint64_t S, int64_t nsm
                     tab[start + j] = make_uint4((uint32_t)S, (uint32_t)(S >> 32), (uint32_t)self, (uint32_t)self);
                 }
             };
-            for (; xa < im || xb < i1; ++xa, ++xb) {
-                if (xa < im) large_step(xa, ja);
-                if (xb < i1) large_step(xb, jb);
-            }
+            for (int64_t s2 = 0; s2 < len; ++s2)
+#pragma unroll
+                for (int u = 0; u < W; ++u)
+                    if (xx[u] + s2 < xe[u]) large_step(xx[u] + s2, jj[u]);
         }
     }
 }

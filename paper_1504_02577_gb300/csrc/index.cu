@@ -190,7 +190,7 @@ __global__ void offsets_kernel(const int32_t* __restrict__ keys, int64_t nnz, in
     for (int64_t v = prev + 1; v <= cur; ++v) off[v] = i;
 }
 
-// cls[v] = min(|P_v|, 255) and its histogram (a count of v with any u never
+// cls[v] = path_code(|P_v|) and its histogram (a count of v with any u never
 // exceeds |P_v| or |P_u|)
 __global__ void cls_kernel(const int64_t* __restrict__ off, int64_t n, uint8_t* __restrict__ cls,
                            unsigned long long* __restrict__ hist) {
@@ -199,7 +199,7 @@ __global__ void cls_kernel(const int64_t* __restrict__ off, int64_t n, uint8_t* 
     __syncthreads();
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const int64_t np = off[v + 1] - off[v];
-        const uint32_t c = np < 255 ? (uint32_t)np : 255u;
+        const uint32_t c = path_code(np);
         cls[v] = (uint8_t)c;
         atomicAdd(&h[c], 1u);
     }

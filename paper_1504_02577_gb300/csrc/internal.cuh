@@ -73,8 +73,8 @@ struct panther_index {
     int64_t R = 0;                   // rows of the paths its ids refer to
     int64_t* off = nullptr;          // [n+1]
     int32_t* pid = nullptr;          // [nnz]
-    uint8_t* cls = nullptr;          // [n] min(|P_v|, 255): an upper bound of any count with v
-    int64_t* cls_hist = nullptr;     // [256] vertices per cls value
+    uint8_t* cls = nullptr;          // [n] path_code(|P_v|) (|P_v| bounds any count with v)
+    int64_t* cls_hist = nullptr;     // [256] vertices per code
 };
 
 struct pantherpp_vecs {
@@ -126,6 +126,25 @@ panther_status scan_exclusive_i64(panther_ctx* ctx, int64_t* data, int64_t n);
 
 // the index's per-vertex path-count classes (cls, cls_hist) from its offsets
 panther_status index_classes(panther_ctx* ctx, panther_index* ix);
+
+// One-byte code of a path count x = |P_v|, monotone in x: x itself below 128,
+// then 8 steps per doubling (leading bit and the 3 bits after it), 255 from
+// 15 * 2^19 on. code(x) >= c exactly when x >= code_floor(c), so a filter
+// "code >= c" keeps every vertex with at least code_floor(c) paths and drops
+// only vertices with fewer.
+__host__ __device__ inline uint32_t path_code(int64_t x) {
+    if (x < 128) return x < 0 ? 0u : (uint32_t)x;
+    int e = 0;
+    while ((x >> (e + 1)) != 0) ++e;          // leading bit, >= 7
+    if (e > 22) return 255u;
+    return 128u + 8u * (uint32_t)(e - 7) + ((uint32_t)(x >> (e - 3)) & 7u);
+}
+
+__host__ __device__ inline int64_t code_floor(uint32_t c) {
+    if (c < 128) return c;
+    const uint32_t e = 7 + (c - 128) / 8, m = (c - 128) % 8;
+    return (int64_t)(8 + m) << (e - 3);
+}
 
 // ---------------------------------------------------------- device helpers ---
 #ifdef __CUDACC__

@@ -246,7 +246,7 @@ struct PathsRef {
     const int64_t* off;
     const int32_t* pid;
     int64_t n;
-    const uint8_t* cls;   // min(|P_u|, 255) per vertex
+    const uint8_t* cls;   // path_code(|P_u|) per vertex
 };
 
 // insert the distinct vertices u != v of path r into the table (with thr > 0
@@ -1253,8 +1253,9 @@ __global__ void __launch_bounds__(B_T2) b_count_kernel(BPlan B, int k, unsigned 
 
 // after a filtered round: the k-th count c of the query over the u with
 // cls[u] >= thr is a lower bound of its true k-th count, so every u of the true
-// top-k has |P_u| >= c. If c >= thr the filtered list is the answer (-1);
-// otherwise the query is counted again with threshold c.
+// top-k has |P_u| >= c. Every dropped u has |P_u| < code_floor(thr): if
+// c >= code_floor(thr) the filtered list is the answer (-1); otherwise the
+// query is counted again with threshold path_code(c) (whose floor is <= c).
 __global__ void hub_check_kernel(const int32_t* __restrict__ qidx, const uint32_t* __restrict__ thr, int ng, OutRef o,
                                  int32_t* __restrict__ redo) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1264,7 +1265,7 @@ __global__ void hub_check_kernel(const int32_t* __restrict__ qidx, const uint32_
         return;
     }
     const uint32_t kth = o.cnt[(int64_t)qidx[i] * o.k + o.k - 1];
-    redo[i] = kth >= thr[i] ? -1 : (int32_t)kth;
+    redo[i] = (int64_t)kth >= code_floor(thr[i]) ? -1 : (int32_t)kth;
 }
 
 __global__ void g_info_kernel(const int32_t* __restrict__ list, int ng, const int32_t* __restrict__ queries,
@@ -1436,7 +1437,7 @@ static panther_status hub_buckets(panther_ctx* ctx, const PathsRef& P, const int
                 again.push_back(h);
             } else if (hredo[i] >= 0) {
                 HubQuery h = rh[i];
-                h.thr = (uint32_t)hredo[i];
+                h.thr = path_code(hredo[i]);
                 redo.push_back(h);
             }
         }
@@ -1525,7 +1526,7 @@ static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int3
         for (int i = 0; i < rng; ++i)
             if (hredo[i] >= 0) {
                 HubQuery h = rh[i];
-                h.thr = (uint32_t)hredo[i];
+                h.thr = path_code(hredo[i]);
                 redo.push_back(h);
             }
         dev_free(ctx, dplan);
@@ -1674,14 +1675,15 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
         PCK(ctx, cudaStreamSynchronize(s));
         dev_free(ctx, d_np);
         for (int t = 255; t >= 0; --t) above[t] = above[t + 1] + hist[t];
-        // First round: count only candidates u with |P_u| >= HUB_PRUNE * |P_v| / max(k, 10)
-        // (the k-th count of a hub tends to lie well above that); a query whose
-        // k-th count comes out below its threshold is counted again with that
-        // count as the threshold, which is then exact (hub_check_kernel).
+        // First round: count only candidates u with path_code(|P_u|) >=
+        // path_code(t), t = HUB_PRUNE * |P_v| / max(k, 10), which keeps every u
+        // with |P_u| >= t (the k-th count of a hub tends to lie well above t);
+        // a query whose k-th count comes out below the code's floor is counted
+        // again with that count's code, which is then exact (hub_check_kernel).
         std::vector<HubQuery> hubs(ng);
         for (int i = 0; i < ng; ++i) {
             int64_t t = (int64_t)((double)npv[i] * HUB_PRUNE / std::max(k, 10));
-            hubs[i] = HubQuery{gq[i], npv[i], (uint32_t)(t < 2 ? 0 : std::min<int64_t>(t, 255))};
+            hubs[i] = HubQuery{gq[i], npv[i], t < 2 ? 0u : path_code(t)};
         }
         // queries with a small filtered candidate bound count straight into a
         // device table (it stays in L2); the others go through the buckets

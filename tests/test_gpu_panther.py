@@ -311,10 +311,10 @@ def test_topk_group_tiers(pk, k):
 
 def test_topk_hub_threshold_retry(pk):
     # A 30,000-leaf star whose centre is a hub query: its first-round filter
-    # (candidates u with |P_u| >= 255) keeps only the twelve secondary hubs,
-    # whose counts with the centre lie far below 255, so the centre is counted
-    # again with its k-th count as the threshold (k = 10), or with no threshold
-    # at all when fewer than k candidates survive (k = 20).
+    # (candidates u with hundreds of paths or more) keeps at most the twelve
+    # secondary hubs, whose counts with the centre lie far below that, so the
+    # centre is counted again with its k-th count as the threshold, or with no
+    # threshold at all when fewer than k candidates survive.
     n = 40_000
     edges = [(0, u) for u in range(1, 30_001)]
     for s_ in range(1, 13):
@@ -332,6 +332,27 @@ def test_topk_hub_threshold_retry(pk):
         assert np.array_equal(out["ids"], rid), k
         assert np.array_equal(out["cnt"], rcnt), k
     assert rcnt[0].max() < 255        # so the first round cannot be the answer
+
+
+def test_topk_large_hub_thresholds(pk):
+    # Hubs with 1e5 to 3e5 paths: the first-round filters sit in the hundreds
+    # of paths (above the exact range of the one-byte path codes), their k-th
+    # counts in the thousands, so the filtered round is the answer; k = 40
+    # lowers the filters (k = 1 keeps those of k = 10: the divisor is at least 10)
+    g = synth.chung_lu(20_000, 12, 2.05, ("uniform", 1, 5), seed=2)
+    R, T = 2_000_000, 5
+    ref = oracle.sample_paths(g, 3, R, T, oracle.ALIAS)
+    o = oracle.Oracle(g.n, ref)
+    sizes = np.diff(o.off)
+    hubs = np.argsort(-sizes)[:40].astype(np.int32)
+    assert sizes[hubs[0]] > 250_000 and sizes[hubs[5]] > 80_000
+    q = np.concatenate([hubs, np.arange(0, g.n, 211, dtype=np.int32)]).astype(np.int32)
+    for k in (10, 40, 1):
+        out = _run(pk, g, 3, R, T, pk.MODE_ALIAS, k=k, queries=q)
+        rid, rcnt = o.topk_many(q, k)
+        assert np.array_equal(out["ids"], rid), k
+        assert np.array_equal(out["cnt"], rcnt), k
+        assert (rcnt[:6, -1] > sizes[hubs[:6]] * 0.003 * 10 / max(k, 10)).all()
 
 
 def test_topk_edge_cases(pk):

@@ -74,22 +74,22 @@ def _src_hash(*files):
 # unchanged (SHA-256 of the files), else reported as null. The capture and its
 # command are in profiles/.
 NCU_TRAFFIC = {
-    "tables": {"bytes_5M": 4892681216, "sources": {
-        "paper_1504_02577_gb300/csrc/graph.cu": "473448dff53c3cb47de34a2f40391bcc71edf6d32d9263230f88c357b91e2511",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "9cbbaed30a1574e88d850980f52d73918a6952bd11a54d3a20929c540a6a5ba4",
+    "tables": {"bytes_5M": 4334776832, "sources": {
+        "paper_1504_02577_gb300/csrc/graph.cu": "cb2f60dba3f39f195ad950a0c67bd3a661d82192ddfd509d08ce46f356187992",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "dca6f273b85f41c4c763fd5a411da0ded671711cdfca0dd8552cf5610bef03dd",
     }},
-    "sample": {"bytes_5M": 8118935808, "sources": {
+    "sample": {"bytes_5M": 8120454400, "sources": {
         "paper_1504_02577_gb300/csrc/sample.cu": "bb26fa79f1b96c3cd0b604f4973e3a516a52c41b1659bf03f4eecd0249193d27",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "9cbbaed30a1574e88d850980f52d73918a6952bd11a54d3a20929c540a6a5ba4",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "dca6f273b85f41c4c763fd5a411da0ded671711cdfca0dd8552cf5610bef03dd",
     }},
-    "index": {"bytes_5M": 3669294592, "sources": {
-        "paper_1504_02577_gb300/csrc/index.cu": "a8c54eb31744e4cdb2ce6c05eb6ad73d3811190257dc19e34947a7cf604e8c37",
+    "index": {"bytes_5M": 3670223104, "sources": {
+        "paper_1504_02577_gb300/csrc/index.cu": "59a2f95b2a6ee446be3490e6950823c9994516b3420c1fdb8387795ddbafab74",
         "paper_1504_02577_gb300/csrc/capi.cu": "02fa30a2121c3c8dca2f5c7d29513b8191b1ec93498ab936e54f7efe39b61e81",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "9cbbaed30a1574e88d850980f52d73918a6952bd11a54d3a20929c540a6a5ba4",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "dca6f273b85f41c4c763fd5a411da0ded671711cdfca0dd8552cf5610bef03dd",
     }},
-    "topk": {"bytes_5M": 8260066304, "sources": {
-        "paper_1504_02577_gb300/csrc/topk.cu": "41237261f4440288475d15fc43b65929da69b0943c867ae76bf0f09944221e0b",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "9cbbaed30a1574e88d850980f52d73918a6952bd11a54d3a20929c540a6a5ba4",
+    "topk": {"bytes_5M": 8252432384, "sources": {
+        "paper_1504_02577_gb300/csrc/topk.cu": "9e31bea4a2ee3f2d1018f24be906b13eb9f8adafd7e6642d6a9354dd2b3ae294",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "dca6f273b85f41c4c763fd5a411da0ded671711cdfca0dd8552cf5610bef03dd",
     }},
 }
 

@@ -339,26 +339,45 @@ PANTHER_API panther_status panther_load_index(panther_ctx* ctx, const char* path
 
 /* ------------------------------------------------------------ serving --- */
 /* (No counterpart in the paper.) A request loop over resident paths, index
- * and vectors. Requests arrive from any host thread; a scheduler thread
- * admits them while their device bytes fit the memory budget and slots are
- * free, batches admitted top-k requests into one launch, and keeps up to
- * `streams` batches in flight on separate streams, so that new requests
- * start while earlier ones run. Results are identical to a call made alone.
+ * and vectors. Requests arrive from any host thread. `streams` worker
+ * threads each own a context (one CUDA stream) and device buffers sized from
+ * mem_budget_bytes. A free worker takes the oldest pending request and every
+ * later pending request of the same kind whose queries still fit its buffers
+ * (FIFO), runs them as ONE batched call with k = the largest k among them,
+ * and hands each request the first k entries of its rows. Ranking is a total
+ * order, so a result in the mix is identical to the same request made alone.
+ * Up to `streams` batches run at once, so new requests start while earlier
+ * ones are on the GPU.
  *
- * kind: 0 = top-k (Algorithm 1), 1 = Panther++ k-NN. Queries and outputs are
- * host pointers owned by the caller and must stay valid until the request
- * completes (panther_serve_wait returns). */
+ * panther_serve_create: ix and p must belong together (same n and R), v
+ *   (optional, needed for k-NN) must have the same n; streams in [1, 16];
+ *   max_inflight_requests >= 1; mem_budget_bytes >= 1 MiB. The handles stay
+ *   owned by the caller and must outlive the server. EINVAL on bad
+ *   arguments, ENOMEM when the budget or the device cannot hold the buffers.
+ * panther_serve_submit: kind 0 = top-k (Algorithm 1, k in [1, 64], out_vals
+ *   uint32 counts), 1 = Panther++ k-NN (Sec. 3.3, k in [1, 32], out_vals
+ *   uint64 squared distances). queries[q] (ids in [0, n)), out_ids[q][k] and
+ *   out_vals[q][k] are HOST pointers owned by the caller; they must stay
+ *   valid until panther_serve_wait has returned for the ticket. EINVAL on bad
+ *   arguments (checked before queueing); EBUSY when max_inflight_requests
+ *   requests are open, when q exceeds one worker's buffers, or after
+ *   destroy has begun. */
 PANTHER_API panther_status panther_serve_create(int device, const panther_index* ix, const panther_paths* p,
                                     const pantherpp_vecs* v, int64_t mem_budget_bytes,
                                     int max_inflight_requests, int streams, panther_server** out);
 PANTHER_API panther_status panther_serve_submit(panther_server* s, int kind, const int32_t* queries, int64_t q,
                                     int k, int32_t* out_ids, void* out_vals, int64_t* ticket);
-/* Wait for a request; *latency_ms = completion time - submit time. */
+/* Wait for a request (timeout_s <= 0: no limit); *latency_ms = completion
+ * time - submit time. Returns the request's own status and releases the
+ * ticket; ETIMEOUT leaves it open (wait again). One thread waits on a given
+ * ticket at a time; EINVAL for an unknown or already released ticket. */
 PANTHER_API panther_status panther_serve_wait(panther_server* s, int64_t ticket, double timeout_s,
                                   double* latency_ms);
 /* [0] submitted, [1] completed, [2] batches launched, [3] max requests in one batch,
  * [4] max batches in flight at once, [5] requests refused (EBUSY) */
 PANTHER_API panther_status panther_serve_stats(panther_server* s, int64_t stats[6]);
+/* Stops taking requests, finishes the pending ones, joins the workers and
+ * frees the server (tickets not yet waited for are released). */
 PANTHER_API void panther_serve_destroy(panther_server* s);
 
 #ifdef __cplusplus

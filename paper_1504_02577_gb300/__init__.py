@@ -117,6 +117,27 @@ def _ptr(x) -> int | None:
     return int(x)
 
 
+def _buf(x, itemsize: int, count: int, what: str):
+    """Raw pointer of a caller buffer after checking its element size and that
+    it holds at least `count` elements (numpy arrays and torch tensors; a plain
+    integer is taken as a raw pointer and None as NULL, unchecked). The C side
+    cannot see either property: a wrong element type would be read as garbage
+    and a short buffer written past its end."""
+    if x is None or isinstance(x, (int, np.integer)):
+        return _ptr(x)
+    if isinstance(x, np.ndarray):
+        size, n = x.dtype.itemsize, x.size
+    elif hasattr(x, "element_size") and hasattr(x, "numel"):
+        size, n = x.element_size(), x.numel()
+    else:
+        return _ptr(x)
+    if size != itemsize:
+        raise ValueError(f"{what}: elements of {itemsize} bytes expected, got {size}")
+    if n < count:
+        raise ValueError(f"{what}: at least {count} elements expected, got {n}")
+    return _ptr(x)
+
+
 def _check(ctx: int | None, rc: int):
     if rc != OK:
         msg = load_library().panther_last_error(ctx).decode() if ctx else ""
@@ -158,7 +179,8 @@ def panther_sample_size(eps: float, delta: float, c: float, T: int) -> int:
 
 def panther_build_graph(ctx: int, n: int, m: int, row_ptr, col, w, mem: int, modes: int = MODE_BOTH) -> int:
     h = _vp()
-    _check(ctx, load_library().panther_build_graph(ctx, n, m, _ptr(row_ptr), _ptr(col), _ptr(w), mem, modes,
+    _check(ctx, load_library().panther_build_graph(ctx, n, m, _buf(row_ptr, 8, n + 1, "row_ptr"),
+                                                   _buf(col, 4, m, "col"), _buf(w, 4, m, "w"), mem, modes,
                                                    ctypes.byref(h)))
     return h.value
 
@@ -185,7 +207,8 @@ def panther_build_index(ctx: int, p: int) -> int:
 def panther_build_index_noalloc(ctx: int, p: int, dev_off, dev_pid, pid_capacity: int) -> int:
     """Index into caller buffers with no device allocation; returns nnz."""
     nnz = _i64()
-    _check(ctx, load_library().panther_build_index_noalloc(ctx, p, _ptr(dev_off), _ptr(dev_pid), pid_capacity,
+    _check(ctx, load_library().panther_build_index_noalloc(ctx, p, _buf(dev_off, 8, 0, "dev_off"),
+                                                           _buf(dev_pid, 4, 0, "dev_pid"), pid_capacity,
                                                            ctypes.byref(nnz)))
     return nnz.value
 
@@ -199,14 +222,16 @@ def panther_index_view(ix: int):
 
 def panther_topk(ctx: int, ix: int, p: int, queries, q: int, k: int, out_ids, out_counts,
                  flags: int = TOPK_BATCHED) -> None:
-    _check(ctx, load_library().panther_topk(ctx, ix, p, _ptr(queries), q, k, _ptr(out_ids), _ptr(out_counts),
-                                            flags))
+    _check(ctx, load_library().panther_topk(ctx, ix, p, _buf(queries, 4, q, "queries"), q, k,
+                                            _buf(out_ids, 4, q * k, "out_ids"),
+                                            _buf(out_counts, 4, q * k, "out_counts"), flags))
 
 
 def panther_tune_topk(ctx: int, ix: int, p: int, queries, q: int, k: int, out_ids, out_counts):
     chosen = (_int * 3)()
-    _check(ctx, load_library().panther_tune_topk(ctx, ix, p, _ptr(queries), q, k, _ptr(out_ids), _ptr(out_counts),
-                                                 chosen))
+    _check(ctx, load_library().panther_tune_topk(ctx, ix, p, _buf(queries, 4, q, "queries"), q, k,
+                                                 _buf(out_ids, 4, q * k, "out_ids"),
+                                                 _buf(out_counts, 4, q * k, "out_counts"), chosen))
     return list(chosen)
 
 
@@ -227,14 +252,17 @@ def pantherpp_vecs_view(v: int):
 
 
 def pantherpp_knn(ctx: int, v: int, queries, q: int, k: int, out_ids, out_dist2, flags: int = KNN_BF16_SCREEN):
-    _check(ctx, load_library().pantherpp_knn(ctx, v, _ptr(queries), q, k, _ptr(out_ids), _ptr(out_dist2), flags))
+    _check(ctx, load_library().pantherpp_knn(ctx, v, _buf(queries, 4, q, "queries"), q, k,
+                                             _buf(out_ids, 4, q * k, "out_ids"),
+                                             _buf(out_dist2, 8, q * k, "out_dist2"), flags))
 
 
 def pantherpp_knn_cross(ctx: int, vq: int, vc: int, queries, q: int, k: int, out_ids, out_dist2,
                         flags: int = KNN_BF16_SCREEN):
     """Queries are vertices of vq's graph, answers vertices of vc's graph (none excluded)."""
-    _check(ctx, load_library().pantherpp_knn_cross(ctx, vq, vc, _ptr(queries), q, k, _ptr(out_ids),
-                                                   _ptr(out_dist2), flags))
+    _check(ctx, load_library().pantherpp_knn_cross(ctx, vq, vc, _buf(queries, 4, q, "queries"), q, k,
+                                                   _buf(out_ids, 4, q * k, "out_ids"),
+                                                   _buf(out_dist2, 8, q * k, "out_dist2"), flags))
 
 
 def pantherpp_knn_stats(ctx: int):
@@ -318,8 +346,11 @@ def panther_serve_create(device: int, ix: int, p: int, v: int | None, mem_budget
 def panther_serve_submit(s: int, kind: int, queries: np.ndarray, k: int, out_ids: np.ndarray,
                          out_vals: np.ndarray) -> int:
     t = _i64()
-    _check(None, load_library().panther_serve_submit(s, kind, _ptr(queries), queries.shape[0], k, _ptr(out_ids),
-                                                     _ptr(out_vals), ctypes.byref(t)))
+    q = int(queries.shape[0])
+    _check(None, load_library().panther_serve_submit(s, kind, _buf(queries, 4, q, "queries"), q, k,
+                                                     _buf(out_ids, 4, q * k, "out_ids"),
+                                                     _buf(out_vals, 4 if kind == 0 else 8, q * k, "out_vals"),
+                                                     ctypes.byref(t)))
     return t.value
 
 

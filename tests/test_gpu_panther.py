@@ -425,7 +425,8 @@ def test_autotuner_keeps_results_exact(pk):
         P.build_index()
         qt = torch.as_tensor(q, device="cuda:0")
         shape = P.tune_topk(qt, k)
-        assert shape[0] in (256, 512, 1024) and shape[2] in (1, 2, 3)
+        # one of the tuner's candidate shapes (which one wins depends on timing)
+        assert shape[0] in (128, 256, 512, 1024) and shape[1] % 32 == 0 and 1 <= shape[2] <= 8
         ids, cnt = P.topk(qt, k)
         P.sync()
         ids, cnt = ids.cpu().numpy(), cnt.cpu().numpy().astype(np.uint32)

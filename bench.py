@@ -87,8 +87,8 @@ NCU_TRAFFIC = {
         "paper_1504_02577_gb300/csrc/capi.cu": "02fa30a2121c3c8dca2f5c7d29513b8191b1ec93498ab936e54f7efe39b61e81",
         "paper_1504_02577_gb300/csrc/internal.cuh": "dca6f273b85f41c4c763fd5a411da0ded671711cdfca0dd8552cf5610bef03dd",
     }},
-    "topk": {"bytes_5M": 8252432384, "sources": {
-        "paper_1504_02577_gb300/csrc/topk.cu": "9e31bea4a2ee3f2d1018f24be906b13eb9f8adafd7e6642d6a9354dd2b3ae294",
+    "topk": {"bytes_5M": 8264598528, "sources": {
+        "paper_1504_02577_gb300/csrc/topk.cu": "c8b5a629bc94613beb54a206876d142dad31cf98143d01ca55b5b408d143e45c",
         "paper_1504_02577_gb300/csrc/internal.cuh": "dca6f273b85f41c4c763fd5a411da0ded671711cdfca0dd8552cf5610bef03dd",
     }},
 }

@@ -19,6 +19,7 @@
 // from device counters (CTA-tier queries first, then warp-tier queries in
 // chunks), so skewed |P_v| does not leave SMs idle.
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 #include <vector>
 
@@ -1366,13 +1367,16 @@ static panther_status hub_buckets(panther_ctx* ctx, const PathsRef& P, const int
         int L = P.L;
         stride = L <= 8 ? 8 : (L <= 16 ? 16 : 32);
     }
-    static bool attr = false;
-    if (!attr) {
+    // process-wide attributes, set once; contexts on several host threads
+    // (the serving workers) may get here together, and setting them twice is
+    // harmless
+    static std::atomic<bool> attr{false};
+    if (!attr.load(std::memory_order_acquire)) {
         PCK(ctx, cudaFuncSetAttribute(b_scatter_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS1 * 8));
         PCK(ctx, cudaFuncSetAttribute(b_scatter_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS1 * 8));
         PCK(ctx, cudaFuncSetAttribute(b_scatter_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS1 * 8));
         PCK(ctx, cudaFuncSetAttribute(b_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS2 * 8));
-        attr = true;
+        attr.store(true, std::memory_order_release);
     }
     size_t pos = 0;
     panther_status st;

@@ -412,3 +412,60 @@ def test_knn_cross_pins():
         ids, d2 = oracle.knn_cross(a, b, v, 7)
         assert ids[:5].tolist() == [u for _, u in brute] and d2[:5].tolist() == [d for d, _ in brute]
         assert ids[5:].tolist() == [-1, -1] and d2[5:].tolist() == [2**64 - 1] * 2
+
+
+@pytest.mark.parametrize("mode", ["prefix", "alias"])
+def test_perfect_matching_closed_form(mode):
+    # every vertex has exactly one neighbour, so a path never leaves the pair
+    # {2i, 2i+1} it starts in: P_2i = P_2i+1 = the paths started in the pair,
+    # cnt(2i, 2i+1) = |P_2i| and every other count is 0, theta(v) =
+    # [|P_v|, 0, ...], and the k-NN distances are (|P_v| - |P_u|)^2
+    pairs = 40
+    rng = np.random.default_rng(11)
+    g = synth.graph_from_edges(2 * pairs, [(2 * i, 2 * i + 1) for i in range(pairs)],
+                               rng.integers(1, 1000, size=pairs).tolist())
+    m = oracle.PREFIX if mode == "prefix" else oracle.ALIAS
+    R, T = 3000, 4
+    P = oracle.sample_paths(g, 2, R, T, m)
+    assert set(map(frozenset, (set(row) for row in P.tolist()))) <= {frozenset({2 * i, 2 * i + 1})
+                                                                     for i in range(pairs)}
+    o = oracle.Oracle(g.n, P)
+    sizes = np.diff(o.off)
+    starts = np.bincount(P[:, 0] // 2, minlength=pairs)
+    assert (sizes[0::2] == starts).all() and (sizes[1::2] == starts).all() and sizes.sum() == 2 * R
+    q = np.arange(g.n, dtype=np.int32)
+    ids, cnt = o.topk_many(q, 3)
+    mate = q ^ 1
+    assert (ids[:, 0] == np.where(sizes > 0, mate, -1)).all() and (cnt[:, 0] == sizes).all()
+    assert (ids[:, 1:] == -1).all() and (cnt[:, 1:] == 0).all()
+    th = o.theta_all(4)
+    assert (th[:, 0] == sizes).all() and (th[:, 1:] == 0).all()
+    for v in (0, 7, 33):
+        kid, kd2 = oracle.knn(th, v, 6)
+        brute = sorted(((int(sizes[v]) - int(sizes[u])) ** 2, u) for u in range(g.n) if u != v)[:6]
+        assert kid.tolist() == [u for _, u in brute] and kd2.tolist() == [d for d, _ in brute]
+
+
+def test_star_closed_form():
+    # every path through a leaf also passes the centre (T >= 1: a walk
+    # leaves a leaf for the centre, and one at the centre moves to a leaf),
+    # so cnt(centre, leaf) = |P_leaf|, the centre's top-k is the leaves by
+    # (|P_leaf| desc, id asc), and each leaf's count with the centre is its
+    # own |P_leaf|
+    leaves = 25
+    rng = np.random.default_rng(5)
+    g = synth.graph_from_edges(leaves + 1, [(0, u) for u in range(1, leaves + 1)],
+                               rng.integers(1, 50, size=leaves).tolist())
+    for T in (1, 2, 5):
+        P = oracle.sample_paths(g, 4, 4000, T, oracle.ALIAS)
+        o = oracle.Oracle(g.n, P)
+        sizes = np.diff(o.off)
+        assert sizes[0] == 4000                           # every path touches the centre
+        k = 10
+        ids, cnt = o.topk(0, k)
+        order = sorted(range(1, leaves + 1), key=lambda u: (-int(sizes[u]), u))
+        assert ids.tolist() == order[:k] and cnt.tolist() == [int(sizes[u]) for u in order[:k]]
+        for leaf in (1, 9, leaves):
+            lid, lcnt = o.topk(leaf, leaves)
+            pos = lid.tolist().index(0)
+            assert lcnt[pos] == sizes[leaf] and lcnt[0] == sizes[leaf]

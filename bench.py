@@ -45,6 +45,10 @@ METRIC = "paths sampled/s; top-k queries/s batched vs plain at 1 GB300; % of HBM
 #   counting + top-k: per (vertex, path) pair of the index 4 B path id + one
 #     32 B path-row sector; per query 8 B*k of output
 SAMPLER_B_PER_PATH = lambda T: T * 64 + (T + 1) * 4
+#   tables: per vertex the row_ptr entry read (8 B) and the vertex record
+#     {start, deg, S} written (16 B); per CSR entry col + w read (8 B) and one
+#     table entry written (alias 16 B, prefix {cum, col} 8 B)
+TABLES_B = lambda g, mode: g.n * 24 + g.m * (8 + (16 if mode == "alias" else 8))
 INDEX_B_PER_PAIR = 48
 COUNT_B_PER_PAIR = 36
 
@@ -279,7 +283,7 @@ def run_ours(args, ws, rank, local):
         "sample": R * SAMPLER_B_PER_PATH(T),
         "index": nnz * INDEX_B_PER_PAIR,
         "topk": nnz * COUNT_B_PER_PAIR + nq * (16 + 8 * k),
-        "tables": g.m * (4 + 4 + 16 + 16) + g.n * 16,
+        "tables": TABLES_B(g, args.mode),
     }
     stage_obj = {}
     for s in stages:

@@ -176,6 +176,10 @@ PANTHER_API panther_status panther_sample_paths_range(panther_ctx* ctx, const pa
 PANTHER_API panther_status panther_paths_view(const panther_paths* p, const int32_t** dev_rows,
                                   int64_t* R, int* L, int* stride);
 
+/* Shape of a path handle: n vertices of its graph, R rows, T steps, r0 the
+ * global id of row 0. Any output pointer may be NULL. Errors: EINVAL (null p). */
+PANTHER_API panther_status panther_paths_info(const panther_paths* p, int64_t* n, int64_t* R, int* T, int64_t* r0);
+
 /* ------------------------------------------------------------ Sec. 3.1 --- */
 
 /* Build the inverted index P_v = { r : v in p_r } with a device LSD radix
@@ -198,7 +202,10 @@ PANTHER_API panther_status panther_build_index(panther_ctx* ctx, const panther_p
  * call on a device looks up that array's device address, so make it before
  * any stream capture. Calls share the array: two calls that overlap on the
  * GPU (other contexts or streams) race and must be ordered by the caller.
- * Synchronises once (to size the later radix passes).
+ * Every call, not only the first, waits once for the context stream (it
+ * copies the number of pairs found by the first radix pass to the host to
+ * size the later passes), so the call returns only after the work queued
+ * before it on that stream has finished.
  * Errors: EINVAL, EOVERFLOW, ECUDA. */
 PANTHER_API panther_status panther_build_index_noalloc(panther_ctx* ctx, const panther_paths* p, int64_t* dev_off,
                                                        int32_t* dev_pid, int64_t pid_capacity, int64_t* nnz);
@@ -218,7 +225,16 @@ PANTHER_API panther_status panther_index_view(const panther_index* ix, const int
  *          synchronises)
  * Temporary device memory (hub hash tables) is drawn from the context's
  * scratch budget; a batch whose hubs do not fit is processed in several
- * rounds. Errors: EINVAL, ENOMEM, ECUDA. */
+ * rounds.
+ * Host waits: the BATCHED form is not fully asynchronous. After the lane,
+ * group and persistent launches it copies the number of hub queries to the
+ * host and waits for the context stream (once per call); when there are hub
+ * queries it waits again to read their path counts and once per hub round
+ * (to read which queries need a second, exact pass). The call therefore
+ * returns only after its own work and everything queued before it on the
+ * stream has finished, and a serving worker's host thread is held for the
+ * whole batch. The PLAIN form only enqueues (one launch per query).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
 PANTHER_API panther_status panther_topk(panther_ctx* ctx, const panther_index* ix, const panther_paths* p,
                             const int32_t* queries, int64_t q, int k,
                             int32_t* out_ids, uint32_t* out_counts, int flags);

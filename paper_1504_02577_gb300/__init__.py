@@ -46,6 +46,7 @@ SIGNATURES = {
     "panther_build_graph": ([_vp, _i64, _i64, _vp, _vp, _vp, _int, _int, _P(_vp)], _int),
     "panther_sample_paths": ([_vp, _vp, _u64, _i64, _int, _int, _P(_vp)], _int),
     "panther_paths_view": ([_vp, _P(_vp), _P(_i64), _P(_int), _P(_int)], _int),
+    "panther_paths_info": ([_vp, _P(_i64), _P(_i64), _P(_int), _P(_i64)], _int),
     "panther_build_index": ([_vp, _vp, _P(_vp)], _int),
     "panther_index_view": ([_vp, _P(_vp), _P(_vp), _P(_i64), _P(_i64)], _int),
     "panther_build_index_noalloc": ([_vp, _vp, _vp, _vp, _i64, _P(_i64)], _int),
@@ -204,11 +205,25 @@ def panther_build_index(ctx: int, p: int) -> int:
     return h.value
 
 
+def panther_paths_info(p: int):
+    """(n, R, T, r0) of a path handle."""
+    n, R, T, r0 = _i64(), _i64(), _int(), _i64()
+    _check(None, load_library().panther_paths_info(p, ctypes.byref(n), ctypes.byref(R), ctypes.byref(T),
+                                                   ctypes.byref(r0)))
+    return n.value, R.value, T.value, r0.value
+
+
 def panther_build_index_noalloc(ctx: int, p: int, dev_off, dev_pid, pid_capacity: int) -> int:
-    """Index into caller buffers with no device allocation; returns nnz."""
+    """Index into caller buffers with no device allocation; returns nnz.
+
+    dev_pid must hold pid_capacity int32 elements (the library writes up to
+    R*(T+1) of them and trusts pid_capacity) and dev_off n+1 int64 elements,
+    n taken from the paths handle; both are checked here, before the call. A
+    NULL handle (p = 0) skips the dev_off check: the library refuses it."""
+    n_off = panther_paths_info(p)[0] + 1 if p else 0
     nnz = _i64()
-    _check(ctx, load_library().panther_build_index_noalloc(ctx, p, _buf(dev_off, 8, 0, "dev_off"),
-                                                           _buf(dev_pid, 4, 0, "dev_pid"), pid_capacity,
+    _check(ctx, load_library().panther_build_index_noalloc(ctx, p, _buf(dev_off, 8, n_off, "dev_off"),
+                                                           _buf(dev_pid, 4, pid_capacity, "dev_pid"), pid_capacity,
                                                            ctypes.byref(nnz)))
     return nnz.value
 

@@ -168,6 +168,15 @@ panther_status panther_paths_view(const panther_paths* p, const int32_t** dev_ro
     return PANTHER_OK;
 }
 
+panther_status panther_paths_info(const panther_paths* p, int64_t* n, int64_t* R, int* T, int64_t* r0) {
+    if (!p) return PANTHER_EINVAL;
+    if (n) *n = p->n;
+    if (R) *R = p->R;
+    if (T) *T = p->T;
+    if (r0) *r0 = p->r0;
+    return PANTHER_OK;
+}
+
 panther_status panther_index_view(const panther_index* ix, const int64_t** dev_off, const int32_t** dev_pid,
                                   int64_t* n, int64_t* nnz) {
     if (!ix) return PANTHER_EINVAL;

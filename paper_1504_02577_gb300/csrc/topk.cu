@@ -1367,16 +1367,18 @@ static panther_status hub_buckets(panther_ctx* ctx, const PathsRef& P, const int
         int L = P.L;
         stride = L <= 8 ? 8 : (L <= 16 ? 16 : 32);
     }
-    // process-wide attributes, set once; contexts on several host threads
-    // (the serving workers) may get here together, and setting them twice is
-    // harmless
-    static std::atomic<bool> attr{false};
-    if (!attr.load(std::memory_order_acquire)) {
+    // The shared-memory attribute applies to the current device only: it is
+    // set once per device (bit `device` of the mask). Contexts on several host
+    // threads (the serving workers) may get here together; setting it twice
+    // is harmless.
+    static std::atomic<uint64_t> attr_set{0};
+    const uint64_t dev_bit = ctx->device < 64 ? (uint64_t(1) << ctx->device) : 0;
+    if (!dev_bit || !(attr_set.load(std::memory_order_acquire) & dev_bit)) {
         PCK(ctx, cudaFuncSetAttribute(b_scatter_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS1 * 8));
         PCK(ctx, cudaFuncSetAttribute(b_scatter_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS1 * 8));
         PCK(ctx, cudaFuncSetAttribute(b_scatter_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS1 * 8));
         PCK(ctx, cudaFuncSetAttribute(b_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS2 * 8));
-        attr.store(true, std::memory_order_release);
+        attr_set.fetch_or(dev_bit, std::memory_order_acq_rel);
     }
     size_t pos = 0;
     panther_status st;

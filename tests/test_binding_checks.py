@@ -90,6 +90,13 @@ def test_serve_and_noalloc_buffers():
     _reaches_library(pk.panther_build_index_noalloc, 0, 0, np.empty(4, np.int64), np.empty(8, np.int32), 8)
     with pytest.raises(ValueError, match="dev_pid"):
         pk.panther_build_index_noalloc(0, 0, np.empty(4, np.int64), np.empty(8, np.int64), 8)
+    # a pid buffer shorter than the capacity the library is told it has
+    with pytest.raises(ValueError, match="dev_pid"):
+        pk.panther_build_index_noalloc(0, 0, np.empty(4, np.int64), np.empty(7, np.int32), 8)
+    with pytest.raises(ValueError, match="dev_pid"):
+        pk.panther_build_index_noalloc(0, 0, np.empty(4, np.int64), torch.empty(7, dtype=torch.int32), 8)
+    with pytest.raises(ValueError, match="dev_off"):
+        pk.panther_build_index_noalloc(0, 0, np.empty(4, np.int32), np.empty(8, np.int32), 8)
 
 
 def test_raw_pointers_and_null_pass_unchecked():

@@ -239,6 +239,18 @@ PANTHER_API panther_status panther_topk(panther_ctx* ctx, const panther_index* i
                             const int32_t* queries, int64_t q, int k,
                             int32_t* out_ids, uint32_t* out_counts, int flags);
 
+/* Tier sizes of the last panther_topk call on this context (also set by
+ * pantherpp_vectors, which counts through the same tiers):
+ *   [0] queries, [1] lane tier, [2] group tiers (8/16/32 lanes per query),
+ *   [3] warp tier, [4] CTA tier (both persistent passes), [5] hub queries,
+ *   [6] hub queries counted through the bucketed two-pass tier (per round),
+ *   [7] hub queries counted in per-query device tables (per round),
+ *   [8] hub queries whose buckets overflowed (counted again in tables),
+ *   [9] hub queries counted a second time because the first-round
+ *       threshold could have dropped a top-k candidate.
+ * The PLAIN form sets only [0]. Errors: EINVAL. */
+PANTHER_API panther_status panther_topk_stats(panther_ctx* ctx, int64_t stats[10]);
+
 /* Autotuner for the batched form: runs the batch once per candidate launch
  * shape of the persistent kernel (threads per CTA, shared-table slots, CTAs
  * per SM), times three more runs of each with CUDA events on the context
@@ -316,6 +328,15 @@ PANTHER_API panther_status panther_debug_graph_tables(const panther_graph* g, vo
 PANTHER_API panther_status panther_debug_philox(panther_ctx* ctx, uint32_t k0, uint32_t k1, uint64_t r0,
                                                 uint32_t c2, uint32_t c3, int64_t count, uint32_t* dev_out,
                                                 uint32_t* dev_ref);
+
+/* Hub-tier routing (test-only; no counterpart in the paper): from now on
+ * queries whose candidate bound min(|P_v| * T, n-1) exceeds hub_min_cap
+ * (when > 0, at least 256) are hub queries, and route selects how hub
+ * queries are counted: 0 as usual, 1 every one through the bucketed
+ * two-pass tier, 2 every one in a per-query device table. Results do not
+ * change; tests use it to reach every hub kernel on small inputs.
+ * (0, 0) restores the default. Errors: EINVAL. */
+PANTHER_API panther_status panther_debug_topk_route(panther_ctx* ctx, int64_t hub_min_cap, int route);
 
 /* Fault injection (test-only; no counterpart in the paper). The nth device
  * allocation of this context from now on (0-based) fails once with ENOMEM,

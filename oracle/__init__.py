@@ -3,6 +3,9 @@
 Plain, slow, single-threaded C (``panther_oracle.c``) behind ctypes. Only the
 tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may
 import this package; the product path never does, and shares no code with it.
+Functions that take ``threads > 1`` run the all-core driver of the same file:
+it cuts one independent outer loop (rows, path ids, index vertices, queries)
+into ranges, one POSIX thread each, with identical results.
 
 Every function states the passage of the paper it follows (arXiv 1504.02577):
 Algorithm 3 (path generation), Eq. (3) (transition probabilities), the
@@ -33,7 +36,7 @@ def build() -> str:
     if os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-pthread", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -61,6 +64,14 @@ def _load():
                 "po_theta": ([i64, ci, vp, vp, vp, i32, ci, vp, vp], None),
                 "po_dist2": ([vp, vp, ci, vp], ci),
                 "po_knn": ([i64, ci, vp, i32, ci, vp, vp], ci),
+                "po_row_sums": ([i64, i64, vp, vp, vp], None),
+                "po_sample_paths_rs": ([i64, vp, vp, vp, vp, vp, vp, u64, i64, i64, ci, ci, vp], ci),
+                "po_index_range": ([i64, ci, vp, i64, i64, vp, vp], None),
+                "po_mt_alias_tables": ([i64, vp, vp, vp, vp, ci], ci),
+                "po_mt_sample_paths": ([i64, vp, vp, vp, vp, vp, u64, i64, i64, ci, ci, vp, ci], ci),
+                "po_mt_build_index": ([i64, i64, ci, vp, vp, vp, ci], i64),
+                "po_mt_topk_many": ([i64, ci, vp, vp, vp, vp, i64, ci, vp, vp, ci], ci),
+                "po_mt_theta_many": ([i64, ci, vp, vp, vp, vp, i64, ci, vp, ci], ci),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -118,36 +129,56 @@ def select_alias(thr: np.ndarray, al: np.ndarray, c: int, u: int) -> int:
     return int(_load().po_select_alias(_p(thr), _p(al), thr.shape[0], c, u))
 
 
-def alias_tables(g):
+def alias_tables(g, threads: int = 1):
+    """Eq. (3) alias tables of every row (threads > 1: the all-core driver, same tables)."""
     thr = np.zeros(max(g.m, 1), dtype=np.uint64)
     al = np.zeros(max(g.m, 1), dtype=np.int32)
-    _load().po_alias_tables(g.n, _p(g.row_ptr), _p(g.w), _p(thr), _p(al))
+    if threads > 1:
+        if _load().po_mt_alias_tables(g.n, _p(g.row_ptr), _p(g.w), _p(thr), _p(al), threads) != 0:
+            raise MemoryError("po_mt_alias_tables failed")
+    else:
+        _load().po_alias_tables(g.n, _p(g.row_ptr), _p(g.w), _p(thr), _p(al))
     return thr, al
 
 
 # -------------------------------------------------------------- paths ---
-def sample_paths(g, seed: int, R: int, T: int, mode: int = PREFIX, r0: int = 0, tables=None) -> np.ndarray:
-    """Algorithm 3: paths r0 .. r0+R-1 as int32[R][T+1]."""
+def sample_paths(g, seed: int, R: int, T: int, mode: int = PREFIX, r0: int = 0, tables=None,
+                 threads: int = 1) -> np.ndarray:
+    """Algorithm 3: paths r0 .. r0+R-1 as int32[R][T+1].
+
+    threads > 1 runs the all-core driver: row sums once, then contiguous path
+    ranges per thread (identical paths)."""
     lib = _load()
     thr = al = None
     if mode == ALIAS:
-        thr, al = tables if tables is not None else alias_tables(g)
+        thr, al = tables if tables is not None else alias_tables(g, threads)
     out = np.empty((R, T + 1), dtype=np.int32)
     col = g.col if g.m else np.zeros(1, np.int32)
     w = g.w if g.m else np.zeros(1, np.uint32)
-    rc = lib.po_sample_paths(g.n, _p(g.row_ptr), _p(col), _p(w), _p(thr), _p(al),
-                             seed, r0, r0 + R, T, mode, _p(out))
+    if threads > 1:
+        rc = lib.po_mt_sample_paths(g.n, _p(g.row_ptr), _p(col), _p(w), _p(thr), _p(al),
+                                    seed, r0, r0 + R, T, mode, _p(out), threads)
+    else:
+        rc = lib.po_sample_paths(g.n, _p(g.row_ptr), _p(col), _p(w), _p(thr), _p(al),
+                                 seed, r0, r0 + R, T, mode, _p(out))
     if rc != 0:
         raise ValueError("po_sample_paths: bad arguments")
     return out
 
 
-def build_index(n: int, paths: np.ndarray):
-    """Sec. 3.1 inverted index: (off int64[n+1], pid int32[nnz])."""
+def build_index(n: int, paths: np.ndarray, threads: int = 1):
+    """Sec. 3.1 inverted index: (off int64[n+1], pid int32[nnz]).
+
+    threads > 1: one vertex range per thread (identical index)."""
     lib = _load()
     paths = np.ascontiguousarray(paths, dtype=np.int32)
     R, L = paths.shape
     off = np.empty(n + 1, dtype=np.int64)
+    if threads > 1:
+        nnz = lib.po_mt_build_index(n, R, L, _p(paths), _p(off), None, threads)
+        pid = np.empty(max(nnz, 1), dtype=np.int32)
+        lib.po_mt_build_index(n, R, L, _p(paths), _p(off), _p(pid), threads)
+        return off, pid[:nnz]
     nnz = lib.po_build_index(n, R, L, _p(paths), _p(off), None)
     pid = np.empty(max(nnz, 1), dtype=np.int32)
     lib.po_build_index(n, R, L, _p(paths), _p(off), _p(pid))
@@ -175,10 +206,16 @@ class Oracle:
                           _p(self._work), _p(ids), _p(cnt))
         return ids, cnt
 
-    def topk_many(self, queries, k: int):
-        q = np.asarray(queries)
+    def topk_many(self, queries, k: int, threads: int = 1):
+        """topk for every query (threads > 1: query ranges per thread, identical rows)."""
+        q = np.ascontiguousarray(queries, dtype=np.int32)
         ids = np.empty((q.shape[0], k), dtype=np.int32)
         cnt = np.empty((q.shape[0], k), dtype=np.uint32)
+        if threads > 1:
+            if self._lib.po_mt_topk_many(self.n, self.L, _p(self.paths), _p(self.off), _p(self.pid), _p(q),
+                                         q.shape[0], k, _p(ids), _p(cnt), threads) != 0:
+                raise MemoryError("po_mt_topk_many failed")
+            return ids, cnt
         for i, v in enumerate(q):
             ids[i], cnt[i] = self.topk(int(v), k)
         return ids, cnt
@@ -190,8 +227,13 @@ class Oracle:
                            _p(self._work), _p(out))
         return out
 
-    def theta_all(self, D: int) -> np.ndarray:
+    def theta_all(self, D: int, threads: int = 1) -> np.ndarray:
         out = np.empty((self.n, D), dtype=np.uint32)
+        if threads > 1:
+            if self._lib.po_mt_theta_many(self.n, self.L, _p(self.paths), _p(self.off), _p(self.pid), None,
+                                          self.n, D, _p(out), threads) != 0:
+                raise MemoryError("po_mt_theta_many failed")
+            return out
         for v in range(self.n):
             out[v] = self.theta(v, D)
         return out

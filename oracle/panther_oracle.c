@@ -40,10 +40,19 @@
  * 2019): U = x0 | x1<<32, m = U*S (128-bit); reject if low64(m) < 2^64 mod S
  * (then attempt+1), else return high64(m).
  *
+ * All-core driver (the po_mt_* functions at the end): the outer loops of the
+ * method are independent (paths by id, table rows by vertex, index lists by
+ * vertex, queries by id), and the paper's Implementation Notes mention running
+ * them in parallel. Each po_mt_* function only cuts one such loop into
+ * contiguous ranges and runs the single-threaded code above on every range in
+ * its own POSIX thread; it adds no arithmetic of its own, so its output is
+ * identical to the single-threaded call (checked by the CPU tests).
+ *
  * Parity pins (what holds this file to something other than itself): see the
  * CPU tests. Philox itself has no CPU pin beyond bijectivity and uniformity;
  * its pin is the GPU cross-check against curand's Philox4_32_10.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -151,12 +160,23 @@ void po_alias_tables(int64_t n, const int64_t* row_ptr, const uint32_t* w, uint6
 }
 
 /* ------------------------------------------------------- Algorithm 3 --- */
+/* Row sums S_v = sum_j w_vj of rows v0..v1-1 (the denominator of Eq. 3). */
+void po_row_sums(int64_t v0, int64_t v1, const int64_t* row_ptr, const uint32_t* w, uint64_t* S) {
+    for (int64_t v = v0; v < v1; ++v) {
+        uint64_t acc = 0;
+        for (int64_t j = row_ptr[v]; j < row_ptr[v + 1]; ++j) acc += w[j];
+        S[v] = acc;
+    }
+}
+
 /* Paths r0..r1-1, each T+1 vertices, written row-major to out[(r-r0)*(T+1)+i].
  * mode 0 = prefix selection, 1 = alias selection (thr/alias from
- * po_alias_tables; ignored in prefix mode). Returns 0, or -1 on bad input. */
-int po_sample_paths(int64_t n, const int64_t* row_ptr, const int32_t* col, const uint32_t* w,
-                    const uint64_t* thr, const int32_t* alias,
-                    uint64_t seed, int64_t r0, int64_t r1, int T, int mode, int32_t* out) {
+ * po_alias_tables; ignored in prefix mode). rowsum (may be NULL) holds S_v of
+ * every row from po_row_sums; without it S_v is summed at every step (the
+ * same value). Returns 0, or -1 on bad input. */
+int po_sample_paths_rs(int64_t n, const int64_t* row_ptr, const int32_t* col, const uint32_t* w,
+                       const uint64_t* thr, const int32_t* alias, const uint64_t* rowsum,
+                       uint64_t seed, int64_t r0, int64_t r1, int T, int mode, int32_t* out) {
     if (n < 1 || T < 0 || T > 65535 || (mode != 0 && mode != 1)) return -1;
     int L = T + 1;
     for (int64_t r = r0; r < r1; ++r) {
@@ -175,7 +195,8 @@ int po_sample_paths(int64_t n, const int64_t* row_ptr, const int32_t* col, const
             int64_t s = row_ptr[v], d = row_ptr[v + 1] - s;
             if (d == 0) { p[t] = (int32_t)v; continue; }    /* isolated: stay put */
             uint64_t S = 0;
-            for (int64_t j = 0; j < d; ++j) S += w[s + j];
+            if (rowsum) S = rowsum[v];
+            else for (int64_t j = 0; j < d; ++j) S += w[s + j];
             int64_t j = -1;
             for (uint32_t att = 0;; ++att) {
                 po_draw(seed, 0, (uint64_t)r, (uint32_t)t, att, x);
@@ -200,6 +221,12 @@ int po_sample_paths(int64_t n, const int64_t* row_ptr, const int32_t* col, const
         }
     }
     return 0;
+}
+
+int po_sample_paths(int64_t n, const int64_t* row_ptr, const int32_t* col, const uint32_t* w,
+                    const uint64_t* thr, const int32_t* alias,
+                    uint64_t seed, int64_t r0, int64_t r1, int T, int mode, int32_t* out) {
+    return po_sample_paths_rs(n, row_ptr, col, w, thr, alias, NULL, seed, r0, r1, T, mode, out);
 }
 
 /* --------------------------------------------------- inverted index --- */
@@ -230,6 +257,24 @@ int64_t po_build_index(int64_t n, int64_t R, int L, const int32_t* paths, int64_
         free(cur);
     }
     return off[n];
+}
+
+/* The same index restricted to the vertices v0 <= v < v1 (every path is
+ * still scanned in ascending id): cnt[v - v0] = |P_v| on the first call
+ * (pid == NULL); with pid, P_v is written at pid[cur[v - v0]++], cur holding
+ * the start of each list. Used by the all-core driver, one vertex range per
+ * thread. */
+void po_index_range(int64_t R, int L, const int32_t* paths, int64_t v0, int64_t v1, int64_t* cnt_or_cur,
+                    int32_t* pid) {
+    for (int64_t r = 0; r < R; ++r) {
+        const int32_t* p = paths + r * L;
+        for (int i = 0; i < L; ++i) {
+            int64_t u = p[i];
+            if (u < v0 || u >= v1 || po_seen_before(p, i)) continue;
+            if (pid) pid[cnt_or_cur[u - v0]++] = (int32_t)r;
+            else cnt_or_cur[u - v0]++;
+        }
+    }
 }
 
 /* ------------------------------------------------------- Algorithm 1 --- */
@@ -341,4 +386,240 @@ int po_knn(int64_t n, int D, const uint32_t* theta, int32_t v, int k, int32_t* i
     }
     free(all);
     return 0;
+}
+
+/* ------------------------------------------------- all-core driver --- */
+/* Each function below cuts one independent outer loop into nthreads
+ * contiguous ranges and runs the single-threaded function on each range in a
+ * thread of its own. Results are identical to the single-threaded call. */
+
+typedef struct {
+    int kind;
+    int64_t a, b;                    /* range of this thread */
+    /* shared arguments */
+    int64_t n, R;
+    int L, T, mode, k, D;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const uint32_t* w;
+    const uint64_t* thr_in;
+    const int32_t* alias_in;
+    const uint64_t* rowsum;
+    uint64_t seed;
+    const int32_t* paths;
+    const int64_t* off;
+    const int32_t* pidc;
+    const int32_t* queries;
+    /* outputs */
+    uint64_t* thr;
+    int32_t* alias;
+    uint64_t* S;
+    int32_t* out;
+    int64_t* cnt;
+    int32_t* pid;
+    int32_t* ids;
+    uint32_t* cnts;
+    int rc;
+} po_job;
+
+enum { JOB_ALIAS, JOB_ROWSUM, JOB_PATHS, JOB_IDX_COUNT, JOB_IDX_FILL, JOB_TOPK, JOB_THETA };
+
+static void* po_job_run(void* arg) {
+    po_job* j = (po_job*)arg;
+    j->rc = 0;
+    switch (j->kind) {
+    case JOB_ALIAS:
+        for (int64_t v = j->a; v < j->b; ++v) {
+            int64_t s = j->row_ptr[v], d = j->row_ptr[v + 1] - s;
+            if (d > 0) po_alias_row(j->w + s, d, j->thr + s, j->alias + s);
+        }
+        break;
+    case JOB_ROWSUM:
+        po_row_sums(j->a, j->b, j->row_ptr, j->w, j->S);
+        break;
+    case JOB_PATHS:
+        j->rc = po_sample_paths_rs(j->n, j->row_ptr, j->col, j->w, j->thr_in, j->alias_in, j->rowsum, j->seed,
+                                   j->a, j->b, j->T, j->mode, j->out + (j->a - j->R) * (j->T + 1));
+        break;
+    case JOB_IDX_COUNT:
+        po_index_range(j->R, j->L, j->paths, j->a, j->b, j->cnt, NULL);
+        break;
+    case JOB_IDX_FILL:
+        po_index_range(j->R, j->L, j->paths, j->a, j->b, j->cnt, j->pid);
+        break;
+    case JOB_TOPK:
+    case JOB_THETA: {
+        /* zeroed up front (not lazily by calloc), so every call pays the
+           same fixed cost whatever its queries touch */
+        size_t wbytes = sizeof(uint32_t) * (size_t)(j->n > 0 ? j->n : 1);
+        uint32_t* work = (uint32_t*)malloc(wbytes);
+        if (!work) { j->rc = -1; break; }
+        memset(work, 0, wbytes);
+        for (int64_t i = j->a; i < j->b; ++i) {
+            int32_t v = j->queries ? j->queries[i] : (int32_t)i;
+            if (j->kind == JOB_TOPK)
+                po_topk(j->n, j->L, j->paths, j->off, j->pidc, v, j->k, work, j->ids + i * j->k, j->cnts + i * j->k);
+            else
+                po_theta(j->n, j->L, j->paths, j->off, j->pidc, v, j->D, work, j->cnts + i * j->D);
+        }
+        free(work);
+        break;
+    }
+    }
+    return NULL;
+}
+
+/* run `proto` on nthreads ranges whose bounds are cut[0..nthreads] */
+static int po_run_ranges(const po_job* proto, int nthreads, const int64_t* cut) {
+    po_job* jobs = (po_job*)malloc(sizeof(po_job) * (size_t)nthreads);
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    int rc = 0;
+    if (!jobs || !th) { free(jobs); free(th); return -1; }
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t] = *proto;
+        jobs[t].a = cut[t];
+        jobs[t].b = cut[t + 1];
+        if (pthread_create(&th[t], NULL, po_job_run, &jobs[t]) != 0) { jobs[t].rc = -1; th[t] = 0; }
+    }
+    for (int t = 0; t < nthreads; ++t) {
+        if (th[t]) pthread_join(th[t], NULL);
+        else po_job_run(&jobs[t]);             /* no thread: run the range here */
+        if (jobs[t].rc) rc = jobs[t].rc;
+    }
+    free(jobs);
+    free(th);
+    return rc;
+}
+
+/* equal ranges of [lo, hi) */
+static void po_cut_even(int64_t lo, int64_t hi, int nthreads, int64_t* cut) {
+    for (int t = 0; t <= nthreads; ++t) cut[t] = lo + (hi - lo) * t / nthreads;
+}
+
+/* row ranges holding about equal numbers of CSR entries */
+static void po_cut_rows(int64_t n, const int64_t* row_ptr, int nthreads, int64_t* cut) {
+    int64_t m = row_ptr[n], v = 0;
+    cut[0] = 0;
+    for (int t = 1; t < nthreads; ++t) {
+        int64_t target = m * t / nthreads;
+        while (v < n && row_ptr[v] < target) ++v;
+        cut[t] = v;
+    }
+    cut[nthreads] = n;
+}
+
+int po_mt_alias_tables(int64_t n, const int64_t* row_ptr, const uint32_t* w, uint64_t* thr, int32_t* alias,
+                       int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    int64_t* cut = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nthreads + 1));
+    po_job j;
+    memset(&j, 0, sizeof j);
+    j.kind = JOB_ALIAS; j.row_ptr = row_ptr; j.w = w; j.thr = thr; j.alias = alias;
+    po_cut_rows(n, row_ptr, nthreads, cut);
+    int rc = po_run_ranges(&j, nthreads, cut);
+    free(cut);
+    return rc;
+}
+
+/* Paths r0..r1-1 as po_sample_paths (S_v summed once per row first). */
+int po_mt_sample_paths(int64_t n, const int64_t* row_ptr, const int32_t* col, const uint32_t* w,
+                       const uint64_t* thr, const int32_t* alias, uint64_t seed, int64_t r0, int64_t r1, int T,
+                       int mode, int32_t* out, int nthreads) {
+    if (n < 1 || T < 0 || T > 65535 || (mode != 0 && mode != 1) || r1 < r0) return -1;
+    if (nthreads < 1) nthreads = 1;
+    int64_t* cut = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nthreads + 1));
+    uint64_t* S = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n);
+    if (!cut || !S) { free(cut); free(S); return -1; }
+    po_job j;
+    memset(&j, 0, sizeof j);
+    j.kind = JOB_ROWSUM; j.row_ptr = row_ptr; j.w = w; j.S = S;
+    po_cut_rows(n, row_ptr, nthreads, cut);
+    int rc = po_run_ranges(&j, nthreads, cut);
+    if (!rc) {
+        memset(&j, 0, sizeof j);
+        j.kind = JOB_PATHS; j.n = n; j.row_ptr = row_ptr; j.col = col; j.w = w; j.thr_in = thr; j.alias_in = alias;
+        j.rowsum = S; j.seed = seed; j.T = T; j.mode = mode; j.out = out;
+        j.R = r0;                            /* row of path r is r - r0 */
+        po_cut_even(r0, r1, nthreads, cut);
+        rc = po_run_ranges(&j, nthreads, cut);
+    }
+    free(S);
+    free(cut);
+    return rc;
+}
+
+/* po_build_index with one vertex range per thread (off and pid as there). */
+int64_t po_mt_build_index(int64_t n, int64_t R, int L, const int32_t* paths, int64_t* off, int32_t* pid,
+                          int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    int64_t* cut = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nthreads + 1));
+    if (!cut) return -1;
+    po_cut_even(0, n, nthreads, cut);
+    memset(off, 0, sizeof(int64_t) * (size_t)(n + 1));
+    po_job j;
+    memset(&j, 0, sizeof j);
+    j.R = R; j.L = L; j.paths = paths;
+    /* counts: thread t writes |P_v| to off[v + 1] for its vertices */
+    j.kind = JOB_IDX_COUNT;
+    j.cnt = off + 1;                       /* po_index_range indexes cnt[u - v0]: shift per range below */
+    po_job* jobs = (po_job*)malloc(sizeof(po_job) * (size_t)nthreads);
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    int64_t* cur = pid ? (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1)) : NULL;
+    if (!jobs || !th || (pid && !cur)) { free(jobs); free(th); free(cur); free(cut); return -1; }
+    for (int pass = 0; pass < (pid ? 2 : 1); ++pass) {
+        for (int t = 0; t < nthreads; ++t) {
+            jobs[t] = j;
+            jobs[t].a = cut[t];
+            jobs[t].b = cut[t + 1];
+            jobs[t].kind = pass ? JOB_IDX_FILL : JOB_IDX_COUNT;
+            jobs[t].cnt = pass ? cur + cut[t] : off + 1 + cut[t];
+            jobs[t].pid = pass ? pid : NULL;
+            if (pthread_create(&th[t], NULL, po_job_run, &jobs[t]) != 0) th[t] = 0;
+        }
+        for (int t = 0; t < nthreads; ++t) {
+            if (th[t]) pthread_join(th[t], NULL);
+            else po_job_run(&jobs[t]);
+        }
+        if (pass == 0) {
+            for (int64_t v = 0; v < n; ++v) off[v + 1] += off[v];
+            if (cur) memcpy(cur, off, sizeof(int64_t) * (size_t)n);
+        }
+    }
+    free(jobs);
+    free(th);
+    free(cur);
+    free(cut);
+    return off[n];
+}
+
+/* po_topk for queries[0..q) (NULL: vertices 0..q-1), rows ids[q][k], cnts[q][k]. */
+int po_mt_topk_many(int64_t n, int L, const int32_t* paths, const int64_t* off, const int32_t* pid,
+                    const int32_t* queries, int64_t q, int k, int32_t* ids, uint32_t* cnts, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    int64_t* cut = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nthreads + 1));
+    if (!cut) return -1;
+    po_job j;
+    memset(&j, 0, sizeof j);
+    j.kind = JOB_TOPK; j.n = n; j.L = L; j.paths = paths; j.off = off; j.pidc = pid; j.queries = queries;
+    j.k = k; j.ids = ids; j.cnts = cnts;
+    po_cut_even(0, q, nthreads, cut);
+    int rc = po_run_ranges(&j, nthreads, cut);
+    free(cut);
+    return rc;
+}
+
+/* po_theta for queries[0..q) (NULL: vertices 0..q-1), rows theta[q][D]. */
+int po_mt_theta_many(int64_t n, int L, const int32_t* paths, const int64_t* off, const int32_t* pid,
+                     const int32_t* queries, int64_t q, int D, uint32_t* theta, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    int64_t* cut = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nthreads + 1));
+    if (!cut) return -1;
+    po_job j;
+    memset(&j, 0, sizeof j);
+    j.kind = JOB_THETA; j.n = n; j.L = L; j.paths = paths; j.off = off; j.pidc = pid; j.queries = queries;
+    j.D = D; j.cnts = theta;
+    po_cut_even(0, q, nthreads, cut);
+    int rc = po_run_ranges(&j, nthreads, cut);
+    free(cut);
+    return rc;
 }

@@ -58,6 +58,8 @@ SIGNATURES = {
     "pantherpp_knn": ([_vp, _vp, _vp, _i64, _int, _vp, _vp, _int], _int),
     "pantherpp_knn_cross": ([_vp, _vp, _vp, _vp, _i64, _int, _vp, _vp, _int], _int),
     "pantherpp_knn_stats": ([_vp, _P(_i64)], _int),
+    "panther_topk_stats": ([_vp, _P(_i64)], _int),
+    "panther_debug_topk_route": ([_vp, _i64, _int], _int),
     "panther_debug_graph_tables": ([_vp, _vp, _vp, _P(_int)], _int),
     "panther_debug_philox": ([_vp, _u32, _u32, _u64, _u32, _u32, _i64, _vp, _vp], _int),
     "panther_debug_fail_alloc": ([_vp, _i64], _int),
@@ -284,6 +286,20 @@ def pantherpp_knn_stats(ctx: int):
     a = (_i64 * 4)()
     _check(ctx, load_library().pantherpp_knn_stats(ctx, a))
     return list(a)
+
+
+def panther_topk_stats(ctx: int):
+    """Tier sizes of the last top-k call: queries, lane, group, warp, CTA, hub,
+    hub via buckets, hub via tables, bucket overflows, second passes."""
+    a = (_i64 * 10)()
+    _check(ctx, load_library().panther_topk_stats(ctx, a))
+    return list(a)
+
+
+def panther_debug_topk_route(ctx: int, hub_min_cap: int, route: int) -> None:
+    """Test-only hub routing: hub_min_cap > 0 lowers the hub-tier bound; route
+    1 = every hub query through buckets, 2 = through device tables."""
+    _check(ctx, load_library().panther_debug_topk_route(ctx, hub_min_cap, route))
 
 
 def panther_debug_graph_tables(g: int, dev_alias16, dev_prefix):

@@ -45,6 +45,13 @@ struct panther_ctx {
     bool hub_arena_clean = true;
     // fault injection: the allocation numbered fail_alloc_at fails once (-1: off)
     int64_t fail_alloc_at = -1, alloc_seen = 0;
+    // tier sizes of the last top-k call (see panther_topk_stats)
+    int64_t topk_stats[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    // test routing of the hub tier (panther_debug_topk_route): queries whose
+    // candidate bound exceeds dbg_hub_min_cap (> 0) are hub queries; route 1
+    // counts every hub query through the buckets, 2 through device tables
+    int64_t dbg_hub_min_cap = 0;
+    int dbg_hub_route = 0;
 };
 
 struct panther_graph {

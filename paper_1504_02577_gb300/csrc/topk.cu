@@ -1436,8 +1436,10 @@ static panther_status hub_buckets(panther_ctx* ctx, const PathsRef& P, const int
         PCK(ctx, cudaMemcpyAsync(hov.data(), ovf, sizeof(int) * rng, cudaMemcpyDeviceToHost, s));
         PCK(ctx, cudaMemcpyAsync(hredo.data(), dredo, sizeof(int32_t) * rng, cudaMemcpyDeviceToHost, s));
         PCK(ctx, cudaStreamSynchronize(s));
+        ctx->topk_stats[6] += rng;
         for (int i = 0; i < rng; ++i) {
             if (hov[i]) {
+                ++ctx->topk_stats[8];
                 HubQuery h = rh[i];
                 h.thr = 0;
                 again.push_back(h);
@@ -1529,6 +1531,7 @@ static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int3
         PCK(ctx, cudaMemcpyAsync(hredo.data(), dredo, sizeof(int32_t) * rng, cudaMemcpyDeviceToHost, s));
         PCK(ctx, cudaStreamSynchronize(s));   // the host plan must outlive the copy
         ctx->hub_arena_clean = true;
+        ctx->topk_stats[7] += rng;
         for (int i = 0; i < rng; ++i)
             if (hredo[i] >= 0) {
                 HubQuery h = rh[i];
@@ -1559,12 +1562,20 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
     if (st) return st;
     PathsRef P{p->rows, p->R, p->L, ix->off, ix->pid, ix->n, ix->cls};
     OutRef o{ids, cnt, k};
-    const int64_t ccap = (int64_t)sh.cta_slots * 7 / 10;
+    int64_t ccap = (int64_t)sh.cta_slots * 7 / 10;
     // queries above the tuned shape's table but within a 24,576-slot one take a
     // second persistent pass with one 1,024-thread CTA per SM
-    const int64_t ccap_big = sh.cta_slots < BIG_SLOTS ? (int64_t)BIG_SLOTS * 7 / 10 : ccap;
+    int64_t ccap_big = sh.cta_slots < BIG_SLOTS ? (int64_t)BIG_SLOTS * 7 / 10 : ccap;
+    if (ctx->dbg_hub_min_cap > 0) {   // test routing: a lower hub-tier bound
+        ccap = std::min(ccap, std::max<int64_t>(ctx->dbg_hub_min_cap, WCAP));
+        ccap_big = std::min(ccap_big, ccap);
+    }
+    for (int i = 0; i < 10; ++i) ctx->topk_stats[i] = 0;
+    ctx->topk_stats[0] = q;
 
     if (plain) {
+        for (int i = 0; i < 10; ++i) ctx->topk_stats[i] = 0;
+        ctx->topk_stats[0] = q;
         uint32_t gslots = pow2_at_least(2 * ix->n);
         unsigned long long* gtab = nullptr;
         if ((st = dev_alloc(ctx, (void**)&gtab, 8ull * gslots))) return st;
@@ -1659,10 +1670,15 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
     PCK(ctx, cudaGetLastError());
 
     // global tier: read its size (one synchronisation), then run in rounds
-    int h_counts[3];
-    PCK(ctx, cudaMemcpyAsync(h_counts, counts, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
+    int h_counts[16];
+    PCK(ctx, cudaMemcpyAsync(h_counts, counts, sizeof(int) * 16, cudaMemcpyDeviceToHost, s));
     PCK(ctx, cudaStreamSynchronize(s));
     const int ng = h_counts[2];
+    ctx->topk_stats[1] = lane_ok ? h_counts[5] : 0;
+    ctx->topk_stats[2] = (int64_t)h_counts[6] + h_counts[7] + h_counts[8];
+    ctx->topk_stats[3] = h_counts[0];
+    ctx->topk_stats[4] = (int64_t)h_counts[1] + (ccap_big > ccap ? h_counts[10] : 0);
+    ctx->topk_stats[5] = ng;
     if (ng > 0) {
         std::vector<int32_t> gq(ng);
         std::vector<int64_t> npv(ng);
@@ -1696,8 +1712,12 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
         auto run = [&](const std::vector<HubQuery>& list, std::vector<HubQuery>& again,
                        std::vector<HubQuery>& redo) -> panther_status {
             std::vector<HubQuery> tq, bq;
-            for (const HubQuery& h : list)
-                (h.thr > 0 && hub_bound(P, h, above) <= HUB_TABLE_BOUND ? tq : bq).push_back(h);
+            for (const HubQuery& h : list) {
+                bool table = h.thr > 0 && hub_bound(P, h, above) <= HUB_TABLE_BOUND;
+                if (ctx->dbg_hub_route == 1) table = false;
+                if (ctx->dbg_hub_route == 2) table = true;
+                (table ? tq : bq).push_back(h);
+            }
             panther_status r = PANTHER_OK;
             if (!tq.empty()) r = hub_tables(ctx, P, queries, o, k, tq, above, redo);
             if (!r && !bq.empty()) r = hub_buckets(ctx, P, queries, o, k, bq, above, again, redo);
@@ -1705,6 +1725,7 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
         };
         std::vector<HubQuery> again, redo, redo2;
         st = run(hubs, again, redo);
+        ctx->topk_stats[9] = (int64_t)redo.size();
         if (!st && !redo.empty()) st = run(redo, again, redo2);
         // a threshold equal to a lower bound of the k-th count always holds
         if (!st && !redo2.empty()) st = set_err(ctx, PANTHER_ECUDA, "hub threshold check failed twice");
@@ -1831,5 +1852,19 @@ extern "C" panther_status panther_set_topk_shape(panther_ctx* ctx, int threads, 
     ctx->topk_threads = threads;
     ctx->topk_cta_slots = table_slots;
     ctx->topk_blocks_per_sm = ctas_per_sm;
+    return PANTHER_OK;
+}
+
+extern "C" panther_status panther_topk_stats(panther_ctx* ctx, int64_t stats[10]) {
+    if (!ctx || !stats) return PANTHER_EINVAL;
+    for (int i = 0; i < 10; ++i) stats[i] = ctx->topk_stats[i];
+    return PANTHER_OK;
+}
+
+extern "C" panther_status panther_debug_topk_route(panther_ctx* ctx, int64_t hub_min_cap, int route) {
+    if (!ctx) return PANTHER_EINVAL;
+    if (hub_min_cap < 0 || route < 0 || route > 2) return set_err(ctx, PANTHER_EINVAL, "bad test routing");
+    ctx->dbg_hub_min_cap = hub_min_cap;
+    ctx->dbg_hub_route = route;
     return PANTHER_OK;
 }

@@ -1,0 +1,76 @@
+"""The 50M-vertex workload the benchmark times, checked against the oracle.
+
+Chung-Lu graph n = 50,000,000, mean degree 16, exponent 2.1, weights uniform
+in [1, 255], seed 1; R = 1e8 paths of T = 5 steps (alias selection), the
+inverted index of all of them, and top-10 of every vertex in the batched,
+autotuned form the benchmark runs. Compared bit for bit with the oracle (its
+all-core driver, identical to the single-threaded code): every path
+(Algorithm 3), the whole index (Sec. 3.1: off and pid), and the top-10 rows
+(Algorithm 1, Eq. (4)) of 2,000 uniformly drawn vertices plus the 64 vertices
+with the most paths, whose counts run through the hub tiers (pruned device
+tables and buckets) that only this size reaches.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def pk():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_02577_gb300 as pk
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return pk
+
+
+def test_scale_workload_paths_index_topk(pk):
+    p = synth.WORKLOADS["scale"]
+    g = synth.workload_graph("scale")
+    R, T, k = p["R"], p["T"], p["k"]
+    assert g.n == 50_000_000 and g.m == 800_000_000
+    with pk.Panther(0) as P:
+        dev = "cuda:0"
+        P.build_graph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev),
+                      torch.from_numpy(g.w.view(np.int32)).to(dev), pk.MODE_ALIAS)
+        P.sample_paths(1, R, T, pk.MODE_ALIAS)
+        P.build_index()
+        allq = torch.arange(g.n, dtype=torch.int32, device=dev)
+        P.tune_topk(allq, k)
+        ids, cnt = P.topk(allq, k)
+        P.sync()
+        st = pk.panther_topk_stats(P.h.ctx)
+        gpu_paths = P.paths_tensor().cpu().numpy()
+        off_t, pid_t = P.index_tensors()
+        gpu_off, gpu_pid = off_t.cpu().numpy(), pid_t.cpu().numpy()
+        del off_t, pid_t
+        ids, cnt = ids.cpu().numpy(), cnt.cpu().numpy().astype(np.uint32)
+    assert st[5] > 0 and st[6] + st[7] >= st[5]          # hub queries were counted
+    tables = oracle.alias_tables(g, threads=THREADS)
+    ref = oracle.sample_paths(g, 1, R, T, oracle.ALIAS, tables=tables, threads=THREADS)
+    del tables
+    assert np.array_equal(gpu_paths, ref), "paths differ from the oracle"
+    del gpu_paths
+    off, pid = oracle.build_index(g.n, ref, threads=THREADS)
+    assert np.array_equal(gpu_off, off), "index offsets differ"
+    assert np.array_equal(gpu_pid, pid), "index path ids differ"
+    del gpu_off, gpu_pid
+    o = oracle.Oracle(g.n, ref, off, pid)
+    sizes = np.diff(off)
+    rng = np.random.default_rng(2024)
+    heavy = np.argsort(-sizes, kind="stable")[:64]
+    q = np.unique(np.concatenate([heavy, rng.integers(0, g.n, 2000)])).astype(np.int32)
+    assert sizes[heavy[0]] > 1_000_000
+    rid, rcnt = o.topk_many(q, k, threads=THREADS)
+    assert np.array_equal(ids[q], rid), "top-10 ids differ"
+    assert np.array_equal(cnt[q], rcnt), "top-10 counts differ"

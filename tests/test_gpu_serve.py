@@ -1,10 +1,14 @@
 """The request loop: mixed top-k / k-NN requests from several host threads give
-the same result as the same request alone; admission by memory budget."""
+the same result as the same request alone and as the CPU oracle (top-k rows of
+Algorithm 1, exact k-NN of Sec. 3.3 on the oracle's theta); admission by
+memory budget."""
+import os
 import threading
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -83,6 +87,18 @@ def test_mixed_requests_equal_alone(env):
         a_ids, a_vals = _alone(pk, ctx, ih, ph, vh, kind, q, k)
         assert np.array_equal(ids, a_ids)
         assert np.array_equal(vals, a_vals)
+    # every result against the oracle (same paths: seed 1, R = 200,000, T = 5)
+    th = os.cpu_count() or 1
+    o = oracle.Oracle(g.n, oracle.sample_paths(g, 1, 200_000, 5, oracle.ALIAS, threads=th))
+    theta = o.theta_all(50, threads=th)
+    for kind, q, k, ids, vals in reqs:
+        if kind == 0:
+            rid, rcnt = o.topk_many(q, k, threads=th)
+            assert np.array_equal(ids, rid) and np.array_equal(vals, rcnt)
+        else:
+            for i, v in enumerate(q):
+                rid, rd = oracle.knn(theta, int(v), k)
+                assert np.array_equal(ids[i], rid) and np.array_equal(vals[i], rd)
 
 
 def test_admission_and_refusal(env):

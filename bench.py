@@ -472,10 +472,10 @@ class OracleRun:
         self.o.topk_many(q, self.k, threads=self.threads)
         return time.perf_counter() - t0
 
-    def step(self, seed, n_mid=2_048, n_light=32_768):
+    def step(self, seed, n_mid=8_192, n_light=524_288):
         """One sampled estimate of the all-vertex top-k time (seconds), plus the parts."""
         rng = np.random.default_rng(seed)
-        F = min(self._wall(self.empty) for _ in range(3))
+        F = statistics.median(self._wall(self.empty) for _ in range(5))
         est = self.t_heavy
         parts = {}
         for name, pop, ns in (("mid", self.mid, n_mid), ("light", self.light, n_light)):

@@ -51,9 +51,15 @@ def test_noalloc_index_equals_allocating_index_twice():
             pk.panther_free_paths(ph)
         # sizes beyond the static scratch are refused before any launch
         big = pk.panther_sample_paths(ctx, gh, 3, 800_000, 5, pk.MODE_ALIAS)
+        big_pid = torch.empty(800_000 * 6, dtype=torch.int32, device="cuda:0")
         with pytest.raises(pk.PantherError) as ei:
-            pk.panther_build_index_noalloc(ctx, big, off, pid, 800_000 * 6)
+            pk.panther_build_index_noalloc(ctx, big, off, big_pid, 800_000 * 6)
         assert ei.value.code == pk.EOVERFLOW
+        # the binding refuses caller buffers shorter than the call writes
+        with pytest.raises(ValueError, match="dev_off"):
+            pk.panther_build_index_noalloc(ctx, big, off[: g.n], big_pid, 800_000 * 6)
+        with pytest.raises(ValueError, match="dev_pid"):
+            pk.panther_build_index_noalloc(ctx, big, off, big_pid[:100], 800_000 * 6)
         pk.panther_free_paths(big)
         pk.panther_free_graph(gh)
     finally:

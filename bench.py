@@ -326,6 +326,10 @@ def run_ours(args, ws, rank, local):
         out["e2e"] = e2e(pk, torch, P, g, R, T, k, q_host, args, ws)
     P.close()
 
+    # Panther++ k-NN on its own 10M-vertex workload
+    if rank == 0 and not args.no_extras and args.workload == "scale":
+        out["knn"] = knn_block(pk, torch, local, args)
+
     if rank == 0 and ws == 1 and not args.no_extras:
         out["cpu_baseline"] = cpu_baseline(args.workload, g, R, T, k, q_host)
     return out
@@ -559,6 +563,144 @@ def _peak_tensor():
         return float(d["bf16_tflops"]), "measured"
     except Exception:
         return 1900.0, "fallback"
+
+
+KN_ALPHA, KN_BETA = 0.0157, 1.6e-5      # the screen kernel's error-bound constants (see knn.cu)
+
+
+def screening_error(pk, torch, P, theta, nq=16, seed=5):
+    """BF16 screening error of the tensor-core screen against the exact integer
+    distance and against an FP64 computation, over every screened pair of nq
+    queries (half the vertices with the largest |theta|, half uniform).
+
+    y_hat comes from the kernel itself (pantherpp_debug_screen); the exact
+    y = |b|^2 - 2 a.b is formed in int64 from four float64 products of 16-bit
+    halves (each exact), the FP64 one as |b|^2 - 2 (a.b) in float64."""
+    n, D = theta.shape
+    t64 = theta.astype(np.float64)
+    norm2 = (theta.astype(np.int64) ** 2).sum(axis=1)
+    big = np.argsort(-norm2, kind="stable")[: nq // 2]
+    rnd = np.random.default_rng(seed).choice(n, size=nq - big.size, replace=False)
+    q = np.concatenate([big, rnd]).astype(np.int32)
+    npad = pk.pantherpp_debug_screen(P.h.ctx, P.h.vecs)
+    dev = f"cuda:{P.device}"
+    y = torch.empty((nq, npad), dtype=torch.float32, device=dev)
+    cid = torch.empty(npad, dtype=torch.int32, device=dev)
+    pk.pantherpp_debug_screen(P.h.ctx, P.h.vecs, torch.as_tensor(q, device=dev), nq, y, cid)
+    y, cid = y.cpu().numpy(), cid.cpu().numpy()
+    ok = cid >= 0
+    c = cid[ok]
+    lo, hi = (theta & 0xFFFF).astype(np.float64), (theta >> 16).astype(np.float64)
+    a = theta[q].astype(np.int64)
+    exact_rows = (theta.max(axis=1) <= 256)
+    res = {"queries": int(nq), "pairs": 0, "max_abs_err_vs_exact": 0.0, "mean_abs_err_vs_exact": 0.0,
+           "max_abs_err_vs_fp64": 0.0, "mean_abs_err_vs_fp64": 0.0, "max_err_over_bound": 0.0,
+           "exact_pairs_nonzero_err": 0}
+    tot_e = tot_f = 0.0
+    for i in range(nq):
+        ai = a[i]
+        alo, ahi = (ai & 0xFFFF).astype(np.float64), (ai >> 16).astype(np.float64)
+        # a.b = hi.hi 2^32 + (hi.lo + lo.hi) 2^16 + lo.lo, each dot exact in float64 (< 2^53)
+        hh = (hi[c] @ ahi).astype(np.int64)
+        mid = (hi[c] @ alo + lo[c] @ ahi).astype(np.int64)
+        ll = (lo[c] @ alo).astype(np.int64)
+        dot = (hh << 32) + (mid << 16) + ll
+        y_exact = norm2[c] - 2 * dot
+        y_fp64 = norm2[c].astype(np.float64) - 2.0 * (t64[c] @ ai.astype(np.float64))
+        yh = y[i][ok].astype(np.float64)
+        e_exact = np.abs(yh - y_exact.astype(np.float64))
+        e_fp64 = np.abs(yh - y_fp64)
+        bound = (KN_ALPHA * math.sqrt(float(norm2[q[i]])) * np.sqrt(norm2[c].astype(np.float64))
+                 + KN_BETA * norm2[c].astype(np.float64) + 1.0) * 1.0001
+        res["pairs"] += int(c.size)
+        res["max_abs_err_vs_exact"] = max(res["max_abs_err_vs_exact"], float(e_exact.max()))
+        res["max_abs_err_vs_fp64"] = max(res["max_abs_err_vs_fp64"], float(e_fp64.max()))
+        res["max_err_over_bound"] = max(res["max_err_over_bound"], float((e_exact / bound).max()))
+        if exact_rows[q[i]]:
+            res["exact_pairs_nonzero_err"] += int((e_exact[exact_rows[c]] != 0).sum())
+        tot_e += float(e_exact.sum())
+        tot_f += float(e_fp64.sum())
+    res["mean_abs_err_vs_exact"] = tot_e / max(res["pairs"], 1)
+    res["mean_abs_err_vs_fp64"] = tot_f / max(res["pairs"], 1)
+    res["fp64_exact_here"] = bool(float(theta.max()) ** 2 * D < 2.0 ** 53)
+    for key in list(res):
+        if isinstance(res[key], float):
+            res[key] = float(f"{res[key]:.6g}")
+    return res
+
+
+def knn_block(pk, torch, local, args):
+    """Panther++ on its 10M-vertex workload (Sec. 3.3): theta for every vertex,
+    then the exact top-10 nearest vectors of ALL vertices through the BF16
+    tensor-core screen + exact rerank (one call), the FP32 form against the
+    BF16 form on a sample of queries (identical results required), and the
+    screening error of the tensor-core values."""
+    import synth
+    p = dict(synth.WORKLOADS["knn"])
+    g = synth.workload_graph("knn")
+    R, T, D, k = p["R"], p["T"], p["D"], p["k"]
+    dev = f"cuda:{local}"
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    out = {"workload": f"Chung-Lu n={g.n} m={g.m} mean_deg=20 gamma=2.3 loguniform[1,1024]; R={R} T={T} D={D} "
+                       f"k={k}"}
+    with pk.Panther(local) as P:
+        P.build_graph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev),
+                      torch.from_numpy(g.w.view(np.int32)).to(dev), pk.MODE_ALIAS)
+        P.sample_paths(1, R, T, pk.MODE_ALIAS)
+        P.build_index()
+        e0, e1 = ev(), ev()
+        e0.record(P.stream)
+        P.vectors(D)
+        e1.record(P.stream)
+        P.sync()
+        out["vectors_ms"] = round(e0.elapsed_time(e1), 2)
+        nsm = torch.cuda.get_device_properties(local).multi_processor_count
+        ns = min(g.n, 4 * 128 * nsm)
+        qs = torch.from_numpy(synth.uniform_ints(ns, g.n, seed=1, stream=0x71)).to(dev)
+        res = {}
+        for fp32 in (False, True):
+            P.knn(qs[:128], k, fp32=fp32)
+            P.sync()
+            a, b = ev(), ev()
+            a.record(P.stream)
+            res[fp32] = P.knn(qs, k, fp32=fp32)
+            b.record(P.stream)
+            P.sync()
+            res[fp32] = res[fp32] + (a.elapsed_time(b),)
+        identical = bool(torch.equal(res[False][0], res[True][0]) and torch.equal(res[False][1], res[True][1]))
+        out["sample"] = {"queries": ns, "bf16_ms": round(res[False][2], 2), "fp32_ms": round(res[True][2], 2),
+                         "speedup_bf16_vs_fp32": round(res[True][2] / res[False][2], 2), "identical": identical}
+        s_ids, s_d2 = res[False][0], res[False][1]
+        del res
+        allq = torch.arange(g.n, dtype=torch.int32, device=dev)
+        l0 = P.launches()
+        a, b = ev(), ev()
+        a.record(P.stream)
+        ids, d2 = P.knn(allq, k)
+        b.record(P.stream)
+        P.sync()
+        ms = a.elapsed_time(b)
+        launches = P.launches() - l0
+        st = pk.pantherpp_knn_stats(P.h.ctx)
+        # the rows of the sampled queries equal the sampled run's rows
+        sel = qs.long()
+        same_rows = bool(torch.equal(ids[sel], s_ids) and torch.equal(d2[sel], s_d2))
+        out["all_vertices"] = {"queries": g.n, "ms": round(ms, 1), "queries_per_s": round(g.n / ms * 1e3, 1),
+                               "gpu_launches": int(launches), "sample_rows_identical": same_rows,
+                               "pairs_screened": st[0], "pairs_reranked": st[1], "shortlist_overflow_queries": st[2],
+                               "bf16_exact_rows": st[3]}
+        del ids, d2, sel, s_ids, s_d2
+        npad = ((g.n + 255) // 256) * 256
+        flops = 2.0 * g.n * npad * 64
+        peak, kind = _peak_tensor()
+        tf = flops / (ms * 1e-3) / 1e12
+        out["roofline"] = {"bound": "tensor", "kernel": "screen_kernel (tcgen05 bf16, 128x256x64 tiles)",
+                           "achieved": round(tf, 1), "peak": peak, "peak_kind": kind, "unit": "TFLOP/s",
+                           "frac": round(tf / peak, 4), "traffic": None,
+                           "note": "whole k-NN call (screen + rerank) timed; flops = 2 * n * npad * 64"}
+        theta = P.theta_tensor().cpu().numpy().view(np.uint32)
+        out["screening_error"] = screening_error(pk, torch, P, theta)
+    return out
 
 
 def run_knn(args, ws, rank, local):

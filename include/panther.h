@@ -311,6 +311,19 @@ PANTHER_API panther_status pantherpp_knn_cross(panther_ctx* ctx, const pantherpp
  * observed over reranked pairs, [3] pairs whose bound was zero (exact). */
 PANTHER_API panther_status pantherpp_knn_stats(panther_ctx* ctx, int64_t stats[4]);
 
+/* BF16 screening values, for measuring the screening error (no counterpart
+ * in the paper). Runs the tensor-core screen of pantherpp_knn for q queries
+ * (1 <= q <= 128, device int32 vertex ids) against every vertex and writes
+ * each screened value: out_y (device float[q][npad]) receives
+ * y_hat = |b|^2 - 2 a_hat.b_hat (FP32 accumulation of BF16 inputs) for query
+ * i and the candidate at position p, out_cid (device int32[npad]) the vertex
+ * at each position (-1: padding, whose values are meaningless). The exact
+ * value is |b|^2 - 2 a.b, so d_hat = |a|^2 + y_hat. With out_y and out_cid
+ * both NULL the call only sets *npad (the candidate positions, a multiple of
+ * 256). Synchronises. Errors: EINVAL (also D > 56), ENOMEM, ECUDA. */
+PANTHER_API panther_status pantherpp_debug_screen(panther_ctx* ctx, const pantherpp_vecs* v, const int32_t* queries,
+                                                  int64_t q, float* out_y, int32_t* out_cid, int64_t* npad);
+
 /* ------------------------------------------------------ test support --- */
 
 /* Copies of the graph's transition tables, for tests: dev_alias16 receives

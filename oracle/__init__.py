@@ -72,6 +72,7 @@ def _load():
                 "po_mt_build_index": ([i64, i64, ci, vp, vp, vp, ci], i64),
                 "po_mt_topk_many": ([i64, ci, vp, vp, vp, vp, i64, ci, vp, vp, ci], ci),
                 "po_mt_theta_many": ([i64, ci, vp, vp, vp, vp, i64, ci, vp, ci], ci),
+                "po_mt_knn_many": ([i64, ci, vp, vp, i64, ci, vp, vp, ci], ci),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -262,6 +263,18 @@ def knn_cross(theta_q: np.ndarray, theta_c: np.ndarray, v: int, k: int):
     ids[:order.size] = order
     dist[:order.size] = d2[order]
     return ids, dist
+
+
+def knn_many(theta: np.ndarray, queries, k: int, threads: int = 1):
+    """knn for every query: (ids int32[q][k], d2 uint64[q][k]); threads > 1 splits the queries."""
+    theta = np.ascontiguousarray(theta, dtype=np.uint32)
+    q = np.ascontiguousarray(queries, dtype=np.int32)
+    n, D = theta.shape
+    ids = np.empty((q.shape[0], k), dtype=np.int32)
+    d2 = np.empty((q.shape[0], k), dtype=np.uint64)
+    if _load().po_mt_knn_many(n, D, _p(theta), _p(q), q.shape[0], k, _p(ids), _p(d2), max(1, threads)) != 0:
+        raise OverflowError("squared distance exceeds 64 bits")
+    return ids, d2
 
 
 def knn(theta: np.ndarray, v: int, k: int):

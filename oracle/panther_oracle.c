@@ -419,10 +419,12 @@ typedef struct {
     int32_t* pid;
     int32_t* ids;
     uint32_t* cnts;
+    const uint32_t* theta;
+    uint64_t* d2;
     int rc;
 } po_job;
 
-enum { JOB_ALIAS, JOB_ROWSUM, JOB_PATHS, JOB_IDX_COUNT, JOB_IDX_FILL, JOB_TOPK, JOB_THETA };
+enum { JOB_ALIAS, JOB_ROWSUM, JOB_PATHS, JOB_IDX_COUNT, JOB_IDX_FILL, JOB_TOPK, JOB_THETA, JOB_KNN };
 
 static void* po_job_run(void* arg) {
     po_job* j = (po_job*)arg;
@@ -446,6 +448,10 @@ static void* po_job_run(void* arg) {
         break;
     case JOB_IDX_FILL:
         po_index_range(j->R, j->L, j->paths, j->a, j->b, j->cnt, j->pid);
+        break;
+    case JOB_KNN:
+        for (int64_t i = j->a; i < j->b; ++i)
+            if (po_knn(j->n, j->D, j->theta, j->queries[i], j->k, j->ids + i * j->k, j->d2 + i * j->k)) j->rc = -1;
         break;
     case JOB_TOPK:
     case JOB_THETA: {
@@ -618,6 +624,21 @@ int po_mt_theta_many(int64_t n, int L, const int32_t* paths, const int64_t* off,
     memset(&j, 0, sizeof j);
     j.kind = JOB_THETA; j.n = n; j.L = L; j.paths = paths; j.off = off; j.pidc = pid; j.queries = queries;
     j.D = D; j.cnts = theta;
+    po_cut_even(0, q, nthreads, cut);
+    int rc = po_run_ranges(&j, nthreads, cut);
+    free(cut);
+    return rc;
+}
+
+/* po_knn for queries[0..q), rows ids[q][k], d2[q][k]; -1 if a distance overflows. */
+int po_mt_knn_many(int64_t n, int D, const uint32_t* theta, const int32_t* queries, int64_t q, int k, int32_t* ids,
+                   uint64_t* d2, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    int64_t* cut = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nthreads + 1));
+    if (!cut) return -1;
+    po_job j;
+    memset(&j, 0, sizeof j);
+    j.kind = JOB_KNN; j.n = n; j.D = D; j.theta = theta; j.queries = queries; j.k = k; j.ids = ids; j.d2 = d2;
     po_cut_even(0, q, nthreads, cut);
     int rc = po_run_ranges(&j, nthreads, cut);
     free(cut);

@@ -59,6 +59,7 @@ SIGNATURES = {
     "pantherpp_knn_cross": ([_vp, _vp, _vp, _vp, _i64, _int, _vp, _vp, _int], _int),
     "pantherpp_knn_stats": ([_vp, _P(_i64)], _int),
     "panther_topk_stats": ([_vp, _P(_i64)], _int),
+    "pantherpp_debug_screen": ([_vp, _vp, _vp, _i64, _vp, _vp, _P(_i64)], _int),
     "panther_debug_topk_route": ([_vp, _i64, _int], _int),
     "panther_debug_graph_tables": ([_vp, _vp, _vp, _P(_int)], _int),
     "panther_debug_philox": ([_vp, _u32, _u32, _u64, _u32, _u32, _i64, _vp, _vp], _int),
@@ -286,6 +287,21 @@ def pantherpp_knn_stats(ctx: int):
     a = (_i64 * 4)()
     _check(ctx, load_library().pantherpp_knn_stats(ctx, a))
     return list(a)
+
+
+def pantherpp_debug_screen(ctx: int, v: int, queries=None, q: int = 0, out_y=None, out_cid=None) -> int:
+    """BF16 screening values y_hat[q][npad] and candidate ids[npad]; returns npad.
+    With no outputs only npad is returned (to size them)."""
+    npad = _i64()
+    if out_y is None and out_cid is None:
+        _check(ctx, load_library().pantherpp_debug_screen(ctx, v, None, 0, None, None, ctypes.byref(npad)))
+        return npad.value
+    _check(ctx, load_library().pantherpp_debug_screen(ctx, v, 0, 0, None, None, ctypes.byref(npad)))
+    n = npad.value
+    _check(ctx, load_library().pantherpp_debug_screen(ctx, v, _buf(queries, 4, q, "queries"), q,
+                                                      _buf(out_y, 4, q * n, "out_y"), _buf(out_cid, 4, n, "out_cid"),
+                                                      ctypes.byref(npad)))
+    return npad.value
 
 
 def panther_topk_stats(ctx: int):

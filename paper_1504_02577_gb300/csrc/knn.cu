@@ -388,6 +388,9 @@ struct ScreenArgs {
     int* overflow;           // [qpad]
     uint32_t* status;
     bool exclude_self;       // queries and candidates are the same vertices
+    float* dump;             // DUMP form only: y_hat of every pair, [q][npad] by query index
+    const int32_t* qidx;     // DUMP form only: query index of each slot
+    int64_t npad;
 };
 
 // shared memory map (offsets from a 1024-aligned base)
@@ -399,6 +402,9 @@ constexpr uint32_t SM_BAR = SM_LIST + KN_M * KN_SPLIT * KN_KMAX * 8;   // barrie
 constexpr uint32_t SM_TOTAL = SM_BAR + 256;
 constexpr uint32_t KN_SMEM_BYTES = SM_TOTAL + 1024;
 
+// DUMP = true is the measurement form (pantherpp_debug_screen): it also
+// writes every screened value y_hat to S.dump; DUMP = false is the k-NN path.
+template <bool DUMP>
 __global__ void __launch_bounds__(KN_THREADS, 1)
     screen_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, ScreenArgs S) {
     extern __shared__ uint8_t smraw[];
@@ -561,6 +567,10 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
     {                                                                                                    \
         _Pragma("unroll") for (int j = 0; j < 32; ++j) y[j] = __uint_as_float(U[j]);                     \
         const int c0 = h * 128 + (G) * 32;                                                               \
+        if (DUMP && rc.qid >= 0) {                                                                       \
+            float* dst = S.dump + (int64_t)S.qidx[slot] * S.npad + ct * KN_N + c0;                       \
+            _Pragma("unroll") for (int j = 0; j < 32; ++j) dst[j] = y[j];                                \
+        }                                                                                                \
         r = select_group(r, rc, y, fast, cid + c0, cnrm + c0, cncf + c0, ct * KN_N + c0, S.nexact);      \
     }
                     KN_GROUP(u0, 0)
@@ -1082,7 +1092,8 @@ static int64_t knn_ranges(int64_t nqt, int64_t nct, int num_sms, bool fp32) {
 // queries are vertices of vq, candidates every vertex of vc; `same` excludes
 // the candidate with the query's id (one graph: the query itself)
 static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* vq, const pantherpp_vecs* vc, bool same,
-                              const int32_t* queries, int64_t q, int k, int32_t* ids, uint64_t* d2, bool fp32) {
+                              const int32_t* queries, int64_t q, int k, int32_t* ids, uint64_t* d2, bool fp32,
+                              float* dump = nullptr) {
     const pantherpp_vecs& x = *vc;
     const pantherpp_vecs* v = vq;
     cudaStream_t s = ctx->stream;
@@ -1151,10 +1162,17 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* vq, const 
             return PANTHER_ECUDA;
         }
         ScreenArgs S{x.cid, x.cnrm, x.cncf, x.ctile, x.npad / KN_N, x.nexact, qv, qn, qex, qtile, qpad / KN_M,
-                     nch, k, lists, sl, sc, ovf, ctx->d_status, same};
-        PCK(ctx, cudaFuncSetAttribute(screen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KN_SMEM_BYTES));
+                     nch, k, lists, sl, sc, ovf, ctx->d_status, same, dump, qidx, x.npad};
         int64_t grid = std::min<int64_t>(qpad / KN_M * nch, ctx->num_sms);
-        screen_kernel<<<(unsigned)grid, KN_THREADS, KN_SMEM_BYTES, s>>>(tmA, tmB, S);
+        if (dump) {
+            PCK(ctx, cudaFuncSetAttribute(screen_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)KN_SMEM_BYTES));
+            screen_kernel<true><<<(unsigned)grid, KN_THREADS, KN_SMEM_BYTES, s>>>(tmA, tmB, S);
+        } else {
+            PCK(ctx, cudaFuncSetAttribute(screen_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)KN_SMEM_BYTES));
+            screen_kernel<false><<<(unsigned)grid, KN_THREADS, KN_SMEM_BYTES, s>>>(tmA, tmB, S);
+        }
         ctx->launches++;
     } else {
         fp32_kernel<<<(unsigned)(qpad / F_T), F_T, 0, s>>>(vq->theta, vc->theta, same, v->D, qv, qex, qn, qpad,
@@ -1273,4 +1291,38 @@ extern "C" panther_status pantherpp_knn_stats(panther_ctx* ctx, int64_t stats[4]
     if (!ctx || !stats) return PANTHER_EINVAL;
     for (int i = 0; i < 4; ++i) stats[i] = ctx->knn_stats[i];
     return PANTHER_OK;
+}
+
+// Measurement of the BF16 screening error (no counterpart in the paper): the
+// tensor-core screen of up to 128 queries against every candidate, keeping
+// every screened value. out_y[i][p] = y_hat = |b|^2 - 2 a_hat.b_hat for query
+// i and the candidate at position p (out_cid[p], -1 for padding); the exact
+// value is |b|^2 - 2 a.b, so d_hat = |a|^2 + y_hat.
+extern "C" panther_status pantherpp_debug_screen(panther_ctx* ctx, const pantherpp_vecs* v, const int32_t* queries,
+                                                 int64_t q, float* out_y, int32_t* out_cid, int64_t* npad) {
+    if (!ctx || !v || !npad) return PANTHER_EINVAL;
+    *npad = v->npad;
+    if (!out_y && !out_cid) return PANTHER_OK;
+    if (!queries || !out_y || !out_cid || q < 1 || q > KN_M)
+        return set_err(ctx, PANTHER_EINVAL, "1 <= q <= 128 queries and both outputs are needed");
+    if (v->D > KN_K - 8) return set_err(ctx, PANTHER_EINVAL, "BF16 screening needs D <= 56");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    int32_t* ids = nullptr;
+    uint64_t* d2 = nullptr;
+    panther_status st;
+    if ((st = dev_alloc(ctx, (void**)&ids, sizeof(int32_t) * q)) || (st = dev_alloc(ctx, (void**)&d2, 8 * q))) {
+        dev_free(ctx, ids);
+        return st;
+    }
+    PCK(ctx, cudaMemsetAsync(out_y, 0xff, sizeof(float) * q * v->npad, s));   // NaN where nothing is screened
+    st = knn_run(ctx, v, v, true, queries, q, 1, ids, d2, false, out_y);
+    if (!st) {
+        cudaError_t e = cudaMemcpyAsync(out_cid, v->cid, sizeof(int32_t) * v->npad, cudaMemcpyDeviceToDevice, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        if (e) st = cuda_err(ctx, e, "screen dump");
+    }
+    dev_free(ctx, ids);
+    dev_free(ctx, d2);
+    return st;
 }

@@ -216,3 +216,45 @@ def test_knn_cross_graph(pk, fp32):
             free(h)
     finally:
         pk.panther_destroy(ctx)
+
+
+@pytest.mark.parametrize("case", ["small", "large_counts"])
+def test_screen_values_within_the_proven_bound(pk, case):
+    """Every tensor-core screened value y_hat (BF16 inputs, FP32 accumulation)
+    lies within the error bound the rerank relies on,
+    |y_hat - y| <= (0.0157 |a||b| + 1.6e-5 |b|^2 + 1) * 1.0001 with
+    y = |b|^2 - 2 a.b exact, and equals y exactly when both rows hold only
+    entries <= 256 (BF16-exact rows)."""
+    if case == "small":
+        g, seed, R = synth.workload_graph("small"), 1, 200_000
+    else:
+        g, seed, R = synth.chung_lu(700, 12, 2.4, ("uniform", 1, 20), seed=6), 4, 600_000
+    T, D = 5, 50
+    with pk.Panther(0) as P:
+        P.build_graph(g.row_ptr, g.col, g.w, pk.MODE_ALIAS)
+        P.sample_paths(seed, R, T, pk.MODE_ALIAS)
+        P.build_index()
+        P.vectors(D)
+        theta = P.theta_tensor().cpu().numpy().view(np.uint32).astype(np.int64)
+        npad = pk.pantherpp_debug_screen(P.h.ctx, P.h.vecs)
+        norm2 = (theta ** 2).sum(axis=1)
+        q = np.unique(np.concatenate([np.argsort(-norm2)[:64], np.arange(0, g.n, max(1, g.n // 64))]))[:128]
+        q = q.astype(np.int32)
+        y = torch.empty((q.size, npad), dtype=torch.float32, device="cuda:0")
+        cid = torch.empty(npad, dtype=torch.int32, device="cuda:0")
+        pk.pantherpp_debug_screen(P.h.ctx, P.h.vecs, torch.as_tensor(q, device="cuda:0"), q.size, y, cid)
+        y, cid = y.cpu().numpy().astype(np.float64), cid.cpu().numpy()
+    assert npad % 256 == 0 and sorted(cid[cid >= 0].tolist()) == list(range(g.n))
+    ok = cid >= 0
+    c = cid[ok]
+    exact_row = theta.max(axis=1) <= 256
+    if case == "large_counts":
+        assert (~exact_row).sum() > 100
+    for i, v in enumerate(q):
+        y_exact = norm2[c] - 2 * (theta[c] @ theta[v])           # int64, exact here
+        err = np.abs(y[i][ok] - y_exact.astype(np.float64))
+        bound = (0.0157 * np.sqrt(float(norm2[v])) * np.sqrt(norm2[c].astype(np.float64))
+                 + 1.6e-5 * norm2[c] + 1.0) * 1.0001
+        assert (err <= bound).all(), (v, float((err / bound).max()))
+        if exact_row[v]:
+            assert (err[exact_row[c]] == 0).all(), v

@@ -74,3 +74,39 @@ def test_scale_workload_paths_index_topk(pk):
     rid, rcnt = o.topk_many(q, k, threads=THREADS)
     assert np.array_equal(ids[q], rid), "top-10 ids differ"
     assert np.array_equal(cnt[q], rcnt), "top-10 counts differ"
+
+
+def test_knn_workload_theta_all_and_sampled_knn(pk):
+    """The 10M-vertex Panther++ workload (Chung-Lu mean degree 20, exponent
+    2.3, log-uniform weights in [1, 1024], R = 5e7, T = 5, D = 50): theta of
+    every vertex equal to the oracle's (Sec. 3.3), and the exact top-10
+    nearest vectors (BF16 screen + exact rerank, the form the benchmark
+    times) of 96 uniform queries and the 32 vertices with the largest theta
+    norms equal to the oracle's all-pairs search."""
+    p = synth.WORKLOADS["knn"]
+    g = synth.workload_graph("knn")
+    R, T, D, k = p["R"], p["T"], p["D"], p["k"]
+    with pk.Panther(0) as P:
+        dev = "cuda:0"
+        P.build_graph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev),
+                      torch.from_numpy(g.w.view(np.int32)).to(dev), pk.MODE_ALIAS)
+        P.sample_paths(1, R, T, pk.MODE_ALIAS)
+        P.build_index()
+        P.vectors(D)
+        theta = P.theta_tensor().cpu().numpy().view(np.uint32)
+        norm2 = (theta.astype(np.int64) ** 2).sum(axis=1)
+        rng = np.random.default_rng(77)
+        q = np.concatenate([np.argsort(-norm2, kind="stable")[:32], rng.integers(0, g.n, 96)]).astype(np.int32)
+        ids, d2 = P.knn(torch.as_tensor(q, device=dev), k)
+        P.sync()
+        ids, d2 = ids.cpu().numpy(), d2.cpu().numpy().view(np.uint64)
+    tables = oracle.alias_tables(g, threads=THREADS)
+    ref = oracle.sample_paths(g, 1, R, T, oracle.ALIAS, tables=tables, threads=THREADS)
+    del tables
+    o = oracle.Oracle(g.n, ref)
+    rth = o.theta_all(D, threads=THREADS)
+    assert np.array_equal(theta, rth), "theta differs from the oracle"
+    assert rth.max() > 256                              # inexact BF16 rows exist: the bound decides
+    rid, rd = oracle.knn_many(rth, q, k, threads=THREADS)
+    assert np.array_equal(ids, rid), "k-NN ids differ"
+    assert np.array_equal(d2, rd), "k-NN distances differ"

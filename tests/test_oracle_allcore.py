@@ -57,3 +57,13 @@ def test_more_threads_than_items():
     a = o.topk_many(np.arange(4, dtype=np.int32), 3)
     b = o.topk_many(np.arange(4, dtype=np.int32), 3, threads=16)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_knn_many(g):
+    P = oracle.sample_paths(g, 4, 40_000, 5, oracle.ALIAS)
+    th = oracle.Oracle(g.n, P).theta_all(20)
+    q = np.arange(0, g.n, 5, dtype=np.int32)
+    ids, d2 = oracle.knn_many(th, q, 7, threads=3)
+    for i, v in enumerate(q):
+        a, b = oracle.knn(th, int(v), 7)
+        assert np.array_equal(ids[i], a) and np.array_equal(d2[i], b)

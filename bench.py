@@ -321,6 +321,23 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and not args.no_extras and args.workload != "batched":
         out["batched_vs_plain"] = batched_vs_plain(pk, torch, local)
 
+    # serving over the resident state of this workload (paths, index, theta)
+    topk_checks = []
+    if rank == 0 and not args.no_extras and args.workload == "scale":
+        P.vectors(50)
+        P.sync()
+        sv = serve_measure(pk, P.h.ctx, P.h.index, P.h.paths, P.h.vecs, g.n, local, n_burst=300, n_level=400,
+                           levels=(0.95,), n_serial=40)
+        topk_checks = sv.pop("_topk_checks")
+        out["serving"] = sv
+        pk.pantherpp_free_vecs(P.h.vecs)
+        P.h.vecs = None
+
+    # the unweighted fast path (t_ij = 1/deg) over the same graph: no table,
+    # one column entry per step; same step otherwise
+    if not args.no_extras and args.workload == "scale":
+        out["unweighted"] = unweighted_block(pk, torch, P, d_rp, d_col, args, R, T, k, queries, nq, peak)
+
     # end to end through the C ABI with host buffers
     if not args.no_extras:
         out["e2e"] = e2e(pk, torch, P, g, R, T, k, q_host, args, ws)
@@ -331,8 +348,52 @@ def run_ours(args, ws, rank, local):
         out["knn"] = knn_block(pk, torch, local, args)
 
     if rank == 0 and ws == 1 and not args.no_extras:
-        out["cpu_baseline"] = cpu_baseline(args.workload, g, R, T, k, q_host)
+        run = OracleRun(g, R, T, k, queries=q_host)
+        step_s, topk_s, F, parts = run.step(seed=1)
+        out["cpu_baseline"] = run.describe(step_s, topk_s, F, parts)
+        if topk_checks:   # served top-k rows against the oracle (same seed, R, T)
+            ok = True
+            for q, kk, ids, cnt in topk_checks:
+                rid, rcnt = run.o.topk_many(q, kk, threads=run.threads)
+                ok &= bool(np.array_equal(ids, rid) and np.array_equal(cnt, rcnt))
+            out["serving"]["topk_requests_checked_vs_oracle"] = len(topk_checks)
+            out["serving"]["topk_identical_to_oracle"] = ok
     return out
+
+
+def unweighted_block(pk, torch, P, d_rp, d_col, args, R, T, k, queries, nq, peak, steps=5, warmup=2):
+    """The step of the main workload on the same graph read as unweighted
+    (Eq. (3) with every weight equal): graph records and a copy of col
+    instead of alias tables, one column entry per sampling step."""
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    rec = []
+    for i in range(warmup + steps):
+        e = [ev() for _ in range(5)]
+        s = P.stream
+        e[0].record(s)
+        P.build_graph(d_rp, d_col, None, pk.MODE_UNWEIGHTED)
+        e[1].record(s)
+        P.sample_paths(args.seed, R, T, pk.MODE_UNWEIGHTED)
+        e[2].record(s)
+        P.build_index()
+        e[3].record(s)
+        P.topk(queries, k)
+        e[4].record(s)
+        if i >= warmup:
+            rec.append(e)
+    P.sync()
+    torch.cuda.synchronize()
+    names = ["tables", "sample", "index", "topk"]
+    ms = {nm: statistics.median(r[i].elapsed_time(r[i + 1]) for r in rec) for i, nm in enumerate(names)}
+    tot = statistics.median(r[0].elapsed_time(r[4]) for r in rec)
+    m = int(d_col.shape[0])
+    n = int(d_rp.shape[0]) - 1
+    tb = n * 24 + m * 12          # row_ptr read + vrec written; col read (validation) + col copied
+    return {"ms_per_step": round(tot, 3), "queries_per_s": round(nq / (tot * 1e-3), 1),
+            "paths_sampled_per_s": round(R / (ms["sample"] * 1e-3), 1),
+            "stages_ms": {nm: round(v, 3) for nm, v in ms.items()},
+            "tables_algo_bytes": tb, "tables_frac": round(tb / (ms["tables"] * 1e-3) / 1e9 / peak, 4),
+            "note": "same graph, weights ignored (t_ij = 1/deg); paths differ from the weighted run"}
 
 
 def batched_vs_plain(pk, torch, local):
@@ -871,32 +932,15 @@ def _requests(n, count, rng):
     return reqs
 
 
-def run_serve(args, ws, rank, local):
-    """Request loop over the resident graph, paths, index and Panther++ vectors
-    of the scale workload: capacity from a saturating burst, then Poisson
-    arrivals at 0.5 / 0.8 / 0.95 of it (p50 / p99 latency), against the same
-    requests executed one after another, and a check that every checked
-    request returns the same rows alone and in the mix."""
+def serve_measure(pk, ctx, ih, ph, vh, n, device, n_burst=300, n_level=400, levels=(0.5, 0.8, 0.95), n_serial=60,
+                  oracle_check=None):
+    """Request loop over resident paths, index and Panther++ vectors: capacity
+    from a saturating burst, then Poisson arrivals at fractions of it (p50 /
+    p99 latency), against the same kind of requests executed one after another
+    in the plain form; every 20th request of the last level is compared with
+    the same request alone (and, given oracle_check, its top-k rows with the
+    oracle's)."""
     import threading
-    import torch
-    import synth
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_1504_02577_gb300 as pk
-
-    torch.cuda.set_device(local)
-    p = dict(synth.WORKLOADS["scale"])
-    if args.n:
-        p["R"] = max(1, p["R"] * args.n // p["n"])
-        p["n"] = args.n
-    g = synth.workload_graph("scale", n=p["n"])
-    ctx = pk.panther_create(local)
-    gh = pk.panther_build_graph(ctx, g.n, g.m, g.row_ptr, g.col, g.w, pk.MEM_HOST, pk.MODE_ALIAS)
-    ph = pk.panther_sample_paths(ctx, gh, 1, p["R"], p["T"], pk.MODE_ALIAS)
-    ih = pk.panther_build_index(ctx, ph)
-    vh = pk.pantherpp_vectors(ctx, ih, ph, 50)
-    pk.panther_free_graph(gh)
-    pk.panther_sync(ctx)
     rng = np.random.default_rng(1)
 
     def outputs(req):
@@ -914,8 +958,7 @@ def run_serve(args, ws, rank, local):
             pk.pantherpp_knn(ctx, vh, q, q.shape[0], k, ids, vals, pk.KNN_BF16_SCREEN | pk.IO_HOST)
         return ids, vals
 
-    # serial plain execution of the same kind of stream (one request after another)
-    serial = _requests(g.n, 60, rng)
+    serial = _requests(n, n_serial, rng)
     alone(serial[0], plain=True)
     t0 = time.perf_counter()
     nq_serial = 0
@@ -924,10 +967,9 @@ def run_serve(args, ws, rank, local):
         nq_serial += r[1].shape[0]
     serial_qps = nq_serial / (time.perf_counter() - t0)
 
-    srv = pk.panther_serve_create(local, ih, ph, vh, 8 << 30, 4096, 4)
+    srv = pk.panther_serve_create(device, ih, ph, vh, 8 << 30, 4096, 4)
 
     def run_stream(reqs, rate):
-        """Submit with exponential inter-arrival times (rate = requests/s; 0 = all at once)."""
         outs = [outputs(r) for r in reqs]
         tickets = [None] * len(reqs)
         lat = [None] * len(reqs)
@@ -962,52 +1004,85 @@ def run_serve(args, ws, rank, local):
         nq = sum(r[1].shape[0] for r in reqs)
         return outs, np.array(lat), wall, nq
 
-    burst = _requests(g.n, 300, rng)
+    burst = _requests(n, n_burst, rng)
     _, lat_b, wall_b, nq_b = run_stream(burst, 0)
     cap_rps = len(burst) / wall_b
-    levels = {}
+    res_levels = {}
     check = None
-    for frac in (0.5, 0.8, 0.95):
-        reqs = _requests(g.n, 400, rng)
+    for frac in levels:
+        reqs = _requests(n, n_level, rng)
         outs, lat, wall, nq = run_stream(reqs, frac * cap_rps)
         kinds = np.array([r[0] for r in reqs])
-        levels[str(frac)] = {"offered_rps": round(frac * cap_rps, 1), "achieved_rps": round(len(reqs) / wall, 1),
-                             "queries_per_s": round(nq / wall, 1), "p50_ms": round(float(np.percentile(lat, 50)), 3),
-                             "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                             "topk_p50_ms": round(float(np.percentile(lat[kinds == 0], 50)), 3),
-                             "topk_p99_ms": round(float(np.percentile(lat[kinds == 0], 99)), 3),
-                             "knn_p50_ms": round(float(np.percentile(lat[kinds == 1], 50)), 3),
-                             "knn_p99_ms": round(float(np.percentile(lat[kinds == 1], 99)), 3)}
+        res_levels[str(frac)] = {"offered_rps": round(frac * cap_rps, 1), "achieved_rps": round(len(reqs) / wall, 1),
+                                 "queries_per_s": round(nq / wall, 1),
+                                 "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                                 "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                                 "topk_p50_ms": round(float(np.percentile(lat[kinds == 0], 50)), 3),
+                                 "topk_p99_ms": round(float(np.percentile(lat[kinds == 0], 99)), 3),
+                                 "knn_p50_ms": round(float(np.percentile(lat[kinds == 1], 50)), 3),
+                                 "knn_p99_ms": round(float(np.percentile(lat[kinds == 1], 99)), 3)}
         check = (reqs, outs)
     st = pk.panther_serve_stats(srv)
     pk.panther_serve_destroy(srv)
-    # identity: each of a sample of requests equals the same request alone
     reqs, outs = check
-    same = True
+    same, n_checked = True, 0
     for i in range(0, len(reqs), 20):
         a_ids, a_vals = alone(reqs[i])
         same &= bool(np.array_equal(a_ids, outs[i][0]) and np.array_equal(a_vals, outs[i][1]))
+        n_checked += 1
+    top = res_levels[str(levels[-1])]
+    out = {"capacity_rps": round(cap_rps, 1), "burst_p50_ms": round(float(np.percentile(lat_b, 50)), 3),
+           "burst_p99_ms": round(float(np.percentile(lat_b, 99)), 3), "poisson": res_levels,
+           "serial_plain_queries_per_s": round(serial_qps, 1),
+           "speedup_vs_serial": round(top["queries_per_s"] / serial_qps, 2),
+           "identical_alone_and_mixed": same, "requests_checked_alone": n_checked,
+           "mix": "75% top-k k in {5,10,50} 1-4096 vertices log-uniform, 25% k-NN k=10 1-1024 vertices",
+           "streams": 4, "mem_budget_gib": 8,
+           "server_stats": {"submitted": st[0], "completed": st[1], "batches": st[2],
+                            "max_requests_per_batch": st[3], "max_batches_in_flight": st[4], "refused": st[5]}}
+    out["_topk_checks"] = [(reqs[i][1], reqs[i][2], outs[i][0], outs[i][1])
+                           for i in range(0, len(reqs), 20) if reqs[i][0] == 0]
+    return out
+
+
+def run_serve(args, ws, rank, local):
+    """Request loop over the resident graph, paths, index and Panther++ vectors
+    of the scale workload (see serve_measure)."""
+    import torch
+    import synth
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_02577_gb300 as pk
+
+    torch.cuda.set_device(local)
+    p = dict(synth.WORKLOADS["scale"])
+    if args.n:
+        p["R"] = max(1, p["R"] * args.n // p["n"])
+        p["n"] = args.n
+    g = synth.workload_graph("scale", n=p["n"])
+    ctx = pk.panther_create(local)
+    gh = pk.panther_build_graph(ctx, g.n, g.m, g.row_ptr, g.col, g.w, pk.MEM_HOST, pk.MODE_ALIAS)
+    ph = pk.panther_sample_paths(ctx, gh, 1, p["R"], p["T"], pk.MODE_ALIAS)
+    ih = pk.panther_build_index(ctx, ph)
+    vh = pk.pantherpp_vectors(ctx, ih, ph, 50)
+    pk.panther_free_graph(gh)
+    pk.panther_sync(ctx)
+    res = serve_measure(pk, ctx, ih, ph, vh, g.n, local)
+    res.pop("_topk_checks")
     pk.pantherpp_free_vecs(vh)
     pk.panther_free_index(ih)
     pk.panther_free_paths(ph)
     pk.panther_destroy(ctx)
-    top = levels["0.95"]
-    return {
+    top = res["poisson"]["0.95"]
+    out = {
         "metric": METRIC, "value": top["queries_per_s"], "unit": "queries/s (served, 0.95 load)", "n_gpus": ws,
-        "steps": len(burst), "warmup": 0, "ms_per_step": round(1e3 * wall_b / len(burst), 3),
+        "steps": 300, "warmup": 0, "ms_per_step": None,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/u64 (integer counts)",
         "data": "synthetic",
-        "config": {"workload": "serve", "graph": f"Chung-Lu n={g.n} m={g.m} (scale workload)", "R": p["R"],
-                   "mix": "75% top-k k in {5,10,50} 1-4096 vertices log-uniform, 25% k-NN k=10 1-1024 vertices",
-                   "streams": 4, "mem_budget_gib": 8},
-        "capacity_rps": round(cap_rps, 1), "burst_p50_ms": round(float(np.percentile(lat_b, 50)), 3),
-        "burst_p99_ms": round(float(np.percentile(lat_b, 99)), 3), "poisson": levels,
-        "serial_plain_queries_per_s": round(serial_qps, 1),
-        "speedup_vs_serial": round(top["queries_per_s"] / serial_qps, 2),
-        "identical_alone_and_mixed": same,
-        "server_stats": {"submitted": st[0], "completed": st[1], "batches": st[2], "max_requests_per_batch": st[3],
-                         "max_batches_in_flight": st[4], "refused": st[5]},
+        "config": {"workload": "serve", "graph": f"Chung-Lu n={g.n} m={g.m} (scale workload)", "R": p["R"]},
     }
+    out.update(res)
+    return out
 
 def main():
     ap = argparse.ArgumentParser()

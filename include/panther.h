@@ -67,8 +67,10 @@ typedef enum {
 enum { PANTHER_MEM_HOST = 0, PANTHER_MEM_DEVICE = 1 };
 
 /* neighbour selection (Eq. 3); panther_build_graph takes a bit mask of the
- * tables to build, panther_sample_paths one mode */
-enum { PANTHER_MODE_PREFIX = 1, PANTHER_MODE_ALIAS = 2, PANTHER_MODE_BOTH = 3 };
+ * tables to build, panther_sample_paths one mode. UNWEIGHTED is Eq. (3) with
+ * every weight equal, t_ij = 1/deg(i) (the paper's unweighted networks): no
+ * table, a step reads one column entry. */
+enum { PANTHER_MODE_PREFIX = 1, PANTHER_MODE_ALIAS = 2, PANTHER_MODE_BOTH = 3, PANTHER_MODE_UNWEIGHTED = 4 };
 
 /* panther_topk / pantherpp_knn flags */
 enum {
@@ -128,12 +130,16 @@ PANTHER_API panther_status panther_sample_size(double eps, double delta, double 
  *   m        number of directed CSR entries (2|E|), m < 2^32
  *   row_ptr  int64[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = m
  *   col      int32[m], neighbours of each row in strictly ascending order
- *   w        uint32[m], weights >= 1; w(u,v) = w(v,u)
+ *   w        uint32[m], weights >= 1; w(u,v) = w(v,u). May be NULL when
+ *            modes is PANTHER_MODE_UNWEIGHTED alone (every weight 1).
  *   mem      PANTHER_MEM_HOST or PANTHER_MEM_DEVICE for the three arrays
- *   modes    PANTHER_MODE_PREFIX | PANTHER_MODE_ALIAS: tables to build
+ *   modes    a combination of PANTHER_MODE_PREFIX, PANTHER_MODE_ALIAS (the
+ *            tables to build) and PANTHER_MODE_UNWEIGHTED (keep a device copy
+ *            of col, 4 B per entry, for sampling with t_ij = 1/deg; no table)
  * Host arrays are staged in temporary device buffers; device arrays are read
  * in place during the call. The caller keeps ownership and nothing of the
- * CSR is kept afterwards (the tables hold what sampling needs). The call
+ * CSR is kept afterwards (the tables, or the library's own copy of col for
+ * UNWEIGHTED, hold what sampling needs). The call
  * validates the graph on the device (ranges, sorted rows, no self-loops,
  * symmetry with equal weights, every row sum * degree < 2^63) and returns
  * after the tables are built (it synchronises the stream).
@@ -153,10 +159,12 @@ PANTHER_API panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int6
  * with rejection on the 64-bit word (x0 | x1<<32). PREFIX picks the neighbour
  * j with cum(j-1) <= x < cum(j) for x = Uniform[0, sum w); ALIAS picks column
  * c = Uniform[0,deg) (x0,x1) and coin u = Uniform[0, sum w) (x2,x3) of the
- * same draw from the integer Vose table. Both realise Eq. 3 exactly and the
- * paths are reproducible bit for bit.
- *   R in [1, 2^31-1], T in [1, 31], mode PREFIX or ALIAS (its table must
- *   have been built).
+ * same draw from the integer Vose table. UNWEIGHTED picks column
+ * c = Uniform[0,deg) from (x0,x1), the same words and rejections as PREFIX, so
+ * its paths equal PREFIX paths of the same graph with every weight 1. All
+ * realise Eq. 3 exactly and the paths are reproducible bit for bit.
+ *   R in [1, 2^31-1], T in [1, 31], mode PREFIX, ALIAS or UNWEIGHTED (the
+ *   graph must have been built with that mode).
  * Rows live on the device as int32[R][stride], stride = 8, 16 or 32
  * (the smallest that holds T+1); entries past T+1 are unspecified.
  * Errors: EINVAL, ENOMEM, ECUDA. */

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libpanther.so")
 # status codes and flags (include/panther.h)
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBUSY = range(7)
 MEM_HOST, MEM_DEVICE = 0, 1
-MODE_PREFIX, MODE_ALIAS, MODE_BOTH = 1, 2, 3
+MODE_PREFIX, MODE_ALIAS, MODE_BOTH, MODE_UNWEIGHTED = 1, 2, 3, 4
 TOPK_BATCHED, TOPK_PLAIN = 0, 1
 KNN_BF16_SCREEN, KNN_FP32 = 0, 2
 IO_HOST = 0x100
@@ -183,6 +183,7 @@ def panther_sample_size(eps: float, delta: float, c: float, T: int) -> int:
 
 def panther_build_graph(ctx: int, n: int, m: int, row_ptr, col, w, mem: int, modes: int = MODE_BOTH) -> int:
     h = _vp()
+    # w may be None for MODE_UNWEIGHTED alone (every weight 1)
     _check(ctx, load_library().panther_build_graph(ctx, n, m, _buf(row_ptr, 8, n + 1, "row_ptr"),
                                                    _buf(col, 4, m, "col"), _buf(w, 4, m, "w"), mem, modes,
                                                    ctypes.byref(h)))
@@ -474,12 +475,13 @@ class Panther:
     def __exit__(self, *exc):
         self.close()
 
-    def build_graph(self, row_ptr, col, w, modes: int = MODE_BOTH):
+    def build_graph(self, row_ptr, col, w=None, modes: int = MODE_BOTH):
         n = int(row_ptr.shape[0]) - 1
         m = int(col.shape[0])
         mem = MEM_HOST if isinstance(row_ptr, np.ndarray) else MEM_DEVICE
         if self.h.graph:
             panther_free_graph(self.h.graph)
+            self.h.graph = None          # not left dangling if the build below fails
         self._enter()
         self.h.graph = panther_build_graph(self.h.ctx, n, m, row_ptr, col, w, mem, modes)
         self.n = n
@@ -488,6 +490,7 @@ class Panther:
     def sample_paths(self, seed: int, R: int, T: int, mode: int = MODE_ALIAS):
         if self.h.paths:
             panther_free_paths(self.h.paths)
+            self.h.paths = None
         self.h.paths = panther_sample_paths(self.h.ctx, self.h.graph, seed, R, T, mode)
         return self.h.paths
 
@@ -503,6 +506,7 @@ class Panther:
     def build_index(self):
         if self.h.index:
             panther_free_index(self.h.index)
+            self.h.index = None
         self.h.index = panther_build_index(self.h.ctx, self.h.paths)
         return self.h.index
 
@@ -543,6 +547,7 @@ class Panther:
     def vectors(self, D: int = 50):
         if self.h.vecs:
             pantherpp_free_vecs(self.h.vecs)
+            self.h.vecs = None
         self.h.vecs = pantherpp_vectors(self.h.ctx, self.h.index, self.h.paths, D)
         return self.h.vecs
 

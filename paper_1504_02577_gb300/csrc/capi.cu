@@ -201,6 +201,7 @@ void panther_free_graph(panther_graph* g) {
     dev_free(c, g->vrec);
     dev_free(c, g->prefix);
     dev_free(c, g->alias);
+    dev_free(c, g->col);
     cudaStreamSynchronize(c->stream);
     delete g;
 }

@@ -21,6 +21,10 @@
 // Rows of degree <= 16 take one thread (the sequential construction), rows up
 // to BIG_DEG one warp, and longer rows are cut into segments of SEG entries
 // spread over CTAs, with a per-row scan of the segment sums in between.
+//
+// UNWEIGHTED: no table. The graph keeps its own copy of col, and a step picks
+// col[start + Uniform[0, deg)] (t_ij = 1/deg, Eq. (3) with equal weights).
+// The validation kernels read a NULL weight array as all ones.
 #include <algorithm>
 #include <vector>
 
@@ -191,7 +195,7 @@ __device__ void row_stats(const G& g, int64_t v, int64_t start, int64_t deg, int
     bool bad = false;
     for (int64_t i = g.rank(); i < deg; i += G::size) {
         int32_t u = col[start + i];
-        uint32_t ww = w[start + i];
+        uint32_t ww = w ? w[start + i] : 1u;
         bad |= (u < 0) || ((int64_t)u >= n) || ((int64_t)u == v) || (ww == 0) ||
                (i > 0 && col[start + i - 1] >= u);
         s += ww;
@@ -286,7 +290,7 @@ __global__ void __launch_bounds__(256) stats_thread_kernel(const int64_t* __rest
         int32_t prev = -1;
         for (int64_t i = a; i < b; ++i) {
             int32_t u = col[i];
-            uint32_t ww = w[i];
+            uint32_t ww = w ? w[i] : 1u;
             bad |= (u < 0) || ((int64_t)u >= n) || ((int64_t)u == v) || (ww == 0) || (i > a && prev >= u);
             prev = u;
             s += ww;
@@ -356,7 +360,7 @@ __global__ void stats_seg_kernel(const int64_t* __restrict__ row_ptr, int64_t n,
     bool bad = false;
     for (int64_t e = a + threadIdx.x; e < b; e += BLK) {
         int32_t u = col[e];
-        uint32_t ww = w[e];
+        uint32_t ww = (w ? w[e] : 1u);
         bad |= (u < 0) || ((int64_t)u >= n) || ((int64_t)u == v) || (ww == 0) || (e > start && col[e - 1] >= u);
         sum += ww;
         if (u >= 0) {
@@ -413,7 +417,7 @@ __global__ void stats_short_kernel(const int64_t* __restrict__ row_ptr, int64_t 
             const int64_t i = (int64_t)g.rank() * 4 + j;
             if (i < deg) {
                 const int32_t u = col[a + i];
-                const uint32_t ww = w[a + i];
+                const uint32_t ww = (w ? w[a + i] : 1u);
                 bad |= (u < 0) || ((int64_t)u >= n) || ((int64_t)u == v) || (ww == 0) ||
                        (i > 0 && col[a + i - 1] >= u);
                 sum += ww;
@@ -1001,9 +1005,11 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
     if (n < 1 || n >= (int64_t(1) << 31)) return set_err(ctx, PANTHER_EINVAL, "n must be in [1, 2^31)");
     if (m < 0) return set_err(ctx, PANTHER_EINVAL, "m must be >= 0");
     if (m >= (int64_t(1) << 32)) return set_err(ctx, PANTHER_EOVERFLOW, "m must be < 2^32");
-    if (!row_ptr || (m > 0 && (!col || !w))) return set_err(ctx, PANTHER_EINVAL, "null graph array");
+    if (modes < 1 || modes > 7)
+        return set_err(ctx, PANTHER_EINVAL, "modes must combine PREFIX, ALIAS and UNWEIGHTED");
+    if (!row_ptr || (m > 0 && (!col || (!w && modes != PANTHER_MODE_UNWEIGHTED))))
+        return set_err(ctx, PANTHER_EINVAL, "null graph array (w may be NULL only for UNWEIGHTED alone)");
     if (mem != PANTHER_MEM_HOST && mem != PANTHER_MEM_DEVICE) return set_err(ctx, PANTHER_EINVAL, "bad mem");
-    if (modes < 1 || modes > 3) return set_err(ctx, PANTHER_EINVAL, "modes must be PREFIX, ALIAS or both");
     cudaSetDevice(ctx->device);
     cudaStream_t s = ctx->stream;
     cudaMemcpyKind kind = mem == PANTHER_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -1049,16 +1055,16 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
     if (mem == PANTHER_MEM_HOST) {
         if ((st = dev_alloc(ctx, (void**)&t_rp, sizeof(int64_t) * (n + 1))) ||
             (st = dev_alloc(ctx, (void**)&t_col, sizeof(int32_t) * m)) ||
-            (st = dev_alloc(ctx, (void**)&t_w, sizeof(uint32_t) * m)))
+            (w && (st = dev_alloc(ctx, (void**)&t_w, sizeof(uint32_t) * m))))
             return fail(st);
         if ((e = cudaMemcpyAsync(t_rp, row_ptr, sizeof(int64_t) * (n + 1), kind, s)) ||
             (m && (e = cudaMemcpyAsync(t_col, col, sizeof(int32_t) * m, kind, s))) ||
-            (m && (e = cudaMemcpyAsync(t_w, w, sizeof(uint32_t) * m, kind, s))))
+            (m && w && (e = cudaMemcpyAsync(t_w, w, sizeof(uint32_t) * m, kind, s))))
             return fail(cuda_err(ctx, e, "graph upload"));
     }
     const int64_t* d_rp = mem == PANTHER_MEM_HOST ? t_rp : row_ptr;
     const int32_t* d_col = mem == PANTHER_MEM_HOST ? t_col : col;
-    const uint32_t* d_w = mem == PANTHER_MEM_HOST ? t_w : w;
+    const uint32_t* d_w = w ? (mem == PANTHER_MEM_HOST ? t_w : w) : nullptr;
     if ((e = cudaMemsetAsync(nbig, 0, sizeof(int) * 8, s)) ||
         (e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 4, s)) ||
         (e = cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), s)) ||
@@ -1232,6 +1238,16 @@ extern "C" panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int64
         dev_free(ctx, sidx);
         dev_free(ctx, scum);
         if (e) return free_plan(), fail(cuda_err(ctx, e, "alias table"));
+    }
+    if ((modes & PANTHER_MODE_UNWEIGHTED) && m > 0) {
+        if (mem == PANTHER_MEM_HOST) {         // the staged copy becomes the graph's own
+            g->col = t_col;
+            t_col = nullptr;
+        } else {
+            if ((st = dev_alloc(ctx, (void**)&g->col, sizeof(int32_t) * m))) return free_plan(), fail(st);
+            if ((e = cudaMemcpyAsync(g->col, col, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s)))
+                return free_plan(), fail(cuda_err(ctx, e, "column copy"));
+        }
     }
     free_plan();
     dev_free(ctx, t_rp);

@@ -62,6 +62,7 @@ struct panther_graph {
     void* prefix = nullptr;          // [m]: uint2 {cum, col} or uint4 {cum_lo, cum_hi, col, 0}
     int prefix_wide = 0;             // 1 when a row sum reaches 2^32
     uint4* alias = nullptr;          // [m]: {thr_lo, thr_hi, col_self, col_alias}
+    int32_t* col = nullptr;          // [m]: neighbours (UNWEIGHTED mode only)
     uint64_t max_row_sum = 0;
 };
 

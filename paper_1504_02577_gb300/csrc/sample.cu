@@ -47,7 +47,7 @@ __device__ __forceinline__ uint32_t pick_prefix64(const uint4* __restrict__ e, u
     return v;
 }
 
-// MODE 1 = prefix, 2 = alias
+// MODE 1 = prefix, 2 = alias, 4 = unweighted (tab = the column array)
 template <int MODE, bool WIDE, int STRIDE>
 __global__ void __launch_bounds__(256, 5) sample_kernel(const uint4* __restrict__ vrec, const void* __restrict__ tab,
                                                      int64_t n, uint64_t seed, int64_t r0, int64_t R, int T,
@@ -67,7 +67,17 @@ __global__ void __launch_bounds__(256, 5) sample_kernel(const uint4* __restrict_
                 uint4 rec = __ldg(&vrec[v]);
                 if (rec.y != 0) {
                     uint64_t S = (uint64_t)rec.z | ((uint64_t)rec.w << 32);
-                    if (MODE == 1) {
+                    if (MODE == 4) {
+                        // t_ij = 1/deg: Uniform[0, deg) from the same words as
+                        // the prefix draw, so the walk equals prefix selection
+                        // with every weight 1
+                        uint64_t c = 0;
+                        for (uint32_t att = 0;; ++att) {
+                            pword4 w = path_draw(seed, (uint64_t)(r0 + r), (uint32_t)t, att);
+                            if (lemire64((uint64_t)w.x | ((uint64_t)w.y << 32), (uint64_t)rec.y, &c)) break;
+                        }
+                        v = (uint64_t)(uint32_t)__ldg((const int32_t*)tab + rec.x + c);
+                    } else if (MODE == 1) {
                         uint64_t x = 0;
                         for (uint32_t att = 0;; ++att) {
                             pword4 w = path_draw(seed, (uint64_t)(r0 + r), (uint32_t)t, att);
@@ -126,8 +136,8 @@ extern "C" panther_status panther_sample_paths_range(panther_ctx* ctx, const pan
     if (R < 1 || R > 0x7fffffffLL) return set_err(ctx, PANTHER_EINVAL, "R must be in [1, 2^31-1]");
     if (r0 < 0 || r0 > INT64_MAX - R) return set_err(ctx, PANTHER_EINVAL, "r0 must be >= 0 and r0 + R < 2^63");
     if (T < 1 || T > 31) return set_err(ctx, PANTHER_EINVAL, "T must be in [1, 31]");
-    if (mode != PANTHER_MODE_PREFIX && mode != PANTHER_MODE_ALIAS)
-        return set_err(ctx, PANTHER_EINVAL, "mode must be PREFIX or ALIAS");
+    if (mode != PANTHER_MODE_PREFIX && mode != PANTHER_MODE_ALIAS && mode != PANTHER_MODE_UNWEIGHTED)
+        return set_err(ctx, PANTHER_EINVAL, "mode must be PREFIX, ALIAS or UNWEIGHTED");
     if (!(g->modes & mode)) return set_err(ctx, PANTHER_EINVAL, "the graph has no table for this mode");
     cudaSetDevice(ctx->device);
     panther_paths* p = new panther_paths();
@@ -153,8 +163,10 @@ extern "C" panther_status panther_sample_paths_range(panther_ctx* ctx, const pan
             launch_sample<1, true>(ctx, g, g->prefix, seed, r0, R, T, p->stride, p->rows, blocks);
         else
             launch_sample<1, false>(ctx, g, g->prefix, seed, r0, R, T, p->stride, p->rows, blocks);
-    } else {
+    } else if (mode == PANTHER_MODE_ALIAS) {
         launch_sample<2, false>(ctx, g, g->alias, seed, r0, R, T, p->stride, p->rows, blocks);
+    } else {
+        launch_sample<4, false>(ctx, g, g->col, seed, r0, R, T, p->stride, p->rows, blocks);
     }
     ctx->launches++;
     cudaError_t e = cudaGetLastError();

@@ -270,6 +270,7 @@ def run_ours(args, ws, rank, local):
         torch.cuda.nvtx.range_pop()
     launches = P.launches() - l0
     P.sync()
+    tiers = pk.panther_topk_stats(P.h.ctx)
     ms_total = start.elapsed_time(end)
     ms_step = _max_over_ranks(ms_total / args.steps, ws)
     stage_ms = {s: statistics.median(r[i].elapsed_time(r[i + 1]) for r in rec) for i, s in enumerate(stages)}
@@ -315,6 +316,8 @@ def run_ours(args, ws, rank, local):
         "clocks": clocks,
         "graph_gen_s": round(gen_s, 2),
         "topk_shape": {"threads": shape[0], "table_slots": shape[1], "ctas_per_sm": shape[2]},
+        "topk_tiers": dict(zip(["queries", "lane", "group", "warp", "cta", "hub", "hub_via_buckets",
+                                "hub_via_tables", "bucket_overflows", "second_passes"], tiers)),
     }
 
     # batched vs plain on the 1M-vertex batched-query workload (16,384 queries, top-5)

@@ -163,10 +163,10 @@ PANTHER_API panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int6
  * c = Uniform[0,deg) from (x0,x1), the same words and rejections as PREFIX, so
  * its paths equal PREFIX paths of the same graph with every weight 1. All
  * realise Eq. 3 exactly and the paths are reproducible bit for bit.
- *   R in [1, 2^31-1], T in [1, 31], mode PREFIX, ALIAS or UNWEIGHTED (the
+ *   R in [1, 2^31-1], T in [1, 127], mode PREFIX, ALIAS or UNWEIGHTED (the
  *   graph must have been built with that mode).
- * Rows live on the device as int32[R][stride], stride = 8, 16 or 32
- * (the smallest that holds T+1); entries past T+1 are unspecified.
+ * Rows live on the device as int32[R][stride], stride = 8, 16, 32, 64 or 128
+ * (the smallest that holds T+1); entries past T+1 are -1.
  * Errors: EINVAL, ENOMEM, ECUDA. */
 PANTHER_API panther_status panther_sample_paths(panther_ctx* ctx, const panther_graph* g, uint64_t seed,
                                     int64_t R, int T, int mode, panther_paths** out);

@@ -138,7 +138,7 @@ panther_status panther_load_paths(panther_ctx* ctx, const char* path, panther_pa
     FileHeader hd;
     panther_status st = read_header(ctx, fl.f, "PNTHPATH", &hd);
     if (st) return st;
-    if (hd.T < 1 || hd.T > 31 || hd.L != hd.T + 1 || hd.stride != (uint32_t)path_stride((int)hd.L) || hd.n < 1 ||
+    if (hd.T < 1 || hd.T > (uint32_t)MAX_T || hd.L != hd.T + 1 || hd.stride != (uint32_t)path_stride((int)hd.L) || hd.n < 1 ||
         hd.n >= (int64_t(1) << 31) || hd.R < 1 || hd.R > 0x7fffffffLL || hd.x < 0 ||
         (hd.mode != PANTHER_MODE_PREFIX && hd.mode != PANTHER_MODE_ALIAS && hd.mode != PANTHER_MODE_UNWEIGHTED))
         return set_err(ctx, PANTHER_EINVAL, "inconsistent paths checkpoint header");

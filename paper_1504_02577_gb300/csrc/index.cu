@@ -4,7 +4,8 @@
 // [R][stride] array is a (key = vertex, value = r) pair unless j >= T+1 or the
 // same vertex occurred earlier in row r (P_v is a set). Rows are stride-
 // aligned inside every 32-lane round, so the duplicate test is one
-// __match_any_sync. Later passes read the (key, value) pairs of the previous
+// __match_any_sync; rows of 64 or 128 entries span two or four rounds of one
+// warp, and their entries are also compared with the row's earlier rounds. Later passes read the (key, value) pairs of the previous
 // pass. Every pass is: tile histogram -> exclusive scan over (digit, tile) ->
 // stable scatter. The scatter ranks items with warp-private digit counters:
 // warps own contiguous sub-ranges of a tile and walk them in order, so the
@@ -46,8 +47,8 @@ __device__ __forceinline__ bool item_ok(const Src& s, int64_t i, int32_t x) {
     if (s.first) {
         const unsigned lane = threadIdx.x & 31;
         const unsigned peers = __match_any_sync(0xffffffffu, x);
-        const unsigned rowbase = lane & ~(unsigned)(s.stride - 1);
-        const unsigned rowmask = (s.stride == 32) ? 0xffffffffu : (((1u << s.stride) - 1u) << rowbase);
+        const unsigned rowbase = s.stride >= 32 ? 0u : lane & ~(unsigned)(s.stride - 1);
+        const unsigned rowmask = (s.stride >= 32) ? 0xffffffffu : (((1u << s.stride) - 1u) << rowbase);
         const unsigned before = peers & rowmask & ((1u << lane) - 1u);
         const int j = (int)(i & (s.stride - 1));
         return i < s.R * s.stride && j < s.L && before == 0;
@@ -55,6 +56,32 @@ __device__ __forceinline__ bool item_ok(const Src& s, int64_t i, int32_t x) {
     return i < s.count;
 }
 
+// Pass 0 with rows wider than a 32-item round (stride 64 or 128): bit k is
+// set when the item of round k repeats an entry of an earlier round of the
+// same row (rows are stride-aligned and a warp's rounds hold whole rows, so
+// the at most three earlier rounds of the row are in this warp's registers;
+// each is compared through 32 broadcasts). Every lane must call it.
+__device__ __forceinline__ uint32_t long_row_repeats(const Src& s, int64_t wbase, const int32_t (&x)[IX_ROUNDS]) {
+    uint32_t rep = 0;
+#pragma unroll
+    for (int k = 1; k < IX_ROUNDS; ++k) {
+        const int64_t row = (wbase + k * 32) / s.stride;
+        bool d = false;
+#pragma unroll
+        for (int o = 1; o <= 3; ++o) {
+            if (k - o < 0) continue;
+            if ((wbase + (k - o) * 32) / s.stride != row) continue;     // warp-uniform
+#pragma unroll 8
+            for (int sl = 0; sl < 32; ++sl) d |= __shfl_sync(0xffffffffu, x[k - o], sl) == x[k];
+        }
+        rep |= (d ? 1u : 0u) << k;
+    }
+    return rep;
+}
+
+// LONG: pass 0 over rows of 64 or 128 entries (separate instantiations keep
+// the registers of the common kernels unchanged)
+template <bool LONG>
 __global__ void __launch_bounds__(IX_T) hist_kernel(Src s, int shift, int radix, int64_t ntiles,
                                                     int64_t* __restrict__ counts) {
     __shared__ unsigned h[MAX_RADIX];
@@ -64,10 +91,12 @@ __global__ void __launch_bounds__(IX_T) hist_kernel(Src s, int shift, int radix,
     int32_t x[IX_ROUNDS];
 #pragma unroll
     for (int k = 0; k < IX_ROUNDS; ++k) x[k] = load_raw(s, base + k * 32);   // all loads in flight
+    const uint32_t rep = LONG ? long_row_repeats(s, base - (threadIdx.x & 31), x) : 0u;
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < IX_ROUNDS; ++k)
-        if (item_ok(s, base + k * 32, x[k])) atomicAdd(&h[((uint32_t)x[k] >> shift) & (radix - 1)], 1u);
+        if (item_ok(s, base + k * 32, x[k]) && !((rep >> k) & 1u))
+            atomicAdd(&h[((uint32_t)x[k] >> shift) & (radix - 1)], 1u);
     __syncthreads();
     for (int d = threadIdx.x; d < radix; d += IX_T) counts[(int64_t)d * ntiles + blockIdx.x] = h[d];
 }
@@ -78,6 +107,7 @@ __global__ void __launch_bounds__(IX_T) hist_kernel(Src s, int shift, int radix,
 constexpr size_t SC_SMEM = (size_t)IX_WARPS * MAX_RADIX * 4 + (size_t)MAX_RADIX * 8 + (size_t)MAX_RADIX * 4 +
                            (size_t)IX_TILE * 8 + 64;
 
+template <bool LONG>
 __global__ void __launch_bounds__(IX_T, 2) scatter_kernel(Src s, int shift, int radix, int64_t ntiles,
                                                           const int64_t* __restrict__ offs,
                                                           int32_t* __restrict__ okeys, int32_t* __restrict__ ovals) {
@@ -101,6 +131,12 @@ __global__ void __launch_bounds__(IX_T, 2) scatter_kernel(Src s, int shift, int 
     for (int k = 0; k < IX_ROUNDS; ++k) key[k] = (uint32_t)load_raw(s, base + k * 32 + lane);   // loads in flight
 #pragma unroll
     for (int k = 0; k < IX_ROUNDS; ++k) okmask |= (item_ok(s, base + k * 32 + lane, (int32_t)key[k]) ? 1u : 0u) << k;
+    if (LONG) {
+        int32_t xk[IX_ROUNDS];
+#pragma unroll
+        for (int k = 0; k < IX_ROUNDS; ++k) xk[k] = (int32_t)key[k];
+        okmask &= ~long_row_repeats(s, base, xk);
+    }
     __syncthreads();
     // phase 1: per-warp digit counts and each item's rank within its warp
 #pragma unroll
@@ -280,7 +316,8 @@ extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_pa
         panther_free_index(ix);
         return st;
     }
-    PCK(ctx, cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM));
+    PCK(ctx, cudaFuncSetAttribute(scatter_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM));
+    PCK(ctx, cudaFuncSetAttribute(scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM));
     Src src{};
     src.rows = p->rows;
     src.R = p->R;
@@ -294,7 +331,10 @@ extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_pa
         int64_t ntiles = pass == 0 ? tiles0 : ceil_div(count, IX_TILE);
         if (ntiles < 1) ntiles = 1;
         int64_t len = (int64_t)radix * ntiles;
-        hist_kernel<<<(unsigned)ntiles, IX_T, 0, s>>>(src, shift, radix, ntiles, counts);
+        if (src.first && src.stride > 32)
+            hist_kernel<true><<<(unsigned)ntiles, IX_T, 0, s>>>(src, shift, radix, ntiles, counts);
+        else
+            hist_kernel<false><<<(unsigned)ntiles, IX_T, 0, s>>>(src, shift, radix, ntiles, counts);
         ctx->launches++;
         cudaError_t e = cudaMemcpyAsync(offs, counts, sizeof(int64_t) * len, cudaMemcpyDeviceToDevice, s);
         if (e) { cleanup(); panther_free_index(ix); return cuda_err(ctx, e, "index scan copy"); }
@@ -307,7 +347,10 @@ extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_pa
             if (!e) e = cudaStreamSynchronize(s);
             if (e) { cleanup(); panther_free_index(ix); return cuda_err(ctx, e, "index count"); }
         }
-        scatter_kernel<<<(unsigned)ntiles, IX_T, SC_SMEM, s>>>(src, shift, radix, ntiles, offs, ok, ov);
+        if (src.first && src.stride > 32)
+            scatter_kernel<true><<<(unsigned)ntiles, IX_T, SC_SMEM, s>>>(src, shift, radix, ntiles, offs, ok, ov);
+        else
+            scatter_kernel<false><<<(unsigned)ntiles, IX_T, SC_SMEM, s>>>(src, shift, radix, ntiles, offs, ok, ov);
         ctx->launches++;
         e = cudaGetLastError();
         if (e) { cleanup(); panther_free_index(ix); return cuda_err(ctx, e, "index scatter"); }
@@ -433,7 +476,8 @@ extern "C" panther_status panther_build_index_noalloc(panther_ctx* ctx, const pa
     const int radix = 1 << rb;
     const int64_t tiles0 = ceil_div(p->R * p->stride, IX_TILE);
     if (tiles0 > NA_MAX_TILES) return set_err(ctx, PANTHER_EOVERFLOW, "too many path rows for the static scratch");
-    PCK(ctx, cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM));
+    PCK(ctx, cudaFuncSetAttribute(scatter_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM));
+    PCK(ctx, cudaFuncSetAttribute(scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM));
     Src src{};
     src.rows = p->rows;
     src.R = p->R;
@@ -447,7 +491,10 @@ extern "C" panther_status panther_build_index_noalloc(panther_ctx* ctx, const pa
         int64_t ntiles = pass == 0 ? tiles0 : ceil_div(count, IX_TILE);
         if (ntiles < 1) ntiles = 1;
         const int64_t len = (int64_t)radix * ntiles;
-        hist_kernel<<<(unsigned)ntiles, IX_T, 0, s>>>(src, pass * rb, radix, ntiles, counts);
+        if (src.first && src.stride > 32)
+            hist_kernel<true><<<(unsigned)ntiles, IX_T, 0, s>>>(src, pass * rb, radix, ntiles, counts);
+        else
+            hist_kernel<false><<<(unsigned)ntiles, IX_T, 0, s>>>(src, pass * rb, radix, ntiles, counts);
         na_scan_kernel<<<1, 1024, 0, s>>>(counts, offs, len, tot);
         ctx->launches += 2;
         if (pass == 0) {
@@ -455,7 +502,10 @@ extern "C" panther_status panther_build_index_noalloc(panther_ctx* ctx, const pa
             PCK(ctx, cudaStreamSynchronize(s));
         }
         int32_t* outv = last ? dev_pid : ov;     // the final pass writes the caller's pid array
-        scatter_kernel<<<(unsigned)ntiles, IX_T, SC_SMEM, s>>>(src, pass * rb, radix, ntiles, offs, ok, outv);
+        if (src.first && src.stride > 32)
+            scatter_kernel<true><<<(unsigned)ntiles, IX_T, SC_SMEM, s>>>(src, pass * rb, radix, ntiles, offs, ok, outv);
+        else
+            scatter_kernel<false><<<(unsigned)ntiles, IX_T, SC_SMEM, s>>>(src, pass * rb, radix, ntiles, offs, ok, outv);
         ctx->launches++;
         PCK(ctx, cudaGetLastError());
         src.first = 0;

@@ -126,8 +126,11 @@ void dev_free(panther_ctx* ctx, void* p);
 
 static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// stride of a path row for L vertices: 8, 16 or 32 int32
-static inline int path_stride(int L) { return L <= 8 ? 8 : (L <= 16 ? 16 : 32); }
+// stride of a path row for L vertices: 8, 16, 32, 64 or 128 int32
+static inline int path_stride(int L) {
+    return L <= 8 ? 8 : (L <= 16 ? 16 : (L <= 32 ? 32 : (L <= 64 ? 64 : 128)));
+}
+constexpr int MAX_T = 127;   // longest path: T + 1 = 128 vertices fill the widest row
 
 // device-wide exclusive scan of int64 values (in place), n >= 1; uses scratch
 panther_status scan_exclusive_i64(panther_ctx* ctx, int64_t* data, int64_t n);

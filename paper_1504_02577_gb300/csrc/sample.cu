@@ -115,6 +115,76 @@ __global__ void __launch_bounds__(256, 5) sample_kernel(const uint4* __restrict_
     }
 }
 
+// Rows of 64 or 128 entries (T >= 32): the same walk, but the row is not
+// held in registers; every 8 entries go out as two 16-byte stores.
+template <int MODE, bool WIDE>
+__global__ void __launch_bounds__(256) sample_long_kernel(const uint4* __restrict__ vrec, const void* __restrict__ tab,
+                                                          int64_t n, uint64_t seed, int64_t r0, int64_t R, int T,
+                                                          int stride, int32_t* __restrict__ rows, uint32_t* status) {
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += nthreads) {
+        int32_t buf[8];
+        int4* dst = (int4*)(rows + r * stride);
+        uint64_t v = 0;
+        for (uint32_t att = 0;; ++att) {
+            pword4 x = path_draw(seed, (uint64_t)(r0 + r), 0, att);
+            if (lemire64((uint64_t)x.x | ((uint64_t)x.y << 32), (uint64_t)n, &v)) break;
+        }
+        buf[0] = (int32_t)v;
+        for (int t8 = 0; t8 < stride; t8 += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int t = t8 + u;
+                if (t == 0) continue;
+                if (t > T) {
+                    buf[u] = -1;
+                    continue;
+                }
+                const uint4 rec = __ldg(&vrec[v]);
+                if (rec.y != 0) {
+                    const uint64_t S = (uint64_t)rec.z | ((uint64_t)rec.w << 32);
+                    if (MODE == 4) {
+                        uint64_t c = 0;
+                        for (uint32_t att = 0;; ++att) {
+                            pword4 w = path_draw(seed, (uint64_t)(r0 + r), (uint32_t)t, att);
+                            if (lemire64((uint64_t)w.x | ((uint64_t)w.y << 32), (uint64_t)rec.y, &c)) break;
+                        }
+                        v = (uint64_t)(uint32_t)__ldg((const int32_t*)tab + rec.x + c);
+                    } else if (MODE == 1) {
+                        uint64_t x = 0;
+                        for (uint32_t att = 0;; ++att) {
+                            pword4 w = path_draw(seed, (uint64_t)(r0 + r), (uint32_t)t, att);
+                            if (lemire64((uint64_t)w.x | ((uint64_t)w.y << 32), S, &x)) break;
+                        }
+                        if (WIDE)
+                            v = pick_prefix64((const uint4*)tab + rec.x, rec.y, x);
+                        else
+                            v = pick_prefix32((const uint2*)tab + rec.x, rec.y, (uint32_t)x);
+                    } else {
+                        uint64_t c = 0, uu = 0;
+                        for (uint32_t att = 0;; ++att) {
+                            pword4 w = path_draw(seed, (uint64_t)(r0 + r), (uint32_t)t, att);
+                            bool ok0 = lemire64((uint64_t)w.x | ((uint64_t)w.y << 32), (uint64_t)rec.y, &c);
+                            bool ok1 = lemire64((uint64_t)w.z | ((uint64_t)w.w << 32), S, &uu);
+                            if (ok0 && ok1) break;
+                        }
+                        const uint4 e = __ldg((const uint4*)tab + rec.x + c);
+                        const uint64_t thr = (uint64_t)e.x | ((uint64_t)e.y << 32);
+                        v = uu < thr ? e.z : e.w;
+                    }
+                    if (v >= (uint64_t)n) {
+                        flag_status(status, ST_BAD_INDEX);
+                        v = 0;
+                    }
+                }
+                buf[u] = (int32_t)v;
+            }
+            dst[t8 / 4] = make_int4(buf[0], buf[1], buf[2], buf[3]);
+            dst[t8 / 4 + 1] = make_int4(buf[4], buf[5], buf[6], buf[7]);
+        }
+    }
+}
+
 template <int MODE, bool WIDE>
 void launch_sample(panther_ctx* ctx, const panther_graph* g, const void* tab, uint64_t seed, int64_t r0, int64_t R,
                    int T, int stride, int32_t* rows, unsigned blocks) {
@@ -123,8 +193,11 @@ void launch_sample(panther_ctx* ctx, const panther_graph* g, const void* tab, ui
         sample_kernel<MODE, WIDE, 8><<<blocks, 256, 0, s>>>(g->vrec, tab, g->n, seed, r0, R, T, rows, ctx->d_status);
     else if (stride == 16)
         sample_kernel<MODE, WIDE, 16><<<blocks, 256, 0, s>>>(g->vrec, tab, g->n, seed, r0, R, T, rows, ctx->d_status);
-    else
+    else if (stride == 32)
         sample_kernel<MODE, WIDE, 32><<<blocks, 256, 0, s>>>(g->vrec, tab, g->n, seed, r0, R, T, rows, ctx->d_status);
+    else
+        sample_long_kernel<MODE, WIDE><<<blocks, 256, 0, s>>>(g->vrec, tab, g->n, seed, r0, R, T, stride, rows,
+                                                              ctx->d_status);
 }
 
 }  // namespace
@@ -135,7 +208,7 @@ extern "C" panther_status panther_sample_paths_range(panther_ctx* ctx, const pan
     *out = nullptr;
     if (R < 1 || R > 0x7fffffffLL) return set_err(ctx, PANTHER_EINVAL, "R must be in [1, 2^31-1]");
     if (r0 < 0 || r0 > INT64_MAX - R) return set_err(ctx, PANTHER_EINVAL, "r0 must be >= 0 and r0 + R < 2^63");
-    if (T < 1 || T > 31) return set_err(ctx, PANTHER_EINVAL, "T must be in [1, 31]");
+    if (T < 1 || T > MAX_T) return set_err(ctx, PANTHER_EINVAL, "T must be in [1, 127]");
     if (mode != PANTHER_MODE_PREFIX && mode != PANTHER_MODE_ALIAS && mode != PANTHER_MODE_UNWEIGHTED)
         return set_err(ctx, PANTHER_EINVAL, "mode must be PREFIX, ALIAS or UNWEIGHTED");
     if (!(g->modes & mode)) return set_err(ctx, PANTHER_EINVAL, "the graph has no table for this mode");

@@ -426,11 +426,50 @@ __device__ __forceinline__ bool hash_add_conv(unsigned long long* tab, uint32_t 
     return ok;
 }
 
+// Rows of 64 or 128 entries (T >= 32): the warp takes its lanes' paths one
+// at a time. Lane l holds entries l, l+32, ... of the row (one coalesced
+// 128-byte load per round); an entry is a candidate at its first occurrence
+// in the row (no lower lane of its round, no lane of an earlier round holds
+// it) and if it is not v; with thr > 0 only the u with cls[u] >= thr.
+// Returns false if a table ran out of slots. Every lane must call it.
+template <int STRIDE>
+__device__ __forceinline__ bool insert_paths_warp(const PathsRef& P, int32_t r, int32_t v, unsigned long long* tab,
+                                                  uint32_t nslots, bool active, uint32_t thr) {
+    constexpr int NR = STRIDE / 32;
+    const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    active &= (uint32_t)r < (uint64_t)P.R;
+    unsigned pend = __ballot_sync(0xffffffffu, active);
+    bool ok = true;
+    while (pend) {                                        // warp-uniform
+        const int src = __ffs(pend) - 1;
+        pend &= pend - 1;
+        const int32_t rr = __shfl_sync(0xffffffffu, r, src);
+        const int32_t* row = P.rows + (int64_t)rr * STRIDE;
+        int32_t y[NR];
+#pragma unroll
+        for (int m = 0; m < NR; ++m) y[m] = __ldg(row + m * 32 + lane);
+#pragma unroll
+        for (int m = 0; m < NR; ++m) {
+            if (m * 32 >= P.L) break;                     // warp-uniform: the rest is padding
+            bool take = m * 32 + (int)lane < P.L && y[m] != v;
+            take &= (__match_any_sync(0xffffffffu, y[m]) & lt) == 0;
+#pragma unroll
+            for (int mm = 0; mm < m; ++mm)
+#pragma unroll 8
+                for (int sl = 0; sl < 32; ++sl) take &= __shfl_sync(0xffffffffu, y[mm], sl) != y[m];
+            if (thr && take) take = __ldg(P.cls + y[m]) >= thr;
+            if (__any_sync(0xffffffffu, take)) ok &= hash_add_conv(tab, nslots, (uint32_t)y[m], 1u, take);
+        }
+    }
+    return ok;
+}
+
 // insert the distinct vertices u != v of path r (lanes with active == false pass r = -1);
 // with thr > 0 only the u with cls[u] >= thr
 template <int STRIDE>
 __device__ __forceinline__ bool insert_path_conv(const PathsRef& P, int32_t r, int32_t v, unsigned long long* tab,
                                                  uint32_t nslots, bool active, uint32_t thr = 0) {
+    if constexpr (STRIDE > 32) return insert_paths_warp<STRIDE>(P, r, v, tab, nslots, active, thr);
     active &= (uint32_t)r < (uint64_t)P.R;
     int32_t x[STRIDE];
     const int4* src = (const int4*)(P.rows + (int64_t)(active ? r : 0) * STRIDE);
@@ -919,6 +958,7 @@ __device__ __forceinline__ uint32_t warp_sort32_desc32(uint32_t a) {
 template <int STRIDE>
 __device__ bool warp_query32(const PathsRef& P, int32_t v, int64_t qi, uint32_t* tab, const OutRef& o, int cb,
                              uint32_t* status) {
+    if constexpr (STRIDE > 32) return false;              // long rows: the wide form
     const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     const int64_t a = P.off[v], b = P.off[v + 1];
     if (b - a >= (int64_t(1) << cb) - 1) return false;
@@ -1034,8 +1074,16 @@ __global__ void __launch_bounds__(1024, 1) single_kernel(PathsRef P, const int32
     }
     // global table: gtab is EMPTY on entry and left EMPTY on exit
     bool ok = true;
-    for (int64_t e = P.off[v] + threadIdx.x; e < P.off[v + 1]; e += blockDim.x)
-        ok &= insert_path<STRIDE, false>(P, P.pid[e], (int32_t)v, gtab, gslots);
+    if constexpr (STRIDE > 32) {
+        for (int64_t base = P.off[v] + (threadIdx.x & ~31u); base < P.off[v + 1]; base += blockDim.x) {
+            const int64_t e = base + (threadIdx.x & 31);
+            const bool act = e < P.off[v + 1];
+            ok &= insert_paths_warp<STRIDE>(P, act ? P.pid[e] : -1, (int32_t)v, gtab, gslots, act, 0);
+        }
+    } else {
+        for (int64_t e = P.off[v] + threadIdx.x; e < P.off[v + 1]; e += blockDim.x)
+            ok &= insert_path<STRIDE, false>(P, P.pid[e], (int32_t)v, gtab, gslots);
+    }
     if (!ok) flag_status(status, ST_HASH_FULL);
     __syncthreads();
     __threadfence_block();
@@ -1093,8 +1141,16 @@ __global__ void g_count_kernel(PathsRef P, const int32_t* __restrict__ queries, 
     unsigned long long* tab = arena + G.tab_off[g];
     const uint32_t thr = G.thr ? G.thr[g] : 0;
     bool ok = true;
-    for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x)
-        ok &= insert_path<STRIDE, false>(P, P.pid[e], v, tab, G.tab_n[g], thr);
+    if constexpr (STRIDE > 32) {
+        for (int64_t base = a + (threadIdx.x & ~31u); base < b; base += blockDim.x) {   // warp-uniform
+            const int64_t e = base + (threadIdx.x & 31);
+            const bool act = e < b;
+            ok &= insert_paths_warp<STRIDE>(P, act ? P.pid[e] : -1, v, tab, G.tab_n[g], act, thr);
+        }
+    } else {
+        for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x)
+            ok &= insert_path<STRIDE, false>(P, P.pid[e], v, tab, G.tab_n[g], thr);
+    }
     if (!ok) flag_status(status, ST_HASH_FULL);
 }
 
@@ -1362,11 +1418,7 @@ static panther_status hub_buckets(panther_ctx* ctx, const PathsRef& P, const int
     const int bpaths = std::max(32, B_SLOTS1 / (2 * std::max(1, P.L - 1)));
     const int64_t per_bucket = (int64_t)B_CAP * 8 + 4 + KMAX * 8;
     const int64_t budget = std::max<int64_t>(ctx->scratch_budget, per_bucket * 64);
-    int stride = 0;
-    {   // stride of the path rows from L
-        int L = P.L;
-        stride = L <= 8 ? 8 : (L <= 16 ? 16 : 32);
-    }
+    const int stride = path_stride(P.L);
     // The shared-memory attribute applies to the current device only: it is
     // set once per device (bit `device` of the mask). Contexts on several host
     // threads (the serving workers) may get here together; setting it twice
@@ -1377,6 +1429,8 @@ static panther_status hub_buckets(panther_ctx* ctx, const PathsRef& P, const int
         PCK(ctx, cudaFuncSetAttribute(b_scatter_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS1 * 8));
         PCK(ctx, cudaFuncSetAttribute(b_scatter_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS1 * 8));
         PCK(ctx, cudaFuncSetAttribute(b_scatter_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS1 * 8));
+        PCK(ctx, cudaFuncSetAttribute(b_scatter_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS1 * 8));
+        PCK(ctx, cudaFuncSetAttribute(b_scatter_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS1 * 8));
         PCK(ctx, cudaFuncSetAttribute(b_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, B_SLOTS2 * 8));
         attr_set.fetch_or(dev_bit, std::memory_order_acq_rel);
     }
@@ -1424,7 +1478,9 @@ static panther_status hub_buckets(panther_ctx* ctx, const PathsRef& P, const int
         const unsigned g1 = (unsigned)coff.back();
         if (stride == 8) b_scatter_kernel<8><<<g1, 512, B_SLOTS1 * 8, s>>>(P, queries, B, ctx->d_status);
         else if (stride == 16) b_scatter_kernel<16><<<g1, 512, B_SLOTS1 * 8, s>>>(P, queries, B, ctx->d_status);
-        else b_scatter_kernel<32><<<g1, 512, B_SLOTS1 * 8, s>>>(P, queries, B, ctx->d_status);
+        else if (stride == 32) b_scatter_kernel<32><<<g1, 512, B_SLOTS1 * 8, s>>>(P, queries, B, ctx->d_status);
+        else if (stride == 64) b_scatter_kernel<64><<<g1, 512, B_SLOTS1 * 8, s>>>(P, queries, B, ctx->d_status);
+        else b_scatter_kernel<128><<<g1, 512, B_SLOTS1 * 8, s>>>(P, queries, B, ctx->d_status);
         b_count_kernel<<<(unsigned)nbt, B_T2, B_SLOTS2 * 8, s>>>(B, k, partial, ctx->d_status);
         GPlan G{B.qidx, nullptr, nullptr, nullptr, B.bucket_off, rng, nullptr};
         g_merge_cta_kernel<<<rng, 256, 0, s>>>(G, partial, o);
@@ -1464,7 +1520,7 @@ static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int3
                                  std::vector<HubQuery>& redo) {
     cudaStream_t s = ctx->stream;
     const int64_t budget_slots = std::max<int64_t>(ctx->scratch_budget / 8 / 2, 1 << 20);
-    const int stride = P.L <= 8 ? 8 : (P.L <= 16 ? 16 : 32);
+    const int stride = path_stride(P.L);
     size_t pos = 0;
     unsigned long long*& arena = ctx->hub_arena;
     int64_t& arena_slots = ctx->hub_arena_slots;
@@ -1521,7 +1577,9 @@ static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int3
                 (const int64_t*)(dplan + o_i), (const int64_t*)(dplan + o_s), rng, (const uint32_t*)(dplan + o_t)};
         if (stride == 8) g_count_kernel<8><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
         else if (stride == 16) g_count_kernel<16><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
-        else g_count_kernel<32><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
+        else if (stride == 32) g_count_kernel<32><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
+        else if (stride == 64) g_count_kernel<64><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
+        else g_count_kernel<128><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
         g_select_kernel<<<(unsigned)soff.back(), 512, 0, s>>>(G, arena, k, partial);
         g_merge_cta_kernel<<<rng, 256, 0, s>>>(G, partial, o);
         hub_check_kernel<<<(unsigned)ceil_div(rng, 256), 256, 0, s>>>(G.qidx, G.thr, rng, o, dredo);
@@ -1558,7 +1616,9 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
     panther_status st;
     if (p->stride == 8) st = set_smem_attr<8>(ctx, attr);
     else if (p->stride == 16) st = set_smem_attr<16>(ctx, attr);
-    else st = set_smem_attr<32>(ctx, attr);
+    else if (p->stride == 32) st = set_smem_attr<32>(ctx, attr);
+    else if (p->stride == 64) st = set_smem_attr<64>(ctx, attr);
+    else st = set_smem_attr<128>(ctx, attr);
     if (st) return st;
     PathsRef P{p->rows, p->R, p->L, ix->off, ix->pid, ix->n, ix->cls};
     OutRef o{ids, cnt, k};
@@ -1586,8 +1646,13 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
                 single_kernel<8><<<1, sh.threads, smem, s>>>(P, queries, i, o, sh.cta_slots, gtab, gslots, ctx->d_status);
             else if (p->stride == 16)
                 single_kernel<16><<<1, sh.threads, smem, s>>>(P, queries, i, o, sh.cta_slots, gtab, gslots, ctx->d_status);
-            else
+            else if (p->stride == 32)
                 single_kernel<32><<<1, sh.threads, smem, s>>>(P, queries, i, o, sh.cta_slots, gtab, gslots, ctx->d_status);
+            else if (p->stride == 64)
+                single_kernel<64><<<1, sh.threads, smem, s>>>(P, queries, i, o, sh.cta_slots, gtab, gslots, ctx->d_status);
+            else
+                single_kernel<128><<<1, sh.threads, smem, s>>>(P, queries, i, o, sh.cta_slots, gtab, gslots,
+                                                              ctx->d_status);
             ctx->launches++;
         }
         dev_free(ctx, gtab);
@@ -1651,7 +1716,9 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
     unsigned blocks = (unsigned)(ctx->num_sms * sh.blocks_per_sm);
     if (p->stride == 8) persistent_kernel<8><<<blocks, sh.threads, smem, s>>>(A);
     else if (p->stride == 16) persistent_kernel<16><<<blocks, sh.threads, smem, s>>>(A);
-    else persistent_kernel<32><<<blocks, sh.threads, smem, s>>>(A);
+    else if (p->stride == 32) persistent_kernel<32><<<blocks, sh.threads, smem, s>>>(A);
+    else if (p->stride == 64) persistent_kernel<64><<<blocks, sh.threads, smem, s>>>(A);
+    else persistent_kernel<128><<<blocks, sh.threads, smem, s>>>(A);
     ctx->launches++;
     if (ccap_big > ccap) {
         // CTA tier only: its list is tier 7's, its counters start at [9]
@@ -1660,7 +1727,9 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
         const unsigned bb = (unsigned)ctx->num_sms;
         if (p->stride == 8) persistent_kernel<8><<<bb, BIG_T, BIG_SMEM, s>>>(B);
         else if (p->stride == 16) persistent_kernel<16><<<bb, BIG_T, BIG_SMEM, s>>>(B);
-        else persistent_kernel<32><<<bb, BIG_T, BIG_SMEM, s>>>(B);
+        else if (p->stride == 32) persistent_kernel<32><<<bb, BIG_T, BIG_SMEM, s>>>(B);
+        else if (p->stride == 64) persistent_kernel<64><<<bb, BIG_T, BIG_SMEM, s>>>(B);
+        else persistent_kernel<128><<<bb, BIG_T, BIG_SMEM, s>>>(B);
         ctx->launches++;
     }
     if (side) {

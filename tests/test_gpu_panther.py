@@ -221,12 +221,13 @@ def test_paths_and_index_bit_exact_small_workload(pk, small, mode):
     assert np.array_equal(out["pid"], pid)
 
 
-@pytest.mark.parametrize("T", [1, 2, 7, 9, 15, 20, 31])
-def test_paths_other_lengths(pk, T):
+@pytest.mark.parametrize("T", [1, 2, 7, 9, 15, 20, 31, 32, 47, 63, 64, 99, 127])
+@pytest.mark.parametrize("mode", ["alias", "prefix"])
+def test_paths_other_lengths(pk, T, mode):
     g = synth.chung_lu(3000, 6, 2.2, ("uniform", 1, 1000), seed=9)
     R = 3001     # ragged: not a multiple of any tile
-    out = _run(pk, g, 12345, R, T, pk.MODE_ALIAS)
-    ref = oracle.sample_paths(g, 12345, R, T, oracle.ALIAS)
+    out = _run(pk, g, 12345, R, T, pk.MODE_ALIAS if mode == "alias" else pk.MODE_PREFIX)
+    ref = oracle.sample_paths(g, 12345, R, T, oracle.ALIAS if mode == "alias" else oracle.PREFIX)
     assert np.array_equal(out["paths"], ref)
     off, pid = oracle.build_index(g.n, ref)
     assert np.array_equal(out["off"], off) and np.array_equal(out["pid"], pid)

@@ -109,10 +109,12 @@ def test_default_routing_reports_tiers(pk):
     assert np.array_equal(ids[pick], rid) and np.array_equal(cnt[pick], rcnt)
 
 
-@pytest.mark.parametrize("T", [8, 10, 15, 20, 31])
+@pytest.mark.parametrize("T", [8, 10, 15, 20, 31, 32, 63, 64, 100, 127])
 def test_long_paths_topk_theta_knn(pk, small, T):
+    # rows of 16, 32, 64 and 128 entries; from T = 32 on the counting kernels
+    # walk one path per warp (lanes hold entries l, l+32, ...)
     g = small[0]
-    R, D = 40_000, 50
+    R, D = (40_000 if T <= 31 else 12_000), 50
     ref = oracle.sample_paths(g, 2, R, T, oracle.ALIAS, threads=THREADS)
     o = oracle.Oracle(g.n, ref)
     q = np.arange(g.n, dtype=np.int32)
@@ -122,6 +124,7 @@ def test_long_paths_topk_theta_knn(pk, small, T):
         P.sample_paths(2, R, T, pk.MODE_ALIAS)
         assert np.array_equal(P.paths_tensor().cpu().numpy(), ref)
         P.build_index()
+        off_t, pid_t = (t.cpu().numpy() for t in P.index_tensors())
         qt = torch.as_tensor(q, device="cuda:0")
         got = {}
         for k in (10, 64):
@@ -133,6 +136,7 @@ def test_long_paths_topk_theta_knn(pk, small, T):
         nids, nd2 = P.knn(torch.as_tensor(kq, device="cuda:0"), 10)
         P.sync()
         nids, nd2 = nids.cpu().numpy(), nd2.cpu().numpy().view(np.uint64)
+    assert np.array_equal(off_t, o.off) and np.array_equal(pid_t, o.pid[: pid_t.size])
     for k, (ids, cnt, st) in got.items():
         rid, rcnt = o.topk_many(q, k, threads=THREADS)
         assert np.array_equal(ids, rid), (T, k)
@@ -144,3 +148,55 @@ def test_long_paths_topk_theta_knn(pk, small, T):
     for i, v in enumerate(kq):
         a, b = oracle.knn(rth, int(v), 10)
         assert np.array_equal(nids[i], a) and np.array_equal(nd2[i], b), (T, v)
+
+
+@pytest.mark.parametrize("T,route", [(64, 1), (100, 2), (127, 1), (40, 0)])
+def test_long_paths_hub_tiers_and_plain(pk, T, route):
+    # the 20,000-vertex hub graph with long paths: every query whose bound
+    # exceeds 256 candidates is a hub query, counted through the buckets
+    # (route 1) or device tables (route 2) with the one-path-per-warp
+    # insertion; route 0 keeps the default tiers. The plain form (one launch
+    # per query, device table above the CTA bound) answers the same rows.
+    g = synth.chung_lu(20_000, 12, 2.05, ("uniform", 1, 5), seed=2)
+    R = 6_000
+    ref = oracle.sample_paths(g, 5, R, T, oracle.ALIAS, threads=THREADS)
+    o = oracle.Oracle(g.n, ref)
+    sizes = np.diff(o.off)
+    q = np.unique(np.concatenate([np.argsort(-sizes)[:40], np.arange(0, g.n, 157)])).astype(np.int32)
+    for k in (10, 40):
+        ids, cnt, st = _topk_routed(pk, g, R, T, 5, q, k, 256 if route else 0, route)
+        rid, rcnt = o.topk_many(q, k, threads=THREADS)
+        assert np.array_equal(ids, rid) and np.array_equal(cnt, rcnt), (T, route, k)
+        if route:
+            assert st[5] > 0 and (st[6] if route == 1 else st[7]) > 0
+    with pk.Panther(0) as P:
+        P.build_graph(g.row_ptr, g.col, g.w, pk.MODE_ALIAS)
+        P.sample_paths(5, R, T, pk.MODE_ALIAS)
+        P.build_index()
+        ids, cnt = P.topk(torch.as_tensor(q[:60], device="cuda:0"), 10, plain=True)
+        P.sync()
+    rid, rcnt = o.topk_many(q[:60], 10, threads=THREADS)
+    assert np.array_equal(ids.cpu().numpy(), rid) and np.array_equal(cnt.cpu().numpy().astype(np.uint32), rcnt)
+
+
+def test_long_path_revisits_and_limits(pk):
+    # a 6-vertex graph walked for 127 steps: every row repeats its vertices
+    # many times (each must count once); T = 128 is refused
+    g = synth.graph_from_edges(6, [(0, 1), (1, 2), (2, 0), (3, 4)], [1, 2, 3, 4])
+    R, T = 3_000, 127
+    ref = oracle.sample_paths(g, 8, R, T, oracle.ALIAS)
+    o = oracle.Oracle(g.n, ref)
+    q = np.arange(6, dtype=np.int32)
+    with pk.Panther(0) as P:
+        P.build_graph(g.row_ptr, g.col, g.w, pk.MODE_ALIAS)
+        P.sample_paths(8, R, T, pk.MODE_ALIAS)
+        assert np.array_equal(P.paths_tensor().cpu().numpy(), ref)
+        P.build_index()
+        off_t, pid_t = (t.cpu().numpy() for t in P.index_tensors())
+        ids, cnt = P.topk(torch.as_tensor(q, device="cuda:0"), 5)
+        P.sync()
+        with pytest.raises(pk.PantherError):
+            P.sample_paths(8, 10, 128, pk.MODE_ALIAS)
+    assert np.array_equal(off_t, o.off) and np.array_equal(pid_t, o.pid[: pid_t.size])
+    rid, rcnt = o.topk_many(q, 5)
+    assert np.array_equal(ids.cpu().numpy(), rid) and np.array_equal(cnt.cpu().numpy().astype(np.uint32), rcnt)

@@ -346,6 +346,11 @@ def run_ours(args, ws, rank, local):
         out["e2e"] = e2e(pk, torch, P, g, R, T, k, q_host, args, ws)
     P.close()
 
+    # the paper's own operating point on this graph: eps = sqrt(1/|E|)
+    if rank == 0 and not args.no_extras and args.workload == "scale":
+        out["paper_scale_R"] = paper_scale_block(pk, torch, local, d_rp, d_col, d_w, g, T, k, queries, nq)
+    del d_rp, d_col, d_w
+
     # Panther++ k-NN on its own 10M-vertex workload
     if rank == 0 and not args.no_extras and args.workload == "scale":
         out["knn"] = knn_block(pk, torch, local, args)
@@ -361,6 +366,50 @@ def run_ours(args, ws, rank, local):
                 ok &= bool(np.array_equal(ids, rid) and np.array_equal(cnt, rcnt))
             out["serving"]["topk_requests_checked_vs_oracle"] = len(topk_checks)
             out["serving"]["topk_identical_to_oracle"] = ok
+    return out
+
+
+def paper_scale_block(pk, torch, local, d_rp, d_col, d_w, g, T, k, queries, nq, steps=2, warmup=1):
+    """The same step at the paper's sample size for this graph: eps =
+    sqrt(1/|E|), delta = 0.1, c = 0.5 (its Implementation Notes), i.e.
+    R = ceil(0.5 |E| (log2 C(T,2) + 1 + ln 10)) paths: about 13 times the
+    workload's R and about 7.9e9 (vertex, path) pairs in the index."""
+    E = g.m // 2
+    R = pk.panther_sample_size(math.sqrt(1.0 / E), 0.1, 0.5, T)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    out = {"R": R, "eps": f"sqrt(1/{E})", "delta": 0.1, "c": 0.5}
+    try:
+        with pk.Panther(local) as P:
+            rec = []
+            for i in range(warmup + steps):
+                e = [ev() for _ in range(5)]
+                s = P.stream
+                e[0].record(s)
+                P.build_graph(d_rp, d_col, d_w, pk.MODE_ALIAS)
+                e[1].record(s)
+                P.sample_paths(1, R, T, pk.MODE_ALIAS)
+                e[2].record(s)
+                P.build_index()
+                e[3].record(s)
+                P.topk(queries, k)
+                e[4].record(s)
+                P.sync()
+                if i >= warmup:
+                    rec.append(e)
+            torch.cuda.synchronize()
+            _, _, _, nnz = pk.panther_index_view(P.h.index)
+            st = pk.panther_topk_stats(P.h.ctx)
+    except pk.PantherError as ex:
+        out["error"] = str(ex)
+        return out
+    names = ["tables", "sample", "index", "topk"]
+    ms = {nm: statistics.median(r[i].elapsed_time(r[i + 1]) for r in rec) for i, nm in enumerate(names)}
+    tot = statistics.median(r[0].elapsed_time(r[4]) for r in rec)
+    out.update({"index_pairs": int(nnz), "ms_per_step": round(tot, 1), "queries_per_s": round(nq / (tot * 1e-3), 1),
+                "paths_sampled_per_s": round(R / (ms["sample"] * 1e-3), 1),
+                "stages_ms": {nm: round(v, 2) for nm, v in ms.items()},
+                "topk_tiers": dict(zip(["queries", "lane", "group", "warp", "cta", "hub", "hub_via_buckets",
+                                        "hub_via_tables", "bucket_overflows", "second_passes"], st))})
     return out
 
 

@@ -107,6 +107,11 @@ void panther_destroy(panther_ctx* ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->hub_arena) cudaFreeAsync(ctx->hub_arena, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
+    // the device pool keeps freed blocks for reuse between calls; what no one
+    // uses any more goes back to the device when a context ends
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+    cudaGetLastError();
     for (int i = 0; i < 2; ++i) {
         if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);
         if (ctx->join[i]) cudaEventDestroy(ctx->join[i]);

@@ -239,6 +239,130 @@ __device__ __forceinline__ void write_list(const WarpTopK& t, const OutRef& o, i
     }
 }
 
+// ------------------------------------------- 128-entry lists (k > 64) ---
+// The same descending list with four registers per lane (ranks l, 32+l,
+// 64+l, 96+l), for 64 < k <= 128. Used only by the device-table selection.
+constexpr int KMAX4 = 128;
+
+struct WarpTopK4 {
+    uint64_t r[4] = {0, 0, 0, 0};
+    __device__ __forceinline__ uint64_t kth(int k) const {
+        const int q = (k - 1) >> 5, l = (k - 1) & 31;
+        const uint64_t x = q == 0 ? r[0] : (q == 1 ? r[1] : (q == 2 ? r[2] : r[3]));
+        return __shfl_sync(0xffffffffu, x, l);
+    }
+    __device__ __forceinline__ void insert(uint64_t x) {
+        const unsigned lane = threadIdx.x & 31;
+        int pos = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) pos += __popc(__ballot_sync(0xffffffffu, r[j] > x));
+        uint64_t up[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) up[j] = __shfl_up_sync(0xffffffffu, r[j], 1);
+#pragma unroll
+        for (int j = 3; j >= 1; --j) {
+            const uint64_t carry = __shfl_sync(0xffffffffu, r[j - 1], 31);
+            if (lane == 0) up[j] = carry;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int rank = 32 * j + (int)lane;
+            r[j] = rank < pos ? r[j] : (rank == pos ? x : up[j]);
+        }
+    }
+    // merge another descending 128-list in: the top 128 of the union (keys are
+    // distinct or 0): reverse the other list, take elementwise maxima (a
+    // bitonic sequence), then half-cleaners at distances 64, 32, 16 .. 1
+    __device__ __forceinline__ void merge(const uint64_t (&x)[4]) {
+        const unsigned lane = threadIdx.x & 31;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) r[j] = umax64(r[j], __shfl_sync(0xffffffffu, x[3 - j], 31 - lane));
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const uint64_t hi = umax64(r[j], r[j + 2]), lo = umin64(r[j], r[j + 2]);
+            r[j] = hi;
+            r[j + 2] = lo;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j += 2) {
+            const uint64_t hi = umax64(r[j], r[j + 1]), lo = umin64(r[j], r[j + 1]);
+            r[j] = hi;
+            r[j + 1] = lo;
+        }
+#pragma unroll
+        for (int d = 16; d; d >>= 1) {
+            const bool upper = lane & d;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint64_t p = __shfl_xor_sync(0xffffffffu, r[j], d);
+                r[j] = upper ? umin64(r[j], p) : umax64(r[j], p);
+            }
+        }
+    }
+    // offer one candidate per lane (0 = none)
+    __device__ __forceinline__ void offer(uint64_t c, int k) {
+        uint64_t thr = kth(k);
+        unsigned m = __ballot_sync(0xffffffffu, c > thr);
+        if (__popc(m) > 2) {
+            const unsigned lane = threadIdx.x & 31;
+#pragma unroll
+            for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+                for (int j = kk >> 1; j > 0; j >>= 1) {
+                    const uint64_t pc = __shfl_xor_sync(0xffffffffu, c, j);
+                    const bool desc = (lane & kk) == 0 || kk == 32;
+                    const bool lower = (lane & j) == 0;
+                    c = (lower == desc) ? umax64(c, pc) : umin64(c, pc);
+                }
+            }
+            const uint64_t x[4] = {c, 0, 0, 0};
+            merge(x);
+            return;
+        }
+        while (m) {
+            const int src = __ffs(m) - 1;
+            insert(__shfl_sync(0xffffffffu, c, src));
+            m &= m - 1;
+            thr = kth(k);
+            m &= __ballot_sync(0xffffffffu, c > thr);
+        }
+    }
+};
+
+// merge the 128-lists of all warps of the CTA into warp 0 (log-depth tree);
+// `lists` holds 128 entries per warp; every thread of the CTA must call it
+__device__ __forceinline__ void cta_merge4(WarpTopK4& t, unsigned long long* lists) {
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
+    const unsigned lane = threadIdx.x & 31;
+    for (int s = 1; s < nw; s <<= 1) {
+        if ((w & (2 * s - 1)) == s)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) lists[w * KMAX4 + 32 * j + lane] = t.r[j];
+        __syncthreads();
+        if ((w & (2 * s - 1)) == 0 && w + s < nw) {
+            uint64_t x[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] = lists[(w + s) * KMAX4 + 32 * j + lane];
+            t.merge(x);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void write_list4(const WarpTopK4& t, const OutRef& o, int64_t qi) {
+    const unsigned lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int rk = (int)lane + 32 * j;
+        const uint64_t sc = t.r[j];
+        if (rk < o.k) {
+            const int64_t at = qi * o.k + rk;
+            if (o.ids) o.ids[at] = sc ? (int32_t)(0xffffffffu - (uint32_t)sc) : -1;
+            o.cnt[at] = (uint32_t)(sc >> 32);
+        }
+    }
+}
+
 // ------------------------------------------------------ path insertion ---
 struct PathsRef {
     const int32_t* rows;
@@ -648,6 +772,7 @@ constexpr int CL_PER = 16;
 
 __global__ void __launch_bounds__(256) classify_kernel(const int32_t* __restrict__ queries, int64_t q, PathsRef P,
                                                        int64_t ccap, int64_t ccap_big, bool lane_ok, int group_max,
+                                                       bool all_hub,
                                                        Tiers tiers, OutRef o, uint32_t* status) {
     __shared__ unsigned tot[8];
     __shared__ int base[8];
@@ -669,7 +794,8 @@ __global__ void __launch_bounds__(256) classify_kernel(const int32_t* __restrict
                 int64_t cap = np * (P.L - 1);
                 if (cap > P.n - 1) cap = P.n - 1;
                 if (cap > 0) {
-                    if (lane_ok && np <= LANE_NP) t = 3;
+                    if (all_hub) t = 2;          // k > 64: every query in a device table
+                    else if (lane_ok && np <= LANE_NP) t = 3;
                     else if (np <= 8 && np <= group_max) t = 4;
                     else if (np <= 16 && np <= group_max) t = 5;
                     else if (np <= 32 && np <= group_max) t = 6;
@@ -1197,6 +1323,51 @@ __global__ void g_merge_kernel(GPlan G, const unsigned long long* __restrict__ p
     write_list(t, o, G.qidx[g]);
 }
 
+// 64 < k <= 128: partial 128-lists of the table chunks, then one merge per query
+__global__ void __launch_bounds__(512) g_select4_kernel(GPlan G, unsigned long long* arena, int k,
+                                                        unsigned long long* partial) {
+    __shared__ unsigned long long lists[16 * KMAX4];
+    const int64_t item = blockIdx.x;
+    const int g = find_owner(G.sel_off, G.ng, item);
+    const int64_t c0 = (item - G.sel_off[g]) * G_SLOTS;
+    const int64_t ns = G.tab_n[g];
+    const uint32_t len = (uint32_t)(c0 + G_SLOTS < ns ? G_SLOTS : ns - c0);
+    unsigned long long* tab = arena + G.tab_off[g] + c0;
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
+    const unsigned lane = threadIdx.x & 31;
+    WarpTopK4 t;
+    for (uint32_t base = (uint32_t)w * 32; base < len; base += (uint32_t)nw * 32) {   // warp-uniform
+        const uint32_t s = base + lane;
+        uint64_t sc = 0;
+        if (s < len) {
+            sc = slot_score(tab[s]);
+            if (sc) tab[s] = EMPTY;
+        }
+        t.offer(sc, k);
+    }
+    cta_merge4(t, lists);
+    if (w == 0)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) partial[item * KMAX4 + 32 * j + lane] = t.r[j];
+}
+
+__global__ void __launch_bounds__(256) g_merge4_kernel(GPlan G, const unsigned long long* __restrict__ partial,
+                                                       OutRef o) {
+    __shared__ unsigned long long lists[8 * KMAX4];
+    const int g = blockIdx.x;
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned lane = threadIdx.x & 31;
+    WarpTopK4 t;
+    for (int64_t it = G.sel_off[g] + w; it < G.sel_off[g + 1]; it += nw) {
+        uint64_t x[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[j] = partial[it * KMAX4 + 32 * j + lane];
+        t.merge(x);
+    }
+    cta_merge4(t, lists);
+    if (w == 0) write_list4(t, o, G.qidx[g]);
+}
+
 // ---------------------------------------------- bucketed global tier ---
 // A hub query is counted in two passes without device-wide atomics on
 // counts: (1) a CTA counts one chunk of the hub's paths in shared memory and
@@ -1565,8 +1736,9 @@ static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int3
         char* dplan = nullptr;
         unsigned long long* partial = nullptr;
         int32_t* dredo = nullptr;
+        const int kw = k > KMAX ? KMAX4 : KMAX;     // width of the partial lists
         if ((st = upload(ctx, hp, &dplan)) ||
-            (st = dev_alloc(ctx, (void**)&partial, sizeof(unsigned long long) * KMAX * soff.back())) ||
+            (st = dev_alloc(ctx, (void**)&partial, sizeof(unsigned long long) * kw * soff.back())) ||
             (st = dev_alloc(ctx, (void**)&dredo, sizeof(int32_t) * rng))) {
             dev_free(ctx, dplan);
             dev_free(ctx, partial);
@@ -1580,8 +1752,13 @@ static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int3
         else if (stride == 32) g_count_kernel<32><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
         else if (stride == 64) g_count_kernel<64><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
         else g_count_kernel<128><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
-        g_select_kernel<<<(unsigned)soff.back(), 512, 0, s>>>(G, arena, k, partial);
-        g_merge_cta_kernel<<<rng, 256, 0, s>>>(G, partial, o);
+        if (k > KMAX) {
+            g_select4_kernel<<<(unsigned)soff.back(), 512, 0, s>>>(G, arena, k, partial);
+            g_merge4_kernel<<<rng, 256, 0, s>>>(G, partial, o);
+        } else {
+            g_select_kernel<<<(unsigned)soff.back(), 512, 0, s>>>(G, arena, k, partial);
+            g_merge_cta_kernel<<<rng, 256, 0, s>>>(G, partial, o);
+        }
         hub_check_kernel<<<(unsigned)ceil_div(rng, 256), 256, 0, s>>>(G.qidx, G.thr, rng, o, dredo);
         ctx->launches += 4;
         PCK(ctx, cudaGetLastError());
@@ -1633,6 +1810,17 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
     for (int i = 0; i < 10; ++i) ctx->topk_stats[i] = 0;
     ctx->topk_stats[0] = q;
 
+    if (plain && k > KMAX) {
+        // one query at a time through the device-table path (the 128-entry lists)
+        for (int64_t i = 0; i < q; ++i) {
+            const int32_t* qi = queries ? queries + i : nullptr;
+            if (!qi) return set_err(ctx, PANTHER_EINVAL, "the plain form with k > 64 needs a query array");
+            panther_status r = topk_run(ctx, ix, p, qi, 1, k, ids ? ids + i * k : nullptr, cnt + i * k, false);
+            if (r) return r;
+        }
+        ctx->topk_stats[0] = q;
+        return PANTHER_OK;
+    }
     if (plain) {
         for (int i = 0; i < 10; ++i) ctx->topk_stats[i] = 0;
         ctx->topk_stats[0] = q;
@@ -1669,14 +1857,15 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
     }
     Tiers tiers{{lists, lists + q, lists + 2 * q, lists + 3 * q, lists + 4 * q, lists + 5 * q, lists + 6 * q, lists + 7 * q},
                 counts};
+    const bool all_hub = k > KMAX;                      // 64 < k <= 128: device tables only
     // largest |P_v| the group tiers take: ids must fit below 2^group_ub(G)
-    const int group_max = p->stride != 8 ? 0
+    const int group_max = (p->stride != 8 || all_hub) ? 0
                           : ix->n <= (int64_t(1) << group_ub(32)) ? 32
                           : ix->n <= (int64_t(1) << group_ub(16)) ? 16 : 0;
     const bool lane_ok = p->stride == 8 && k <= LANE_K;
     PCK(ctx, cudaMemsetAsync(counts, 0, sizeof(int) * 16, s));
     classify_kernel<<<(unsigned)ceil_div(q, 256 * CL_PER), 256, 0, s>>>(queries, q, P, ccap, ccap_big, lane_ok,
-                                                                         group_max, tiers, o, ctx->d_status);
+                                                                         group_max, all_hub, tiers, o, ctx->d_status);
     ctx->launches++;
     // the lane and group tiers are independent of the persistent passes: they
     // run on the side streams (joined back into `s` below)
@@ -1714,6 +1903,7 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
     const int narrow_cb = (cb <= 16 && ix->n <= (int64_t(1) << (32 - cb))) ? cb : 0;   // ids < 2^(32-cb)
     PersistArgs A{P, queries, tiers, o, sh.cta_slots, ctx->d_status, narrow_cb};
     unsigned blocks = (unsigned)(ctx->num_sms * sh.blocks_per_sm);
+    if (!all_hub) {
     if (p->stride == 8) persistent_kernel<8><<<blocks, sh.threads, smem, s>>>(A);
     else if (p->stride == 16) persistent_kernel<16><<<blocks, sh.threads, smem, s>>>(A);
     else if (p->stride == 32) persistent_kernel<32><<<blocks, sh.threads, smem, s>>>(A);
@@ -1732,6 +1922,7 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
         else persistent_kernel<128><<<bb, BIG_T, BIG_SMEM, s>>>(B);
         ctx->launches++;
     }
+    }   // !all_hub
     if (side) {
         PCK(ctx, cudaStreamWaitEvent(s, ctx->join[0], 0));
         PCK(ctx, cudaStreamWaitEvent(s, ctx->join[1], 0));
@@ -1774,7 +1965,7 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
         std::vector<HubQuery> hubs(ng);
         for (int i = 0; i < ng; ++i) {
             int64_t t = (int64_t)((double)npv[i] * HUB_PRUNE / std::max(k, 10));
-            hubs[i] = HubQuery{gq[i], npv[i], t < 2 ? 0u : path_code(t)};
+            hubs[i] = HubQuery{gq[i], npv[i], (t < 2 || all_hub) ? 0u : path_code(t)};
         }
         // queries with a small filtered candidate bound count straight into a
         // device table (it stays in L2); the others go through the buckets
@@ -1785,6 +1976,7 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
                 bool table = h.thr > 0 && hub_bound(P, h, above) <= HUB_TABLE_BOUND;
                 if (ctx->dbg_hub_route == 1) table = false;
                 if (ctx->dbg_hub_route == 2) table = true;
+                if (all_hub) table = true;                 // the buckets keep 64-entry lists
                 (table ? tq : bq).push_back(h);
             }
             panther_status r = PANTHER_OK;
@@ -1816,7 +2008,7 @@ extern "C" panther_status panther_topk(panther_ctx* ctx, const panther_index* ix
                                        uint32_t* out_counts, int flags) {
     if (!ctx || !ix || !p) return PANTHER_EINVAL;
     if (q < 0 || q > 0x7fffffffLL) return set_err(ctx, PANTHER_EINVAL, "q must be in [0, 2^31)");
-    if (k < 1 || k > KMAX) return set_err(ctx, PANTHER_EINVAL, "k must be in [1, 64]");
+    if (k < 1 || k > KMAX4) return set_err(ctx, PANTHER_EINVAL, "k must be in [1, 128]");
     if (ix->n != p->n || ix->R != p->R)
         return set_err(ctx, PANTHER_EINVAL, "index and paths do not belong together");
     if (q == 0) return PANTHER_OK;
@@ -1863,7 +2055,7 @@ panther_status topk_counts_all(panther_ctx* ctx, const panther_index* ix, const 
 extern "C" panther_status panther_tune_topk(panther_ctx* ctx, const panther_index* ix, const panther_paths* p,
                                             const int32_t* queries, int64_t q, int k, int32_t* out_ids,
                                             uint32_t* out_counts, int* chosen) {
-    if (!ctx || !ix || !p || !queries || !out_ids || !out_counts || q < 1 || k < 1 || k > KMAX)
+    if (!ctx || !ix || !p || !queries || !out_ids || !out_counts || q < 1 || k < 1 || k > KMAX4)
         return set_err(ctx, PANTHER_EINVAL, "bad tuner arguments");
     if (ix->n != p->n || ix->R != p->R) return set_err(ctx, PANTHER_EINVAL, "index and paths do not belong together");
     cudaSetDevice(ctx->device);

@@ -376,7 +376,7 @@ def test_topk_edge_cases(pk):
         with pytest.raises(pk.PantherError):
             P.sync()                                            # out-of-range query reported
         with pytest.raises(pk.PantherError):
-            P.topk(torch.zeros(1, dtype=torch.int32, device="cuda:0"), 65)
+            P.topk(torch.zeros(1, dtype=torch.int32, device="cuda:0"), 129)
 
 
 def test_topk_host_io(pk, small):

@@ -110,3 +110,39 @@ def test_knn_workload_theta_all_and_sampled_knn(pk):
     rid, rd = oracle.knn_many(rth, q, k, threads=THREADS)
     assert np.array_equal(ids, rid), "k-NN ids differ"
     assert np.array_equal(d2, rd), "k-NN distances differ"
+
+
+def test_index_beyond_2pow31_pairs(pk):
+    """More (vertex, path) pairs than an int32 position can address: 450M
+    paths of T = 5 on a 2,000-vertex graph give about 2.5e9 pairs (the regime
+    of the paper's own sample size, R = c/eps^2 (...) with eps = sqrt(1/|E|),
+    on large graphs). Every path, the whole index (int64 offsets past 2^31)
+    and the top-10 of 40 vertices equal the oracle's."""
+    g = synth.workload_graph("small")
+    R, T, k = 450_000_000, 5, 10
+    q = np.arange(0, g.n, 50, dtype=np.int32)
+    with pk.Panther(0) as P:
+        P.build_graph(g.row_ptr, g.col, g.w, pk.MODE_ALIAS)
+        P.sample_paths(21, R, T, pk.MODE_ALIAS)
+        P.build_index()
+        ids, cnt = P.topk(torch.as_tensor(q, device="cuda:0"), k)
+        P.sync()
+        ids, cnt = ids.cpu().numpy(), cnt.cpu().numpy().astype(np.uint32)
+        _, _, _, nnz = pk.panther_index_view(P.h.index)
+        assert nnz > 2**31
+        gpu_paths = P.paths_tensor().cpu().numpy()
+        ref = oracle.sample_paths(g, 21, R, T, oracle.ALIAS, threads=THREADS)
+        assert np.array_equal(gpu_paths, ref), "paths differ from the oracle"
+        del gpu_paths
+        off_t, pid_t = P.index_tensors()
+        gpu_off = off_t.cpu().numpy()
+        gpu_pid = pid_t.cpu().numpy()
+        del off_t, pid_t
+    off, pid = oracle.build_index(g.n, ref, threads=THREADS)
+    assert off[-1] == nnz
+    assert np.array_equal(gpu_off, off), "index offsets differ"
+    assert np.array_equal(gpu_pid, pid), "index path ids differ"
+    del gpu_pid
+    o = oracle.Oracle(g.n, ref, off, pid)
+    rid, rcnt = o.topk_many(q, k, threads=THREADS)
+    assert np.array_equal(ids, rid) and np.array_equal(cnt, rcnt)

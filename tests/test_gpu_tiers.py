@@ -200,3 +200,32 @@ def test_long_path_revisits_and_limits(pk):
     assert np.array_equal(off_t, o.off) and np.array_equal(pid_t, o.pid[: pid_t.size])
     rid, rcnt = o.topk_many(q, 5)
     assert np.array_equal(ids.cpu().numpy(), rid) and np.array_equal(cnt.cpu().numpy().astype(np.uint32), rcnt)
+
+
+@pytest.mark.parametrize("k", [65, 100, 128])
+def test_topk_k_above_64(pk, small, k):
+    # 64 < k <= 128: every query counted in a device table, 128-entry lists;
+    # all 2,000 vertices (many with fewer than k candidates: padding), the
+    # plain form on a subset, and a long-path case
+    g, ref, o = small
+    q = np.arange(g.n, dtype=np.int32)
+    ids, cnt, st = _topk_routed(pk, g, 200_000, 5, 1, q, k, 0, 0)
+    rid, rcnt = o.topk_many(q, k, threads=THREADS)
+    assert np.array_equal(ids, rid) and np.array_equal(cnt, rcnt)
+    assert st[7] > 1000 and st[1] == st[2] == st[3] == st[4] == 0
+    with pk.Panther(0) as P:
+        P.build_graph(g.row_ptr, g.col, g.w, pk.MODE_ALIAS)
+        P.sample_paths(1, 200_000, 5, pk.MODE_ALIAS)
+        P.build_index()
+        sub = torch.as_tensor(q[::97], device="cuda:0")
+        pids, pcnt = P.topk(sub, k, plain=True)
+        P.sync()
+    assert np.array_equal(pids.cpu().numpy(), rid[::97])
+    assert np.array_equal(pcnt.cpu().numpy().astype(np.uint32), rcnt[::97])
+    T, R = 100, 6_000
+    ref2 = oracle.sample_paths(g, 3, R, T, oracle.ALIAS, threads=THREADS)
+    o2 = oracle.Oracle(g.n, ref2)
+    q2 = np.arange(0, g.n, 5, dtype=np.int32)
+    ids2, cnt2, _ = _topk_routed(pk, g, R, T, 3, q2, k, 0, 0)
+    rid2, rcnt2 = o2.topk_many(q2, k, threads=THREADS)
+    assert np.array_equal(ids2, rid2) and np.array_equal(cnt2, rcnt2)

@@ -78,22 +78,22 @@ def _src_hash(*files):
 # unchanged (SHA-256 of the files), else reported as null. The capture and its
 # command are in profiles/.
 NCU_TRAFFIC = {
-    "tables": {"bytes_5M": 4334776832, "sources": {
-        "paper_1504_02577_gb300/csrc/graph.cu": "cb2f60dba3f39f195ad950a0c67bd3a661d82192ddfd509d08ce46f356187992",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "dca6f273b85f41c4c763fd5a411da0ded671711cdfca0dd8552cf5610bef03dd",
+    "tables": {"bytes_5M": 4367967232, "sources": {
+        "paper_1504_02577_gb300/csrc/graph.cu": "2e1c84b66c7ae7bb7953cb51285365d9aa6479fe7d4feb4baf6db03417cee5a6",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "b1172d07882c5268071533ae62a526e5d6c91192d0bb6e0b227b46cb30599cf0",
     }},
-    "sample": {"bytes_5M": 8120454400, "sources": {
-        "paper_1504_02577_gb300/csrc/sample.cu": "bb26fa79f1b96c3cd0b604f4973e3a516a52c41b1659bf03f4eecd0249193d27",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "dca6f273b85f41c4c763fd5a411da0ded671711cdfca0dd8552cf5610bef03dd",
+    "sample": {"bytes_5M": 8123576832, "sources": {
+        "paper_1504_02577_gb300/csrc/sample.cu": "3ae257be8d6b2d9726f406e2f7e6bc67a92c8ee993f6cb3d6a67728924becbf3",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "b1172d07882c5268071533ae62a526e5d6c91192d0bb6e0b227b46cb30599cf0",
     }},
-    "index": {"bytes_5M": 3670223104, "sources": {
-        "paper_1504_02577_gb300/csrc/index.cu": "59a2f95b2a6ee446be3490e6950823c9994516b3420c1fdb8387795ddbafab74",
-        "paper_1504_02577_gb300/csrc/capi.cu": "02fa30a2121c3c8dca2f5c7d29513b8191b1ec93498ab936e54f7efe39b61e81",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "dca6f273b85f41c4c763fd5a411da0ded671711cdfca0dd8552cf5610bef03dd",
+    "index": {"bytes_5M": 3669556736, "sources": {
+        "paper_1504_02577_gb300/csrc/index.cu": "f7bb8dd1ec297daaac7c81820b235bbb38303bbfc52351640efe5010c595c8d5",
+        "paper_1504_02577_gb300/csrc/capi.cu": "1a53c25df292c600c1314fc954bbc3d073e4163095578b9d03d33a3337936f32",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "b1172d07882c5268071533ae62a526e5d6c91192d0bb6e0b227b46cb30599cf0",
     }},
-    "topk": {"bytes_5M": 8264598528, "sources": {
-        "paper_1504_02577_gb300/csrc/topk.cu": "c8b5a629bc94613beb54a206876d142dad31cf98143d01ca55b5b408d143e45c",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "dca6f273b85f41c4c763fd5a411da0ded671711cdfca0dd8552cf5610bef03dd",
+    "topk": {"bytes_5M": 8260542208, "sources": {
+        "paper_1504_02577_gb300/csrc/topk.cu": "0c9dfda377cdc4813ec9bfa0519d76d15dcc584d6c55d7a208f160b1a6b751fa",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "b1172d07882c5268071533ae62a526e5d6c91192d0bb6e0b227b46cb30599cf0",
     }},
 }
 

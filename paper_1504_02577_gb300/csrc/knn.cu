@@ -69,6 +69,13 @@ __device__ __forceinline__ uint32_t round8(uint32_t x) {
     return q << sh;                  // may carry to 2^(p+1): still 8 significant bits
 }
 
+// minimum of three floats in one instruction (the values are finite here)
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 __device__ __forceinline__ uint16_t bf16_bits_of(float f) {   // f exactly representable
     return (uint16_t)(__float_as_uint(f) >> 16);
 }
@@ -344,15 +351,15 @@ __device__ __forceinline__ Row select_group(Row r, const RowConst& c, const floa
     if (fast) {
         // exact tiles hold exact rows in ascending id order, after every row
         // already in the list, so a candidate tied with the k-th key never
-        // wins its tie: only y < thr can enter
-        float t16[16];
+        // wins its tie: only y < thr can enter. The minimum of the 32 values
+        // decides whether any can: three-input minima, 16 instructions.
+        float t11[11];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) t16[j] = fminf(y[j], y[j + 16]);
-#pragma unroll
-        for (int w = 8; w; w >>= 1)
-#pragma unroll
-            for (int j = 0; j < w; ++j) t16[j] = fminf(t16[j], t16[j + w]);
-        const float m = t16[0];
+        for (int j = 0; j < 10; ++j) t11[j] = fmin3(y[3 * j], y[3 * j + 1], y[3 * j + 2]);
+        t11[10] = fminf(y[30], y[31]);
+        const float m = fminf(fmin3(fmin3(t11[0], t11[1], t11[2]), fmin3(t11[3], t11[4], t11[5]),
+                                    fmin3(t11[6], t11[7], t11[8])),
+                              fminf(t11[9], t11[10]));
         if (m < r.thr) {
 #pragma unroll
             for (int j = 0; j < 32; ++j)

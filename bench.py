@@ -904,8 +904,10 @@ def run_knn(args, ws, rank, local):
 def run_sweep(args, ws, rank, local):
     """Throughput against the method's parameters on a 5M-vertex graph of the
     scale workload's shape (the performance side of the paper's T, k and D
-    studies): sampler and index against T, top-k against T and k, Panther++
-    vectors and k-NN against D. Each point: one warm-up and the median of 3."""
+    studies: T up to 100, k up to 100, D up to the BF16 screen's 56):
+    sampler and index against T, top-k against T and k, Panther++ vectors and
+    k-NN against D. Each point: one warm-up and the median of 3 (one timed
+    run for T >= 50 and k > 64)."""
     import torch
     import synth
     import __graft_entry__
@@ -938,22 +940,23 @@ def run_sweep(args, ws, rank, local):
         return statistics.median(ts)
 
     by_T = []
-    for T in (2, 3, 5, 10, 20, 31):
-        ms_s = timed(lambda: P.sample_paths(args.seed, R, T, pk.MODE_ALIAS))
-        ms_i = timed(lambda: P.build_index())
-        ms_k = timed(lambda: P.topk(allq, 10))
+    for T in (2, 3, 5, 10, 20, 31, 50, 100):
+        reps = 3 if T <= 31 else 1
+        ms_s = timed(lambda: P.sample_paths(args.seed, R, T, pk.MODE_ALIAS), reps)
+        ms_i = timed(lambda: P.build_index(), reps)
+        ms_k = timed(lambda: P.topk(allq, 10), reps)
         by_T.append({"T": T, "sample_ms": round(ms_s, 3), "paths_per_s": round(R / ms_s * 1e3, 1),
                      "index_ms": round(ms_i, 3), "topk_ms": round(ms_k, 3),
                      "topk_queries_per_s": round(g.n / ms_k * 1e3, 1)})
     P.sample_paths(args.seed, R, 5, pk.MODE_ALIAS)
     P.build_index()
     by_k = []
-    for k in (5, 10, 20, 50):
-        ms_k = timed(lambda: P.topk(allq, k))
+    for k in (5, 10, 20, 50, 64, 100, 128):
+        ms_k = timed(lambda: P.topk(allq, k), 3 if k <= 64 else 1)
         by_k.append({"k": k, "topk_ms": round(ms_k, 3), "topk_queries_per_s": round(g.n / ms_k * 1e3, 1)})
     by_D = []
     q = torch.randint(0, g.n, (4096,), generator=torch.Generator().manual_seed(3), dtype=torch.int32).to(dev)
-    for D in (10, 25, 50):
+    for D in (10, 25, 50, 56):
         ms_v = timed(lambda: P.vectors(D), reps=1)
         ms_n = timed(lambda: P.knn(q, 10))
         by_D.append({"D": D, "vectors_ms": round(ms_v, 3), "knn_ms_4096q": round(ms_n, 3),

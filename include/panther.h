@@ -233,7 +233,8 @@ PANTHER_API panther_status panther_index_view(const panther_index* ix, const int
  *   results); the PLAIN form then runs that path once per query.
  *   flags: PANTHER_TOPK_BATCHED or PANTHER_TOPK_PLAIN, optionally
  *          | PANTHER_IO_HOST (queries/outputs in host memory; the call then
- *          synchronises)
+ *          synchronises; batches of 4M queries or more run in four chunks
+ *          whose rows are copied to the host while the next chunk computes)
  * Temporary device memory (hub hash tables) is drawn from the context's
  * scratch budget; a batch whose hubs do not fit is processed in several
  * rounds.

@@ -92,6 +92,14 @@ panther_status panther_create(panther_ctx** out, int device, void* cuda_stream) 
         if (ctx->fork) cudaEventDestroy(ctx->fork);
         ctx->fork = nullptr;
     }
+    // a stream for result copies (optional: without it they go on `stream`)
+    if (cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->copy_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->copy) cudaStreamDestroy(ctx->copy);
+        ctx->copy = nullptr;
+        ctx->copy_ev = nullptr;
+    }
     // keep freed stream-ordered memory in the pool between calls
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
@@ -117,6 +125,11 @@ void panther_destroy(panther_ctx* ctx) {
         if (ctx->join[i]) cudaEventDestroy(ctx->join[i]);
     }
     if (ctx->fork) cudaEventDestroy(ctx->fork);
+    if (ctx->copy) {
+        cudaStreamSynchronize(ctx->copy);
+        cudaStreamDestroy(ctx->copy);
+    }
+    if (ctx->copy_ev) cudaEventDestroy(ctx->copy_ev);
     cudaFree(ctx->d_status);
     cudaFreeHost(ctx->h_status);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);

@@ -38,6 +38,9 @@ struct panther_ctx {
     // on `stream`); null when they could not be created
     cudaStream_t side[2] = {nullptr, nullptr};
     cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+    // copies of host-I/O results that overlap the next chunk's kernels
+    cudaStream_t copy = nullptr;
+    cudaEvent_t copy_ev = nullptr;
     // slot arena of the hub device tables, kept between calls: all slots are
     // EMPTY whenever hub_arena_clean (the select pass empties what it reads)
     unsigned long long* hub_arena = nullptr;

@@ -2030,12 +2030,29 @@ extern "C" panther_status panther_topk(panther_ctx* ctx, const panther_index* ix
         dq = buf;
         di = buf + q;
         dc = (uint32_t*)(buf + q + (size_t)q * k);
-        st = topk_run(ctx, ix, p, dq, q, k, di, dc, mode == PANTHER_TOPK_PLAIN);
-        if (!st) {
-            PCK(ctx, cudaMemcpyAsync(out_ids, di, ob, cudaMemcpyDeviceToHost, s));
-            PCK(ctx, cudaMemcpyAsync(out_counts, dc, ob, cudaMemcpyDeviceToHost, s));
+        // Large batches run in chunks; the rows of a finished chunk travel to
+        // the host on the copy stream while the next chunk computes.
+        const int64_t chunk = (q >= (int64_t(1) << 22) && ctx->copy) ? ceil_div(q, 4) : q;
+        cudaStream_t cs = ctx->copy ? ctx->copy : s;
+        int64_t stats[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int64_t c0 = 0; c0 < q && !st; c0 += chunk) {
+            const int64_t qc = std::min(chunk, q - c0);
+            st = topk_run(ctx, ix, p, dq + c0, qc, k, di + c0 * k, dc + c0 * k, mode == PANTHER_TOPK_PLAIN);
+            if (st) break;
+            for (int i = 0; i < 10; ++i) stats[i] += ctx->topk_stats[i];
+            cudaError_t e = cs == s ? cudaSuccess : cudaEventRecord(ctx->copy_ev, s);
+            if (!e && cs != s) e = cudaStreamWaitEvent(cs, ctx->copy_ev, 0);
+            if (!e) e = cudaMemcpyAsync(out_ids + c0 * k, di + c0 * k, sizeof(int32_t) * qc * k,
+                                        cudaMemcpyDeviceToHost, cs);
+            if (!e) e = cudaMemcpyAsync(out_counts + c0 * k, dc + c0 * k, sizeof(uint32_t) * qc * k,
+                                        cudaMemcpyDeviceToHost, cs);
+            if (e) st = cuda_err(ctx, e, "top-k result copy");
         }
+        for (int i = 0; i < 10; ++i) ctx->topk_stats[i] = stats[i];
+        // the copies must finish before the buffer goes back to the pool
+        cudaError_t e = cudaStreamSynchronize(cs);
         dev_free(ctx, buf);
+        if (!st && e) st = cuda_err(ctx, e, "top-k result copy");
         if (!st) PCK(ctx, cudaStreamSynchronize(s));
         return st;
     }

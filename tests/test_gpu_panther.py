@@ -394,6 +394,31 @@ def test_topk_host_io(pk, small):
     assert np.array_equal(ids, rid) and np.array_equal(cnt, rcnt)
 
 
+def test_topk_host_io_large_batch_in_chunks(pk, small):
+    # 4.5M queries (repeats of the 2,000 vertices) with host buffers: the call
+    # answers them in chunks whose rows are copied back while the next chunk
+    # computes; the rows equal the device-memory call's and the oracle's
+    rng = np.random.default_rng(4)
+    q = rng.integers(0, small.n, size=4_500_000).astype(np.int32)
+    k = 10
+    with pk.Panther(0) as P:
+        P.build_graph(small.row_ptr, small.col, small.w)
+        P.sample_paths(1, 20_000, 5)
+        P.build_index()
+        ids = np.empty((q.shape[0], k), np.int32)
+        cnt = np.empty((q.shape[0], k), np.uint32)
+        pk.panther_topk(P.h.ctx, P.h.index, P.h.paths, q, q.shape[0], k, ids, cnt,
+                        pk.TOPK_BATCHED | pk.IO_HOST)
+        st = pk.panther_topk_stats(P.h.ctx)
+        dids, dcnt = P.topk(torch.as_tensor(q, device="cuda:0"), k)
+        P.sync()
+    assert st[0] == q.shape[0]
+    assert np.array_equal(ids, dids.cpu().numpy()) and np.array_equal(cnt, dcnt.cpu().numpy().astype(np.uint32))
+    o = oracle.Oracle(small.n, oracle.sample_paths(small, 1, 20_000, 5, oracle.ALIAS))
+    rid, rcnt = o.topk_many(np.arange(small.n, dtype=np.int32), k)
+    assert np.array_equal(ids, rid[q]) and np.array_equal(cnt, rcnt[q])
+
+
 def test_batched_workload_full_size_sampled(pk):
     """N=1M Chung-Lu (mean degree 20, gamma 2.3, log-uniform weights), R from the
     sample-size bound (eps 0.01, delta 0.1, c 0.5), 16,384 queries (half from the

@@ -193,9 +193,21 @@ PANTHER_API panther_status panther_paths_info(const panther_paths* p, int64_t* n
 /* Build the inverted index P_v = { r : v in p_r } with a device LSD radix
  * sort of (vertex, path id) pairs. A path that visits v several times is
  * listed once. Layout: off int64[n+1], pid int32[nnz]; P_v is
- * pid[off[v] .. off[v+1]) in ascending path id. Synchronises once to size the
- * output. Errors: EINVAL, ENOMEM, ECUDA. */
+ * pid[off[v] .. off[v+1]) in ascending path id.
+ * Memory: one sort over all pairs needs about 16 B per pair (+ 5% for tile
+ * counts) of temporary device memory next to the result (4 B per pair). When
+ * that exceeds the index budget (panther_set_index_budget; by default the
+ * free device memory less the result), the rows are sorted in chunks of
+ * consecutive paths: |P_v| of every vertex is counted first, then each
+ * chunk's pairs are sorted and appended to the lists, so the temporary memory
+ * follows the chunk and the result is the same. Synchronises once per chunk
+ * to size it. Errors: EINVAL, ENOMEM, ECUDA. */
 PANTHER_API panther_status panther_build_index(panther_ctx* ctx, const panther_paths* p, panther_index** out);
+
+/* Temporary device bytes one panther_build_index call may use (0: the free
+ * device memory less the result, the default; otherwise at least 1 MiB).
+ * Errors: EINVAL. */
+PANTHER_API panther_status panther_set_index_budget(panther_ctx* ctx, int64_t bytes);
 
 /* Index build that allocates nothing (the paper has no counterpart; this is
  * for callers that cannot call cudaMalloc, such as a host application that

@@ -41,6 +41,7 @@ SIGNATURES = {
     "panther_last_error": ([_vp], ctypes.c_char_p),
     "panther_sync": ([_vp], _int),
     "panther_set_scratch_budget": ([_vp, _i64], _int),
+    "panther_set_index_budget": ([_vp, _i64], _int),
     "panther_launch_count": ([_vp], _i64),
     "panther_sample_size": ([_dbl, _dbl, _dbl, _int, _P(_i64)], _int),
     "panther_build_graph": ([_vp, _i64, _i64, _vp, _vp, _vp, _int, _int, _P(_vp)], _int),
@@ -169,6 +170,11 @@ def panther_sync(ctx: int) -> None:
 
 def panther_set_scratch_budget(ctx: int, nbytes: int) -> None:
     _check(ctx, load_library().panther_set_scratch_budget(ctx, nbytes))
+
+
+def panther_set_index_budget(ctx: int, nbytes: int) -> None:
+    """Temporary device bytes of an index build (0: free memory); above it the build runs in chunks."""
+    _check(ctx, load_library().panther_set_index_budget(ctx, nbytes))
 
 
 def panther_launch_count(ctx: int) -> int:

@@ -33,6 +33,7 @@ struct Src {
     const int32_t* vals;
     int64_t count;      // number of pairs (later passes)
     int first;          // 1 for pass 0
+    int64_t r0;         // pass 0: path id of row 0 (a chunk of the rows)
 };
 
 // raw word of item i (pass 0: the path entry, -1 past the end; later passes: the key)
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(IX_T, 2) scatter_kernel(Src s, int shift, int 
 #pragma unroll
     for (int k = 0; k < IX_ROUNDS; ++k) {
         const int64_t i = base + k * 32 + lane;
-        val[k] = s.first ? (int32_t)(i / s.stride) : (((okmask >> k) & 1u) ? __ldg(s.vals + i) : 0);
+        val[k] = s.first ? (int32_t)(s.r0 + i / s.stride) : (((okmask >> k) & 1u) ? __ldg(s.vals + i) : 0);
     }
 #pragma unroll
     for (int k = 0; k < IX_ROUNDS; ++k) {
@@ -244,6 +245,39 @@ __global__ void cls_kernel(const int64_t* __restrict__ off, int64_t n, uint8_t* 
         if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
 }
 
+// |P_v| of every vertex over a range of rows (first occurrences only),
+// accumulated into cnt (64-bit, later scanned in place into offsets)
+template <bool LONG>
+__global__ void __launch_bounds__(IX_T) vcount_kernel(Src s, unsigned long long* __restrict__ cnt) {
+    const int64_t base = (int64_t)blockIdx.x * IX_TILE + (int64_t)(threadIdx.x >> 5) * (IX_ROUNDS * 32) +
+                         (threadIdx.x & 31);
+    int32_t x[IX_ROUNDS];
+#pragma unroll
+    for (int k = 0; k < IX_ROUNDS; ++k) x[k] = load_raw(s, base + k * 32);
+    const uint32_t rep = LONG ? long_row_repeats(s, base - (threadIdx.x & 31), x) : 0u;
+#pragma unroll
+    for (int k = 0; k < IX_ROUNDS; ++k)
+        if (item_ok(s, base + k * 32, x[k]) && !((rep >> k) & 1u)) atomicAdd(&cnt[x[k]], 1ull);
+}
+
+// a chunk's pairs, sorted by vertex, appended to each vertex's list: pair i
+// of vertex v (coff[v] = its first position in the chunk) goes to
+// cur[v] + i - coff[v]; chunks come in ascending path order, so every list
+// stays ascending
+__global__ void place_kernel(const int32_t* __restrict__ keys, const int32_t* __restrict__ vals, int64_t cn,
+                             const int64_t* __restrict__ coff, const int64_t* __restrict__ cur,
+                             int32_t* __restrict__ pid) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cn) return;
+    const int32_t v = keys[i];
+    pid[cur[v] + (i - coff[v])] = vals[i];
+}
+
+__global__ void advance_kernel(const int64_t* __restrict__ coff, int64_t n, int64_t* __restrict__ cur) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) cur[v] += coff[v + 1] - coff[v];
+}
+
 __global__ void total_kernel(const int64_t* __restrict__ counts, const int64_t* __restrict__ offs, int64_t len,
                              int64_t* __restrict__ total) {
     *total = offs[len - 1] + counts[len - 1];
@@ -277,55 +311,20 @@ panther_status index_classes(panther_ctx* ctx, panther_index* ix) {
     return PANTHER_OK;
 }
 
-extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_paths* p, panther_index** out) {
-    if (!ctx || !p || !out) return PANTHER_EINVAL;
-    *out = nullptr;
-    cudaSetDevice(ctx->device);
+// LSD radix sort of the (vertex, path) pairs of src (pass 0 reads its rows);
+// the sorted keys and values end in one of the A/B buffers, returned with
+// the number of pairs. Synchronises once (after pass 0, to size the rest).
+static panther_status radix_pairs(panther_ctx* ctx, Src src, int64_t n, int32_t* kA, int32_t* vA, int32_t* kB,
+                                  int32_t* vB, int64_t* counts, int64_t* offs, int64_t* tot, int64_t* count_out,
+                                  int32_t** keys_out, int32_t** vals_out) {
     cudaStream_t s = ctx->stream;
-    const int64_t n = p->n;
-    const int64_t maxpairs = p->R * p->L;
     int passes, rb;
     radix_plan(n, &passes, &rb);
     const int radix = 1 << rb;
-
-    panther_index* ix = new panther_index();
-    ix->ctx = ctx;
-    ix->n = n;
-    ix->R = p->R;
-    int32_t *kA = nullptr, *vA = nullptr, *kB = nullptr, *vB = nullptr;
-    int64_t *counts = nullptr, *offs = nullptr, *tot = nullptr;
-    panther_status st;
-    const int64_t tiles0 = ceil_div(p->R * p->stride, IX_TILE);
-    const int64_t tilesN = ceil_div(maxpairs, IX_TILE);
-    const int64_t maxtiles = tiles0 > tilesN ? tiles0 : tilesN;
-    auto cleanup = [&]() {
-        dev_free(ctx, kA); dev_free(ctx, vA); dev_free(ctx, kB); dev_free(ctx, vB);
-        dev_free(ctx, counts); dev_free(ctx, offs); dev_free(ctx, tot);
-    };
-    if ((st = dev_alloc(ctx, (void**)&kA, sizeof(int32_t) * maxpairs)) ||
-        (st = dev_alloc(ctx, (void**)&vA, sizeof(int32_t) * maxpairs)) ||
-        (st = dev_alloc(ctx, (void**)&kB, sizeof(int32_t) * maxpairs)) ||
-        (st = dev_alloc(ctx, (void**)&vB, sizeof(int32_t) * maxpairs)) ||
-        (st = dev_alloc(ctx, (void**)&counts, sizeof(int64_t) * radix * maxtiles)) ||
-        (st = dev_alloc(ctx, (void**)&offs, sizeof(int64_t) * radix * maxtiles)) ||
-        (st = dev_alloc(ctx, (void**)&tot, sizeof(int64_t))) ||
-        (st = dev_alloc(ctx, (void**)&ix->off, sizeof(int64_t) * (n + 1))) ||
-        (st = dev_alloc(ctx, (void**)&ix->cls, n)) ||
-        (st = dev_alloc(ctx, (void**)&ix->cls_hist, sizeof(int64_t) * 256))) {
-        cleanup();
-        panther_free_index(ix);
-        return st;
-    }
-    PCK(ctx, cudaFuncSetAttribute(scatter_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM));
-    PCK(ctx, cudaFuncSetAttribute(scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM));
-    Src src{};
-    src.rows = p->rows;
-    src.R = p->R;
-    src.L = p->L;
-    src.stride = p->stride;
-    src.first = 1;
+    const int64_t tiles0 = ceil_div(src.R * src.stride, IX_TILE);
     int32_t *ik = nullptr, *iv = nullptr, *ok = kA, *ov = vA;
     int64_t count = 0;
+    panther_status st;
     for (int pass = 0; pass < passes; ++pass) {
         int shift = pass * rb;
         int64_t ntiles = pass == 0 ? tiles0 : ceil_div(count, IX_TILE);
@@ -337,15 +336,15 @@ extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_pa
             hist_kernel<false><<<(unsigned)ntiles, IX_T, 0, s>>>(src, shift, radix, ntiles, counts);
         ctx->launches++;
         cudaError_t e = cudaMemcpyAsync(offs, counts, sizeof(int64_t) * len, cudaMemcpyDeviceToDevice, s);
-        if (e) { cleanup(); panther_free_index(ix); return cuda_err(ctx, e, "index scan copy"); }
-        if ((st = scan_exclusive_i64(ctx, offs, len))) { cleanup(); panther_free_index(ix); return st; }
+        if (e) return cuda_err(ctx, e, "index scan copy");
+        if ((st = scan_exclusive_i64(ctx, offs, len))) return st;
         if (pass == 0) {
             // the number of pairs is needed to size the later passes
             total_kernel<<<1, 1, 0, s>>>(counts, offs, len, tot);
             ctx->launches++;
             e = cudaMemcpyAsync(&count, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
             if (!e) e = cudaStreamSynchronize(s);
-            if (e) { cleanup(); panther_free_index(ix); return cuda_err(ctx, e, "index count"); }
+            if (e) return cuda_err(ctx, e, "index count");
         }
         if (src.first && src.stride > 32)
             scatter_kernel<true><<<(unsigned)ntiles, IX_T, SC_SMEM, s>>>(src, shift, radix, ntiles, offs, ok, ov);
@@ -353,7 +352,7 @@ extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_pa
             scatter_kernel<false><<<(unsigned)ntiles, IX_T, SC_SMEM, s>>>(src, shift, radix, ntiles, offs, ok, ov);
         ctx->launches++;
         e = cudaGetLastError();
-        if (e) { cleanup(); panther_free_index(ix); return cuda_err(ctx, e, "index scatter"); }
+        if (e) return cuda_err(ctx, e, "index scatter");
         // next pass reads what this one wrote
         src.first = 0;
         src.keys = ok;
@@ -363,19 +362,158 @@ extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_pa
         ok = (ok == kA) ? kB : kA;
         ov = (ov == vA) ? vB : vA;
     }
-    ix->nnz = count;
-    offsets_kernel<<<(unsigned)ceil_div(count + 1, 256), 256, 0, s>>>(ik, count, n, ix->off, ctx->d_status);
-    ctx->launches++;
-    if ((st = index_classes(ctx, ix))) {
+    *count_out = count;
+    *keys_out = ik;
+    *vals_out = iv;
+    return PANTHER_OK;
+}
+
+// device bytes of the temporary buffers of one radix sort over `rows` rows
+static int64_t radix_temp_bytes(int64_t rows, int L, int stride, int radix) {
+    const int64_t pairs = rows * L;
+    const int64_t tiles = std::max(ceil_div(rows * stride, IX_TILE), ceil_div(pairs, IX_TILE));
+    return 4 * pairs * 4 + 2 * (int64_t)radix * tiles * 8 + 64;
+}
+
+extern "C" panther_status panther_set_index_budget(panther_ctx* ctx, int64_t bytes) {
+    if (!ctx || bytes < 0) return PANTHER_EINVAL;
+    if (bytes > 0 && bytes < (int64_t(1) << 20)) return set_err(ctx, PANTHER_EINVAL, "index budget below 1 MiB");
+    ctx->index_budget = bytes;
+    return PANTHER_OK;
+}
+
+extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_paths* p, panther_index** out) {
+    if (!ctx || !p || !out) return PANTHER_EINVAL;
+    *out = nullptr;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const int64_t n = p->n;
+    int passes, rb;
+    radix_plan(n, &passes, &rb);
+    const int radix = 1 << rb;
+
+    // rows per radix sort: all of them when their temporary buffers fit the
+    // budget (set, or else the free device memory less what the results
+    // need); otherwise the largest chunk that fits
+    int64_t rows = p->R;
+    {
+        const int64_t need = radix_temp_bytes(p->R, p->L, p->stride, radix);
+        int64_t budget = ctx->index_budget;
+        if (budget == 0) {
+            const int64_t results = p->R * p->L * 4 + 3 * (n + 1) * 8 + n + (int64_t(256) << 20);
+            size_t fr = 0, tot = 0;
+            if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && (int64_t)fr - results < need) {
+                // memory the pool keeps but no one uses goes back first
+                cudaMemPool_t pool;
+                if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+                cudaMemGetInfo(&fr, &tot);
+            }
+            cudaGetLastError();
+            budget = fr > 0 ? std::max<int64_t>((int64_t)fr - results, int64_t(1) << 20) : need;
+        }
+        if (need > budget) {
+            int64_t lo = 1, hi = p->R;           // largest chunk whose buffers fit
+            while (lo < hi) {
+                const int64_t mid = lo + (hi - lo + 1) / 2;
+                if (radix_temp_bytes(mid, p->L, p->stride, radix) <= budget) lo = mid; else hi = mid - 1;
+            }
+            rows = lo;
+            if (radix_temp_bytes(rows, p->L, p->stride, radix) > budget)
+                return set_err(ctx, PANTHER_ENOMEM, "the index budget does not hold the buffers of one row");
+        }
+    }
+
+    panther_index* ix = new panther_index();
+    ix->ctx = ctx;
+    ix->n = n;
+    ix->R = p->R;
+    int32_t *kA = nullptr, *vA = nullptr, *kB = nullptr, *vB = nullptr;
+    int64_t *counts = nullptr, *offs = nullptr, *tot = nullptr, *cur = nullptr, *coff = nullptr;
+    panther_status st;
+    const int64_t maxpairs = rows * p->L;
+    const int64_t maxtiles = std::max(ceil_div(rows * p->stride, IX_TILE), ceil_div(maxpairs, IX_TILE));
+    auto cleanup = [&]() {
+        dev_free(ctx, kA); dev_free(ctx, vA); dev_free(ctx, kB); dev_free(ctx, vB);
+        dev_free(ctx, counts); dev_free(ctx, offs); dev_free(ctx, tot); dev_free(ctx, cur); dev_free(ctx, coff);
+    };
+    auto fail = [&](panther_status e) {
         cleanup();
         panther_free_index(ix);
-        return st;
+        return e;
+    };
+    if ((st = dev_alloc(ctx, (void**)&kA, sizeof(int32_t) * maxpairs)) ||
+        (st = dev_alloc(ctx, (void**)&vA, sizeof(int32_t) * maxpairs)) ||
+        (st = dev_alloc(ctx, (void**)&kB, sizeof(int32_t) * maxpairs)) ||
+        (st = dev_alloc(ctx, (void**)&vB, sizeof(int32_t) * maxpairs)) ||
+        (st = dev_alloc(ctx, (void**)&counts, sizeof(int64_t) * radix * maxtiles)) ||
+        (st = dev_alloc(ctx, (void**)&offs, sizeof(int64_t) * radix * maxtiles)) ||
+        (st = dev_alloc(ctx, (void**)&tot, sizeof(int64_t))) ||
+        (st = dev_alloc(ctx, (void**)&ix->off, sizeof(int64_t) * (n + 1))) ||
+        (st = dev_alloc(ctx, (void**)&ix->cls, n)) ||
+        (st = dev_alloc(ctx, (void**)&ix->cls_hist, sizeof(int64_t) * 256)))
+        return fail(st);
+    PCK(ctx, cudaFuncSetAttribute(scatter_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM));
+    PCK(ctx, cudaFuncSetAttribute(scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM));
+    Src src{};
+    src.rows = p->rows;
+    src.R = p->R;
+    src.L = p->L;
+    src.stride = p->stride;
+    src.first = 1;
+    src.r0 = 0;
+    cudaError_t e;
+    if (rows == p->R) {
+        // one radix sort over all pairs; its final values are pid
+        int64_t count = 0;
+        int32_t *ik = nullptr, *iv = nullptr;
+        if ((st = radix_pairs(ctx, src, n, kA, vA, kB, vB, counts, offs, tot, &count, &ik, &iv))) return fail(st);
+        ix->nnz = count;
+        offsets_kernel<<<(unsigned)ceil_div(count + 1, 256), 256, 0, s>>>(ik, count, n, ix->off, ctx->d_status);
+        ctx->launches++;
+        if ((st = index_classes(ctx, ix))) return fail(st);
+        // keep the final value array as pid; release everything else
+        ix->pid = iv;
+        if (iv == vA) vA = nullptr; else vB = nullptr;
+    } else {
+        // chunks of `rows` path rows: |P_v| of every vertex first (the
+        // offsets), then each chunk sorted and appended to the lists
+        if ((e = cudaMemsetAsync(ix->off, 0, sizeof(int64_t) * (n + 1), s))) return fail(cuda_err(ctx, e, "index"));
+        const int64_t tilesAll = ceil_div(p->R * p->stride, IX_TILE);
+        if (p->stride > 32)
+            vcount_kernel<true><<<(unsigned)tilesAll, IX_T, 0, s>>>(src, (unsigned long long*)ix->off);
+        else
+            vcount_kernel<false><<<(unsigned)tilesAll, IX_T, 0, s>>>(src, (unsigned long long*)ix->off);
+        ctx->launches++;
+        if ((st = scan_exclusive_i64(ctx, ix->off, n + 1))) return fail(st);
+        int64_t nnz = 0;
+        if ((e = cudaMemcpyAsync(&nnz, ix->off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s)) ||
+            (e = cudaStreamSynchronize(s)))
+            return fail(cuda_err(ctx, e, "index count"));
+        ix->nnz = nnz;
+        if ((st = dev_alloc(ctx, (void**)&ix->pid, sizeof(int32_t) * (nnz > 0 ? nnz : 1))) ||
+            (st = dev_alloc(ctx, (void**)&cur, sizeof(int64_t) * (n + 1))) ||
+            (st = dev_alloc(ctx, (void**)&coff, sizeof(int64_t) * (n + 1))))
+            return fail(st);
+        if ((e = cudaMemcpyAsync(cur, ix->off, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, s)))
+            return fail(cuda_err(ctx, e, "index"));
+        for (int64_t r0 = 0; r0 < p->R; r0 += rows) {
+            Src cs = src;
+            cs.rows = p->rows + r0 * p->stride;
+            cs.R = std::min(rows, p->R - r0);
+            cs.r0 = r0;
+            int64_t cn = 0;
+            int32_t *ck = nullptr, *cv = nullptr;
+            if ((st = radix_pairs(ctx, cs, n, kA, vA, kB, vB, counts, offs, tot, &cn, &ck, &cv))) return fail(st);
+            offsets_kernel<<<(unsigned)ceil_div(cn + 1, 256), 256, 0, s>>>(ck, cn, n, coff, ctx->d_status);
+            if (cn > 0) place_kernel<<<(unsigned)ceil_div(cn, 256), 256, 0, s>>>(ck, cv, cn, coff, cur, ix->pid);
+            advance_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(coff, n, cur);
+            ctx->launches += cn > 0 ? 3 : 2;
+            if ((e = cudaGetLastError())) return fail(cuda_err(ctx, e, "index chunk"));
+        }
+        if ((st = index_classes(ctx, ix))) return fail(st);
     }
-    // keep the final value array as pid; release everything else
-    ix->pid = iv;
-    if (iv == vA) vA = nullptr; else vB = nullptr;
     cleanup();
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e) { panther_free_index(ix); return cuda_err(ctx, e, "index offsets"); }
     *out = ix;
     return PANTHER_OK;

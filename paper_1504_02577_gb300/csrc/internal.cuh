@@ -29,6 +29,7 @@ struct panther_ctx {
     uint32_t* d_status = nullptr;     // [0] flags, [1..3] detail
     uint32_t* h_status = nullptr;     // pinned mirror
     int64_t scratch_budget = int64_t(8) << 30;
+    int64_t index_budget = 0;         // temporary bytes of an index build (0: free device memory)
     std::atomic<int64_t> launches{0};
     std::string err;
     int64_t knn_stats[4] = {0, 0, 0, 0};

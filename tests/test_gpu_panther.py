@@ -233,6 +233,37 @@ def test_paths_other_lengths(pk, T, mode):
     assert np.array_equal(out["off"], off) and np.array_equal(out["pid"], pid)
 
 
+@pytest.mark.parametrize("T,budget", [(5, 1 << 20), (5, 3 << 20), (64, 2 << 20), (3, 10 << 20)])
+def test_index_in_chunks_equals_one_pass(pk, small, T, budget):
+    # an index budget too small for one radix sort over all pairs: the rows
+    # are sorted in chunks of consecutive paths and appended per vertex; the
+    # index must equal the one-pass index and the oracle's (ragged R, long
+    # rows, a budget that leaves two chunks)
+    R = 200_001 if T < 64 else 20_001
+    with pk.Panther(0) as P:
+        P.build_graph(small.row_ptr, small.col, small.w, pk.MODE_ALIAS)
+        P.sample_paths(4, R, T, pk.MODE_ALIAS)
+        P.build_index()
+        off1, pid1 = (t.cpu().numpy() for t in P.index_tensors())
+        launches1 = P.launches()
+        pk.panther_set_index_budget(P.h.ctx, budget)
+        P.build_index()
+        chunk_launches = P.launches() - launches1
+        off2, pid2 = (t.cpu().numpy() for t in P.index_tensors())
+        ids, cnt = P.topk(torch.arange(small.n, dtype=torch.int32, device="cuda:0"), 10)
+        P.sync()
+        paths = P.paths_tensor().cpu().numpy()
+        with pytest.raises(pk.PantherError):
+            pk.panther_set_index_budget(P.h.ctx, 1000)          # below 1 MiB
+    assert chunk_launches > 12                                   # several chunks ran
+    assert np.array_equal(off1, off2) and np.array_equal(pid1, pid2)
+    off, pid = oracle.build_index(small.n, paths)
+    assert np.array_equal(off2, off) and np.array_equal(pid2, pid)
+    o = oracle.Oracle(small.n, paths, off, pid)
+    rid, rcnt = o.topk_many(np.arange(small.n, dtype=np.int32), 10)
+    assert np.array_equal(ids.cpu().numpy(), rid) and np.array_equal(cnt.cpu().numpy().astype(np.uint32), rcnt)
+
+
 def test_paths_wide_prefix_and_isolated(pk):
     # 64-bit cumulative weights and isolated vertices (the walk stays put)
     edges = [(0, i) for i in range(1, 30)] + [(1, 2), (2, 3)]

@@ -264,13 +264,20 @@ def run_ours(args, ws, rank, local):
         torch.cuda.nvtx.range_push("timed")   # lets a profiler keep only the timed launches
         start.record(P.stream)
         for _ in range(args.steps):
-            step(rec)
+            last = step(rec)
         end.record(P.stream)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
     launches = P.launches() - l0
     P.sync()
     tiers = pk.panther_topk_stats(P.h.ctx)
+    # the last timed step's results, for the oracle comparison at the end
+    checked = None
+    if rank == 0 and ws == 1 and not args.no_extras:
+        o_t, p_t = P.index_tensors()
+        checked = {"paths": P.paths_tensor().cpu().numpy(), "off": o_t.cpu().numpy(), "pid": p_t.cpu().numpy(),
+                   "ids": last[0].cpu().numpy(), "cnt": last[1].cpu().numpy().view(np.uint32)}
+        del o_t, p_t
     ms_total = start.elapsed_time(end)
     ms_step = _max_over_ranks(ms_total / args.steps, ws)
     stage_ms = {s: statistics.median(r[i].elapsed_time(r[i + 1]) for r in rec) for i, s in enumerate(stages)}
@@ -356,9 +363,12 @@ def run_ours(args, ws, rank, local):
         out["knn"] = knn_block(pk, torch, local, args)
 
     if rank == 0 and ws == 1 and not args.no_extras:
-        run = OracleRun(g, R, T, k, queries=q_host)
+        run = OracleRun(g, R, T, k, queries=q_host, keep_rows=checked is not None)
         step_s, topk_s, F, parts = run.step(seed=1)
         out["cpu_baseline"] = run.describe(step_s, topk_s, F, parts)
+        if checked is not None:
+            out["parity"] = run.check(checked, q_host)
+            del checked
         if topk_checks:   # served top-k rows against the oracle (same seed, R, T)
             ok = True
             for q, kk, ids, cnt in topk_checks:
@@ -552,7 +562,7 @@ class OracleRun:
     since its queries are exchangeable draws from the stratum.
     """
 
-    def __init__(self, g, R, T, k, threads=None, queries=None):
+    def __init__(self, g, R, T, k, threads=None, queries=None, keep_rows=False):
         import oracle
         oracle.build()
         self.oracle = oracle
@@ -581,13 +591,43 @@ class OracleRun:
         empty = np.nonzero(sizes == 0)[0][:th].astype(np.int32)
         self.empty = empty if empty.size else order[-th:]
         self.o.topk_many(self.empty, k, threads=th)        # first touch of the driver's memory
+        self.keep_rows = keep_rows
+        self.rows = {}                                      # oracle rows of every timed query (keep_rows)
         self.t_heavy = self._wall(self.heavy)
         self.nnz = int(off[-1])
 
     def _wall(self, q):
         t0 = time.perf_counter()
-        self.o.topk_many(q, self.k, threads=self.threads)
-        return time.perf_counter() - t0
+        ids, cnt = self.o.topk_many(q, self.k, threads=self.threads)
+        t = time.perf_counter() - t0
+        if self.keep_rows:
+            self.rows[id(q)] = (np.asarray(q), ids, cnt)
+        return t
+
+    def check(self, gpu, queries):
+        """The GPU's paths and index (in full) and its top-k rows of every
+        query the oracle timed here (the heaviest vertices and both samples)
+        against the oracle's; queries[i] is the vertex of output row i."""
+        res = {"paths_compared": int(gpu["paths"].shape[0]),
+               "paths_identical": bool(np.array_equal(gpu["paths"], self.paths)),
+               "index_pairs_compared": int(gpu["pid"].shape[0]),
+               "index_identical": bool(np.array_equal(gpu["off"], self.o.off)
+                                       and np.array_equal(gpu["pid"], self.o.pid[: gpu["pid"].shape[0]])
+                                       and gpu["pid"].shape[0] == self.nnz)}
+        row_of = np.full(self.g.n, -1, np.int64)
+        row_of[np.asarray(queries)] = np.arange(len(queries))
+        n_rows, same = 0, True
+        for q, ids, cnt in self.rows.values():
+            r = row_of[q]
+            keep = r >= 0
+            same &= bool(np.array_equal(gpu["ids"][r[keep]], ids[keep])
+                         and np.array_equal(gpu["cnt"][r[keep]], cnt[keep]))
+            n_rows += int(keep.sum())
+        res["topk_rows_compared"] = n_rows
+        res["topk_identical"] = same
+        res["what"] = ("the last timed step's paths and index in full, and its top-k rows of the queries the "
+                       "oracle timed (the heaviest vertices and the uniform samples), against the oracle")
+        return res
 
     def step(self, seed, n_mid=8_192, n_light=524_288):
         """One sampled estimate of the all-vertex top-k time (seconds), plus the parts."""
@@ -618,13 +658,6 @@ class OracleRun:
                 "step_s": round(step_s, 2), "topk_s_estimated": round(topk_s, 2),
                 "stages_s": {"tables": round(self.t_tables, 2), "paths": round(self.t_paths, 2),
                              "index": round(self.t_index, 2), "topk": round(topk_s, 2)}}
-
-
-def cpu_baseline(workload, g, R, T, k, q_host):
-    """The oracle on all host cores over the same workload (see OracleRun)."""
-    run = OracleRun(g, R, T, k, queries=q_host)
-    step_s, topk_s, F, parts = run.step(seed=1)
-    return run.describe(step_s, topk_s, F, parts)
 
 
 def run_reference(args, ws, rank):

@@ -67,3 +67,34 @@ def test_gpu_arm_fails_loudly_without_cuda():
     out = _run(["bench.py", "--workload", "small", "--steps", "1", "--warmup", "3"])
     assert out.returncode != 0
     assert not _json_lines(out.stdout)
+
+
+def test_oracle_run_parity_check_logic():
+    # the benchmark's parity block: the GPU's results stand in here as the
+    # oracle's own (all identical), then one changed path entry, index entry
+    # and top-k count are each caught
+    import numpy as np
+    import bench
+    import oracle
+    import synth
+    g = synth.workload_graph("small")
+    R, T, k = 20_000, 5, 10
+    q = np.arange(g.n, dtype=np.int32)
+    run = bench.OracleRun(g, R, T, k, threads=2, queries=q, keep_rows=True)
+    run.step(seed=3, n_mid=300, n_light=300)
+    ids, cnt = run.o.topk_many(q, k, threads=2)
+    gpu = {"paths": run.paths.copy(), "off": run.o.off.copy(), "pid": run.o.pid[: run.nnz].copy(),
+           "ids": ids.copy(), "cnt": cnt.copy()}
+    res = run.check(gpu, q)
+    assert res["paths_identical"] and res["index_identical"] and res["topk_identical"]
+    assert res["topk_rows_compared"] >= 256 and res["index_pairs_compared"] == run.nnz
+    bad = dict(gpu, paths=gpu["paths"].copy())
+    bad["paths"][7, 3] ^= 1
+    assert not run.check(bad, q)["paths_identical"]
+    bad = dict(gpu, pid=gpu["pid"].copy())
+    bad["pid"][11] += 1
+    assert not run.check(bad, q)["index_identical"]
+    bad = dict(gpu, cnt=gpu["cnt"].copy())
+    heavy = int(run.heavy[0])
+    bad["cnt"][heavy, 0] += 1
+    assert not run.check(bad, q)["topk_identical"]

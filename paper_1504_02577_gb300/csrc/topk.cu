@@ -1280,6 +1280,38 @@ __global__ void g_count_kernel(PathsRef P, const int32_t* __restrict__ queries, 
     if (!ok) flag_status(status, ST_HASH_FULL);
 }
 
+// 64 < k <= 128 sends every query of the batch to device tables; queries of
+// at most WARP_NP paths are counted by one warp each instead of a CTA per
+// 512 paths
+constexpr int64_t WARP_NP = 2048;
+
+template <int STRIDE>
+__global__ void __launch_bounds__(256) g_count_warp_kernel(PathsRef P, const int32_t* __restrict__ queries, GPlan G,
+                                                           unsigned long long* arena, uint32_t* status) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw >= G.ng) return;                           // warp-uniform
+    const int g = (int)gw;
+    const int64_t qi = G.qidx[g];
+    const int32_t v = queries ? queries[qi] : (int32_t)qi;
+    const int64_t a = P.off[v], b = P.off[v + 1];
+    if (b - a > WARP_NP) return;                      // counted by g_count_kernel
+    unsigned long long* tab = arena + G.tab_off[g];
+    const uint32_t ns = G.tab_n[g];
+    const uint32_t thr = G.thr ? G.thr[g] : 0;
+    const unsigned lane = threadIdx.x & 31;
+    bool ok = true;
+    if constexpr (STRIDE > 32) {
+        for (int64_t base = a; base < b; base += 32) {            // warp-uniform
+            const int64_t e = base + lane;
+            const bool act = e < b;
+            ok &= insert_paths_warp<STRIDE>(P, act ? P.pid[e] : -1, v, tab, ns, act, thr);
+        }
+    } else {
+        for (int64_t e = a + lane; e < b; e += 32) ok &= insert_path<STRIDE, false>(P, P.pid[e], v, tab, ns, thr);
+    }
+    if (!ok) flag_status(status, ST_HASH_FULL);
+}
+
 // partial top-k of one chunk of one table; empties the slots it read
 __global__ void __launch_bounds__(512) g_select_kernel(GPlan G, unsigned long long* arena, int k,
                                                        unsigned long long* partial) {
@@ -1323,7 +1355,29 @@ __global__ void g_merge_kernel(GPlan G, const unsigned long long* __restrict__ p
     write_list(t, o, G.qidx[g]);
 }
 
-// 64 < k <= 128: partial 128-lists of the table chunks, then one merge per query
+// 64 < k <= 128: tables of at most SMALL4 slots are selected whole by one
+// warp (most queries of a batch: their tables are sized to twice their
+// candidate bound, from 64 slots); larger ones in chunks (partial 128-lists),
+// then one merge per query
+constexpr uint32_t SMALL4 = 2048;
+
+__global__ void __launch_bounds__(256) g_small4_kernel(GPlan G, unsigned long long* arena, OutRef o) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw >= G.ng) return;                           // warp-uniform
+    const int g = (int)gw;
+    const uint32_t ns = G.tab_n[g];
+    if (ns > SMALL4) return;
+    unsigned long long* tab = arena + G.tab_off[g];
+    const unsigned lane = threadIdx.x & 31;
+    WarpTopK4 t;
+    for (uint32_t base = 0; base < ns; base += 32) {  // ns is a power of two >= 64
+        uint64_t sc = slot_score(tab[base + lane]);
+        if (sc) tab[base + lane] = EMPTY;
+        t.offer(sc, o.k);
+    }
+    write_list4(t, o, G.qidx[g]);
+}
+
 __global__ void __launch_bounds__(512) g_select4_kernel(GPlan G, unsigned long long* arena, int k,
                                                         unsigned long long* partial) {
     __shared__ unsigned long long lists[16 * KMAX4];
@@ -1355,6 +1409,7 @@ __global__ void __launch_bounds__(256) g_merge4_kernel(GPlan G, const unsigned l
                                                        OutRef o) {
     __shared__ unsigned long long lists[8 * KMAX4];
     const int g = blockIdx.x;
+    if (G.tab_n[g] <= SMALL4) return;                 // answered by g_small4_kernel
     const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const unsigned lane = threadIdx.x & 31;
     WarpTopK4 t;
@@ -1511,8 +1566,8 @@ __global__ void fill_empty_kernel(unsigned long long* p, int64_t n) {
     for (; i < n; i += st) p[i] = EMPTY;
 }
 
-uint32_t pow2_at_least(int64_t x) {
-    uint32_t p = 1024;
+uint32_t pow2_at_least(int64_t x, uint32_t lo = 1024) {
+    uint32_t p = lo;
     while ((int64_t)p < x && p < (1u << 31)) p <<= 1;
     return p;
 }
@@ -1704,7 +1759,8 @@ static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int3
         int64_t used = 0;
         while (pos < hubs.size()) {
             const HubQuery& h = hubs[pos];
-            uint32_t slots = pow2_at_least(hub_bound(P, h, above) * 2);
+            // k > 64 sends every query here: small ones get small tables
+            uint32_t slots = pow2_at_least(hub_bound(P, h, above) * 2, k > KMAX ? 64u : 1024u);
             if (!rq.empty() && used + slots > budget_slots) break;
             rq.push_back(h.qi);
             rt.push_back(h.thr);
@@ -1712,8 +1768,8 @@ static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int3
             roff.push_back(used);
             rn.push_back(slots);
             used += slots;
-            ioff.push_back(ioff.back() + ceil_div(h.np, G_PATHS));
-            soff.push_back(soff.back() + ceil_div(slots, G_SLOTS));
+            ioff.push_back(ioff.back() + ((k > KMAX && h.np <= WARP_NP) ? 0 : ceil_div(h.np, G_PATHS)));
+            soff.push_back(soff.back() + ((k > KMAX && slots <= SMALL4) ? 0 : ceil_div(slots, G_SLOTS)));
             ++pos;
         }
         if (used > arena_slots) {
@@ -1747,14 +1803,28 @@ static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int3
         ctx->hub_arena_clean = false;   // until the select pass of this round has run
         GPlan G{(const int32_t*)(dplan + o_q), (const int64_t*)(dplan + o_o), (const uint32_t*)(dplan + o_n),
                 (const int64_t*)(dplan + o_i), (const int64_t*)(dplan + o_s), rng, (const uint32_t*)(dplan + o_t)};
-        if (stride == 8) g_count_kernel<8><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
-        else if (stride == 16) g_count_kernel<16><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
-        else if (stride == 32) g_count_kernel<32><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
-        else if (stride == 64) g_count_kernel<64><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
-        else g_count_kernel<128><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
         if (k > KMAX) {
-            g_select4_kernel<<<(unsigned)soff.back(), 512, 0, s>>>(G, arena, k, partial);
-            g_merge4_kernel<<<rng, 256, 0, s>>>(G, partial, o);
+            const unsigned gwb = (unsigned)ceil_div((int64_t)rng * 32, 256);
+            if (stride == 8) g_count_warp_kernel<8><<<gwb, 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
+            else if (stride == 16) g_count_warp_kernel<16><<<gwb, 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
+            else if (stride == 32) g_count_warp_kernel<32><<<gwb, 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
+            else if (stride == 64) g_count_warp_kernel<64><<<gwb, 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
+            else g_count_warp_kernel<128><<<gwb, 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
+            ctx->launches++;
+        }
+        if (ioff.back() > 0) {
+            if (stride == 8) g_count_kernel<8><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
+            else if (stride == 16) g_count_kernel<16><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
+            else if (stride == 32) g_count_kernel<32><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
+            else if (stride == 64) g_count_kernel<64><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
+            else g_count_kernel<128><<<(unsigned)ioff.back(), 256, 0, s>>>(P, queries, G, arena, ctx->d_status);
+        }
+        if (k > KMAX) {
+            g_small4_kernel<<<(unsigned)ceil_div((int64_t)rng * 32, 256), 256, 0, s>>>(G, arena, o);
+            if (soff.back() > 0) {
+                g_select4_kernel<<<(unsigned)soff.back(), 512, 0, s>>>(G, arena, k, partial);
+                g_merge4_kernel<<<rng, 256, 0, s>>>(G, partial, o);
+            }
         } else {
             g_select_kernel<<<(unsigned)soff.back(), 512, 0, s>>>(G, arena, k, partial);
             g_merge_cta_kernel<<<rng, 256, 0, s>>>(G, partial, o);

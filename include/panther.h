@@ -297,9 +297,11 @@ PANTHER_API panther_status panther_set_topk_shape(panther_ctx* ctx, int threads,
 
 /* theta(v) = the D largest counts cnt(v,u), u != v, descending, zero padded,
  * for every vertex (Algorithm 2's loop over V), plus the device data the
- * k-NN search needs (a BF16 copy padded to 64 columns, exact squared norms).
- *   1 <= D <= 64. Errors: EINVAL, ENOMEM, EOVERFLOW (a count >= 2^29, which
- *   would let a squared distance overflow 64 bits), ECUDA. Synchronises. */
+ * k-NN search needs (for D <= 56 a BF16 copy padded to 64 columns; exact
+ * squared norms).
+ *   1 <= D <= 128 (D > 64 counts through the top-k path for k > 64).
+ *   Errors: EINVAL, ENOMEM, EOVERFLOW (max count^2 * D reaches 2^64, so a
+ *   squared distance could overflow 64 bits), ECUDA. Synchronises. */
 PANTHER_API panther_status pantherpp_vectors(panther_ctx* ctx, const panther_index* ix, const panther_paths* p,
                                  int D, pantherpp_vecs** out);
 
@@ -317,7 +319,9 @@ PANTHER_API panther_status pantherpp_vecs_view(const pantherpp_vecs* v, const ui
  *          candidate the bound cannot rule out) or PANTHER_KNN_FP32 (FP32
  *          CUDA-core brute force with the same bound and rerank), optionally
  *          | PANTHER_IO_HOST.
- * Both forms return the exact answer. Errors: EINVAL, ENOMEM, ECUDA. */
+ * Vectors wider than a form's screen (D > 56 for BF16, D > 64 for FP32) are
+ * answered by exact integer brute force over every candidate instead.
+ * Every form returns the exact answer. Errors: EINVAL, ENOMEM, ECUDA. */
 PANTHER_API panther_status pantherpp_knn(panther_ctx* ctx, const pantherpp_vecs* v, const int32_t* queries,
                              int64_t q, int k, int32_t* out_ids, uint64_t* out_dist2, int flags);
 

@@ -119,18 +119,20 @@ __global__ void vec_brow_kernel(const uint32_t* __restrict__ theta, const uint64
                                 float* __restrict__ cncf) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= M.npad) return;
-    uint16_t* row = B + p * KN_K;
+    uint16_t* row = B ? B + p * KN_K : nullptr;      // no BF16 rows when D > 56 (FP32 form only)
     if (p >= M.n) {
         // padding: y = 2^40 for every query, id -1 (never selected)
-        for (int d = 0; d < KN_K; ++d) row[d] = 0;
-        row[M.D] = bf16_bits_of(1099511627776.0f);
+        if (row) {
+            for (int d = 0; d < KN_K; ++d) row[d] = 0;
+            row[M.D] = bf16_bits_of(1099511627776.0f);
+        }
         cid[p] = -1;
         cnrm[p] = 0.f;
         cncf[p] = 1099511627776.0f;
         return;
     }
     int32_t v = perm[p];
-    for (int d = 0; d < KN_K; ++d) {
+    for (int d = 0; row && d < KN_K; ++d) {
         float f = 0.f;
         if (d < M.D) f = -2.0f * (float)round8(theta[(int64_t)v * M.D + d]);
         else if (d < M.D + 8) {
@@ -956,6 +958,20 @@ __global__ void exact_flags_of_queries(const int32_t* __restrict__ queries, int6
     f[i] = (v < 0 || v >= n) ? 1 : exact[v];
 }
 
+// slots of the exact brute-force form: query q0 + i in slot i
+__global__ void brute_slots_kernel(const int32_t* __restrict__ queries, int64_t q0, int64_t qb, int64_t n,
+                                   int32_t* __restrict__ qv, int32_t* __restrict__ qidx, int32_t* __restrict__ slots,
+                                   uint32_t* status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= qb) return;
+    const int32_t v = queries ? queries[q0 + i] : (int32_t)(q0 + i);
+    const bool bad = v < 0 || v >= n;
+    if (bad) flag_status(status, ST_BAD_QUERY);
+    qv[i] = bad ? -1 : v;
+    qidx[i] = (int32_t)(q0 + i);
+    slots[i] = (int32_t)i;
+}
+
 __global__ void fill_i32(int32_t* p, int64_t n, int32_t v) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
@@ -1000,7 +1016,7 @@ extern "C" panther_status pantherpp_vectors(panther_ctx* ctx, const panther_inde
                                             pantherpp_vecs** out) {
     if (!ctx || !ix || !p || !out) return PANTHER_EINVAL;
     *out = nullptr;
-    if (D < 1 || D > 64) return set_err(ctx, PANTHER_EINVAL, "D must be in [1, 64]");
+    if (D < 1 || D > 128) return set_err(ctx, PANTHER_EINVAL, "D must be in [1, 128]");
     if (ix->n != p->n || ix->R != p->R)
         return set_err(ctx, PANTHER_EINVAL, "index and paths do not belong together");
     cudaSetDevice(ctx->device);
@@ -1042,14 +1058,27 @@ extern "C" panther_status pantherpp_vectors(panther_ctx* ctx, const panther_inde
     PCK(ctx, cudaMemcpyAsync(&hmax, maxv, 4, cudaMemcpyDeviceToHost, s));
     PCK(ctx, cudaStreamSynchronize(s));
     v->max_val = hmax;
-    if (hmax >= (1u << 29))
-        return fail(set_err(ctx, PANTHER_EOVERFLOW, "a count reaches 2^29: squared distances could overflow"));
+    if ((unsigned __int128)hmax * hmax * (unsigned)D >= ((unsigned __int128)1 << 64))
+        return fail(set_err(ctx, PANTHER_EOVERFLOW, "max count^2 * D reaches 2^64: squared distances could overflow"));
     pantherpp_vecs& x = *v;
     x.nexact = last_scan + last_flag;
     x.npad = ceil_div(n, KN_N) * KN_N;
     int32_t* perm = nullptr;
+    if (D > KN_K) {   // wider than either screen: k-NN runs the exact brute force on theta alone
+        dev_free(ctx, flag);
+        dev_free(ctx, pos);
+        dev_free(ctx, maxv);
+        cudaError_t ce = cudaStreamSynchronize(s);
+        if (ce) {
+            flag = pos = nullptr;
+            maxv = nullptr;
+            return fail(cuda_err(ctx, ce, "vector preparation"));
+        }
+        *out = v;
+        return PANTHER_OK;
+    }
     if ((st = dev_alloc(ctx, (void**)&perm, sizeof(int32_t) * x.npad)) ||
-        (st = dev_alloc(ctx, (void**)&x.B, (size_t)x.npad * KN_K * 2)) ||
+        (D <= KN_K - 8 && (st = dev_alloc(ctx, (void**)&x.B, (size_t)x.npad * KN_K * 2))) ||
         (st = dev_alloc(ctx, (void**)&x.cid, sizeof(int32_t) * x.npad)) ||
         (st = dev_alloc(ctx, (void**)&x.cnrm, sizeof(float) * x.npad)) ||
         (st = dev_alloc(ctx, (void**)&x.cncf, sizeof(float) * x.npad)) ||
@@ -1248,6 +1277,53 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* vq, const 
     return PANTHER_OK;
 }
 
+// Vectors wider than a screen takes (D > 56 for BF16, D > 64 for FP32): the
+// exact k nearest by integer brute force, queries in batches, each query's
+// candidates cut into ranges screened by separate warps (each keeps a sorted
+// k-list across its lanes), then merged per query.
+static panther_status knn_brute_all(panther_ctx* ctx, const pantherpp_vecs* vq, const pantherpp_vecs* vc, bool same,
+                                    const int32_t* queries, int64_t q, int k, int32_t* ids, uint64_t* d2) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = vc->n;
+    const int64_t nparts = std::max<int64_t>(1, std::min<int64_t>(1024, ceil_div(n, 4096)));
+    const int64_t B = std::min<int64_t>(q, 2048);
+    int32_t *qv = nullptr, *qidx = nullptr, *slots = nullptr, *bid = nullptr;
+    uint64_t* bd = nullptr;
+    auto cleanup = [&]() {
+        dev_free(ctx, qv); dev_free(ctx, qidx); dev_free(ctx, slots); dev_free(ctx, bid); dev_free(ctx, bd);
+    };
+    panther_status st;
+    if ((st = dev_alloc(ctx, (void**)&qv, sizeof(int32_t) * B)) ||
+        (st = dev_alloc(ctx, (void**)&qidx, sizeof(int32_t) * B)) ||
+        (st = dev_alloc(ctx, (void**)&slots, sizeof(int32_t) * B)) ||
+        (st = dev_alloc(ctx, (void**)&bid, sizeof(int32_t) * B * nparts * k)) ||
+        (st = dev_alloc(ctx, (void**)&bd, sizeof(uint64_t) * B * nparts * k))) {
+        cleanup();
+        return st;
+    }
+    for (int64_t q0 = 0; q0 < q; q0 += B) {
+        const int64_t qb = std::min(B, q - q0);
+        brute_slots_kernel<<<(unsigned)ceil_div(qb, 256), 256, 0, s>>>(queries, q0, qb, vq->n, qv, qidx, slots,
+                                                                       ctx->d_status);
+        brute_warp_kernel<<<(unsigned)ceil_div(qb * nparts * 32, 256), 256, 0, s>>>(
+            vq->theta, vc->theta, same, vq->D, n, qv, slots, qb, nparts, k, bid, bd);
+        chunk_merge_kernel<<<(unsigned)std::min<int64_t>(qb, 8 * ctx->num_sms), 256, 0, s>>>(
+            qv, qidx, nullptr, slots, qb, nparts, k, bid, bd, ids, d2);
+        ctx->launches += 3;
+        cudaError_t e = cudaGetLastError();
+        if (e) {
+            cleanup();
+            return cuda_err(ctx, e, "k-NN brute force");
+        }
+    }
+    ctx->knn_stats[0] = q * n;
+    ctx->knn_stats[1] = q * n;     // every pair exact
+    ctx->knn_stats[2] = 0;
+    ctx->knn_stats[3] = 0;
+    cleanup();
+    return PANTHER_OK;
+}
+
 static panther_status knn_entry(panther_ctx* ctx, const pantherpp_vecs* v, const pantherpp_vecs* vc, bool same,
                                 const int32_t* queries, int64_t q, int k, int32_t* out_ids, uint64_t* out_dist2,
                                 int flags) {
@@ -1257,8 +1333,12 @@ static panther_status knn_entry(panther_ctx* ctx, const pantherpp_vecs* v, const
     if (k < 1 || k > KN_KMAX) return set_err(ctx, PANTHER_EINVAL, "k must be in [1, 32]");
     int mode = flags & 0xff;
     if (mode != PANTHER_KNN_BF16_SCREEN && mode != PANTHER_KNN_FP32) return set_err(ctx, PANTHER_EINVAL, "bad flags");
-    if (mode == PANTHER_KNN_BF16_SCREEN && v->D > KN_K - 8)
-        return set_err(ctx, PANTHER_EINVAL, "BF16 screening needs D <= 56 (the norm takes 8 columns)");
+    // wider vectors than the form's screen takes: exact brute force
+    const bool brute = (mode == PANTHER_KNN_BF16_SCREEN && v->D > KN_K - 8) || v->D > KN_K;
+    auto run = [&](const int32_t* qs, int32_t* oi, uint64_t* od) {
+        return brute ? knn_brute_all(ctx, v, vc, same, qs, q, k, oi, od)
+                     : knn_run(ctx, v, vc, same, qs, q, k, oi, od, mode == PANTHER_KNN_FP32);
+    };
     if (q == 0) return PANTHER_OK;
     if (!queries || !out_ids || !out_dist2) return set_err(ctx, PANTHER_EINVAL, "null query or output array");
     cudaSetDevice(ctx->device);
@@ -1271,7 +1351,7 @@ static panther_status knn_entry(panther_ctx* ctx, const pantherpp_vecs* v, const
         uint64_t* dd = (uint64_t*)((char*)buf + qb + ((ib + 15) / 16) * 16);
         int32_t* di = (int32_t*)((char*)buf + qb);
         PCK(ctx, cudaMemcpyAsync(buf, queries, sizeof(int32_t) * q, cudaMemcpyHostToDevice, s));
-        st = knn_run(ctx, v, vc, same, buf, q, k, di, dd, mode == PANTHER_KNN_FP32);
+        st = run(buf, di, dd);
         if (!st) {
             PCK(ctx, cudaMemcpyAsync(out_ids, di, ib, cudaMemcpyDeviceToHost, s));
             PCK(ctx, cudaMemcpyAsync(out_dist2, dd, db, cudaMemcpyDeviceToHost, s));
@@ -1280,7 +1360,7 @@ static panther_status knn_entry(panther_ctx* ctx, const pantherpp_vecs* v, const
         dev_free(ctx, buf);
         return st;
     }
-    return knn_run(ctx, v, vc, same, queries, q, k, out_ids, out_dist2, mode == PANTHER_KNN_FP32);
+    return run(queries, out_ids, out_dist2);
 }
 
 extern "C" panther_status pantherpp_knn(panther_ctx* ctx, const pantherpp_vecs* v, const int32_t* queries, int64_t q,

@@ -143,11 +143,28 @@ def test_knn_host_io_and_errors(pk, small_case):
             assert ids[i].tolist() == rid.tolist() and d2[i].tolist() == rd.tolist()
         with pytest.raises(pk.PantherError):
             P.knn(torch.zeros(1, dtype=torch.int32, device="cuda:0"), 33)
-        P.vectors(60)
-        with pytest.raises(pk.PantherError):            # D > 56 cannot fold the norm
-            P.knn(torch.zeros(1, dtype=torch.int32, device="cuda:0"), 3)
-        ids, d2 = P.knn(torch.zeros(1, dtype=torch.int32, device="cuda:0"), 3, fp32=True)
+        with pytest.raises(pk.PantherError):
+            P.vectors(129)                              # wider than the counting path
         P.sync()
+
+
+@pytest.mark.parametrize("D", [57, 64, 100, 128])
+def test_wide_vectors_theta_and_knn(pk, small_case, D):
+    # D > 56: no room for the exact squared norm in the 64 BF16 columns, so
+    # the BF16 form answers by exact integer brute force; the FP32 form
+    # screens up to D = 64 and brute-forces beyond. theta of D > 64 counts
+    # through the top-k path for k > 64. All must equal the oracle.
+    g, _ = small_case
+    R, T = 200_000, 5
+    th = _oracle_theta(g, 1, R, T, D)
+    q = np.concatenate([np.arange(0, g.n, 17), [5, 5]]).astype(np.int32)
+    out = _vectors(pk, g, 1, R, T, D, queries=q, k=[10, 32], both=True)
+    assert np.array_equal(out["theta"], th)
+    for key, kk in (("bf16_k10", 10), ("fp32_k10", 10), ("bf16_k32", 32), ("fp32_k32", 32)):
+        ids, d2 = out[key]
+        for i, v in enumerate(q):
+            rid, rd = oracle.knn(th, int(v), kk)
+            assert ids[i].tolist() == rid.tolist() and d2[i].tolist() == rd.tolist(), (D, key, i)
 
 
 def test_knn_workload_shape_sampled(pk):

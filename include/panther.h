@@ -319,8 +319,8 @@ PANTHER_API panther_status pantherpp_vecs_view(const pantherpp_vecs* v, const ui
  *          candidate the bound cannot rule out) or PANTHER_KNN_FP32 (FP32
  *          CUDA-core brute force with the same bound and rerank), optionally
  *          | PANTHER_IO_HOST.
- * Vectors wider than a form's screen (D > 56 for BF16, D > 64 for FP32) are
- * answered by exact integer brute force over every candidate instead.
+ * Vectors wider than the BF16 screen's 56 columns (D > 56) take the FP32
+ * screen (64 or 128 columns) under either flag, with the same exact rerank.
  * Every form returns the exact answer. Errors: EINVAL, ENOMEM, ECUDA. */
 PANTHER_API panther_status pantherpp_knn(panther_ctx* ctx, const pantherpp_vecs* v, const int32_t* queries,
                              int64_t q, int k, int32_t* out_ids, uint64_t* out_dist2, int flags);

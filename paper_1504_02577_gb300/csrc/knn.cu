@@ -629,6 +629,8 @@ __global__ void __launch_bounds__(KN_THREADS, 1)
 // |y_hat - y| <= (D+3) 2^-23 (2|a||b| + |b|^2) + 1.
 constexpr int F_T = 128, F_TILE = 32;
 
+// KK: padded vector length, 64 (D <= 64) or 128 (D <= 128)
+template <int KK>
 __global__ void __launch_bounds__(F_T) fp32_kernel(const uint32_t* __restrict__ theta_q,
                                                    const uint32_t* __restrict__ theta_c, bool exclude_self, int D,
                                                    const int32_t* __restrict__ qv,
@@ -638,7 +640,7 @@ __global__ void __launch_bounds__(F_T) fp32_kernel(const uint32_t* __restrict__ 
                                                    const float* __restrict__ cncfv, int64_t npad, int k,
                                                    float2* __restrict__ lists, int32_t* __restrict__ shortlist,
                                                    int32_t* __restrict__ scount, int* __restrict__ overflow) {
-    __shared__ float cb[F_TILE][KN_K];
+    __shared__ float cb[F_TILE][KK];
     __shared__ float cn2[F_TILE], cnr[F_TILE];
     __shared__ int cidx[F_TILE];
     __shared__ float2 lst[F_T * KN_KMAX];
@@ -652,13 +654,13 @@ __global__ void __launch_bounds__(F_T) fp32_kernel(const uint32_t* __restrict__ 
                       lst + threadIdx.x * KN_KMAX, shortlist + (slot < qpad ? slot : 0) * KN_SPLIT * KN_SCAP,
                       overflow + (slot < qpad ? slot : 0), k};
     Row r{__int_as_float(0x7f800000), 0x7fffffff, 0, 0};
-    float a[KN_K];
+    float a[KK];
 #pragma unroll
-    for (int d = 0; d < KN_K; ++d) a[d] = (qid >= 0 && d < D) ? (float)theta_q[(int64_t)qid * D + d] : 0.f;
+    for (int d = 0; d < KK; ++d) a[d] = (qid >= 0 && d < D) ? (float)theta_q[(int64_t)qid * D + d] : 0.f;
     for (int64_t c0 = 0; c0 < npad; c0 += F_TILE) {
         __syncthreads();
-        for (int i = threadIdx.x; i < F_TILE * KN_K; i += F_T) {
-            int c = i / KN_K, d = i % KN_K;
+        for (int i = threadIdx.x; i < F_TILE * KK; i += F_T) {
+            int c = i / KK, d = i % KK;
             int32_t v = cidv[c0 + c];
             cb[c][d] = (v >= 0 && d < D) ? (float)theta_c[(int64_t)v * D + d] : 0.f;
         }
@@ -672,7 +674,7 @@ __global__ void __launch_bounds__(F_T) fp32_kernel(const uint32_t* __restrict__ 
         for (int c = 0; c < F_TILE; ++c) {
             float s = 0.f;
 #pragma unroll
-            for (int d = 0; d < KN_K; ++d) s = fmaf(a[d], cb[c][d], s);
+            for (int d = 0; d < KK; ++d) s = fmaf(a[d], cb[c][d], s);
             float y = fmaf(-2.0f, s, cn2[c]);
             float E = (fmaf(rc.anrm, cnr[c], epsD * cn2[c]) + 1.0f) * 1.0001f;
             if (__fsub_rd(y, E) <= r.thr) r = take_bounded(r, rc, y, E, cidx[c], c0 + c < nexact);
@@ -958,20 +960,6 @@ __global__ void exact_flags_of_queries(const int32_t* __restrict__ queries, int6
     f[i] = (v < 0 || v >= n) ? 1 : exact[v];
 }
 
-// slots of the exact brute-force form: query q0 + i in slot i
-__global__ void brute_slots_kernel(const int32_t* __restrict__ queries, int64_t q0, int64_t qb, int64_t n,
-                                   int32_t* __restrict__ qv, int32_t* __restrict__ qidx, int32_t* __restrict__ slots,
-                                   uint32_t* status) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= qb) return;
-    const int32_t v = queries ? queries[q0 + i] : (int32_t)(q0 + i);
-    const bool bad = v < 0 || v >= n;
-    if (bad) flag_status(status, ST_BAD_QUERY);
-    qv[i] = bad ? -1 : v;
-    qidx[i] = (int32_t)(q0 + i);
-    slots[i] = (int32_t)i;
-}
-
 __global__ void fill_i32(int32_t* p, int64_t n, int32_t v) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
@@ -1064,19 +1052,6 @@ extern "C" panther_status pantherpp_vectors(panther_ctx* ctx, const panther_inde
     x.nexact = last_scan + last_flag;
     x.npad = ceil_div(n, KN_N) * KN_N;
     int32_t* perm = nullptr;
-    if (D > KN_K) {   // wider than either screen: k-NN runs the exact brute force on theta alone
-        dev_free(ctx, flag);
-        dev_free(ctx, pos);
-        dev_free(ctx, maxv);
-        cudaError_t ce = cudaStreamSynchronize(s);
-        if (ce) {
-            flag = pos = nullptr;
-            maxv = nullptr;
-            return fail(cuda_err(ctx, ce, "vector preparation"));
-        }
-        *out = v;
-        return PANTHER_OK;
-    }
     if ((st = dev_alloc(ctx, (void**)&perm, sizeof(int32_t) * x.npad)) ||
         (D <= KN_K - 8 && (st = dev_alloc(ctx, (void**)&x.B, (size_t)x.npad * KN_K * 2))) ||
         (st = dev_alloc(ctx, (void**)&x.cid, sizeof(int32_t) * x.npad)) ||
@@ -1211,7 +1186,12 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* vq, const 
         }
         ctx->launches++;
     } else {
-        fp32_kernel<<<(unsigned)(qpad / F_T), F_T, 0, s>>>(vq->theta, vc->theta, same, v->D, qv, qex, qn, qpad,
+        if (v->D <= KN_K)
+            fp32_kernel<64><<<(unsigned)(qpad / F_T), F_T, 0, s>>>(vq->theta, vc->theta, same, v->D, qv, qex, qn, qpad,
+                                                            x.nexact, x.cid,
+                                                            x.cnrm, x.cncf, x.npad, k, lists, sl, sc, ovf);
+        else
+            fp32_kernel<128><<<(unsigned)(qpad / F_T), F_T, 0, s>>>(vq->theta, vc->theta, same, v->D, qv, qex, qn, qpad,
                                                             x.nexact, x.cid,
                                                             x.cnrm, x.cncf, x.npad, k, lists, sl, sc, ovf);
         ctx->launches++;
@@ -1277,53 +1257,6 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* vq, const 
     return PANTHER_OK;
 }
 
-// Vectors wider than a screen takes (D > 56 for BF16, D > 64 for FP32): the
-// exact k nearest by integer brute force, queries in batches, each query's
-// candidates cut into ranges screened by separate warps (each keeps a sorted
-// k-list across its lanes), then merged per query.
-static panther_status knn_brute_all(panther_ctx* ctx, const pantherpp_vecs* vq, const pantherpp_vecs* vc, bool same,
-                                    const int32_t* queries, int64_t q, int k, int32_t* ids, uint64_t* d2) {
-    cudaStream_t s = ctx->stream;
-    const int64_t n = vc->n;
-    const int64_t nparts = std::max<int64_t>(1, std::min<int64_t>(1024, ceil_div(n, 4096)));
-    const int64_t B = std::min<int64_t>(q, 2048);
-    int32_t *qv = nullptr, *qidx = nullptr, *slots = nullptr, *bid = nullptr;
-    uint64_t* bd = nullptr;
-    auto cleanup = [&]() {
-        dev_free(ctx, qv); dev_free(ctx, qidx); dev_free(ctx, slots); dev_free(ctx, bid); dev_free(ctx, bd);
-    };
-    panther_status st;
-    if ((st = dev_alloc(ctx, (void**)&qv, sizeof(int32_t) * B)) ||
-        (st = dev_alloc(ctx, (void**)&qidx, sizeof(int32_t) * B)) ||
-        (st = dev_alloc(ctx, (void**)&slots, sizeof(int32_t) * B)) ||
-        (st = dev_alloc(ctx, (void**)&bid, sizeof(int32_t) * B * nparts * k)) ||
-        (st = dev_alloc(ctx, (void**)&bd, sizeof(uint64_t) * B * nparts * k))) {
-        cleanup();
-        return st;
-    }
-    for (int64_t q0 = 0; q0 < q; q0 += B) {
-        const int64_t qb = std::min(B, q - q0);
-        brute_slots_kernel<<<(unsigned)ceil_div(qb, 256), 256, 0, s>>>(queries, q0, qb, vq->n, qv, qidx, slots,
-                                                                       ctx->d_status);
-        brute_warp_kernel<<<(unsigned)ceil_div(qb * nparts * 32, 256), 256, 0, s>>>(
-            vq->theta, vc->theta, same, vq->D, n, qv, slots, qb, nparts, k, bid, bd);
-        chunk_merge_kernel<<<(unsigned)std::min<int64_t>(qb, 8 * ctx->num_sms), 256, 0, s>>>(
-            qv, qidx, nullptr, slots, qb, nparts, k, bid, bd, ids, d2);
-        ctx->launches += 3;
-        cudaError_t e = cudaGetLastError();
-        if (e) {
-            cleanup();
-            return cuda_err(ctx, e, "k-NN brute force");
-        }
-    }
-    ctx->knn_stats[0] = q * n;
-    ctx->knn_stats[1] = q * n;     // every pair exact
-    ctx->knn_stats[2] = 0;
-    ctx->knn_stats[3] = 0;
-    cleanup();
-    return PANTHER_OK;
-}
-
 static panther_status knn_entry(panther_ctx* ctx, const pantherpp_vecs* v, const pantherpp_vecs* vc, bool same,
                                 const int32_t* queries, int64_t q, int k, int32_t* out_ids, uint64_t* out_dist2,
                                 int flags) {
@@ -1333,11 +1266,11 @@ static panther_status knn_entry(panther_ctx* ctx, const pantherpp_vecs* v, const
     if (k < 1 || k > KN_KMAX) return set_err(ctx, PANTHER_EINVAL, "k must be in [1, 32]");
     int mode = flags & 0xff;
     if (mode != PANTHER_KNN_BF16_SCREEN && mode != PANTHER_KNN_FP32) return set_err(ctx, PANTHER_EINVAL, "bad flags");
-    // wider vectors than the form's screen takes: exact brute force
-    const bool brute = (mode == PANTHER_KNN_BF16_SCREEN && v->D > KN_K - 8) || v->D > KN_K;
+    // vectors wider than the BF16 screen's 56 columns take the FP32 screen
+    // (64 or 128 columns), with the same exact rerank
+    const bool fp32 = mode == PANTHER_KNN_FP32 || v->D > KN_K - 8;
     auto run = [&](const int32_t* qs, int32_t* oi, uint64_t* od) {
-        return brute ? knn_brute_all(ctx, v, vc, same, qs, q, k, oi, od)
-                     : knn_run(ctx, v, vc, same, qs, q, k, oi, od, mode == PANTHER_KNN_FP32);
+        return knn_run(ctx, v, vc, same, qs, q, k, oi, od, fp32);
     };
     if (q == 0) return PANTHER_OK;
     if (!queries || !out_ids || !out_dist2) return set_err(ctx, PANTHER_EINVAL, "null query or output array");

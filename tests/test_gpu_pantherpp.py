@@ -151,9 +151,9 @@ def test_knn_host_io_and_errors(pk, small_case):
 @pytest.mark.parametrize("D", [57, 64, 100, 128])
 def test_wide_vectors_theta_and_knn(pk, small_case, D):
     # D > 56: no room for the exact squared norm in the 64 BF16 columns, so
-    # the BF16 form answers by exact integer brute force; the FP32 form
-    # screens up to D = 64 and brute-forces beyond. theta of D > 64 counts
-    # through the top-k path for k > 64. All must equal the oracle.
+    # either flag takes the FP32 screen (64 columns up to D = 64, 128 beyond)
+    # with the exact rerank. theta of D > 64 counts through the top-k path
+    # for k > 64. All must equal the oracle.
     g, _ = small_case
     R, T = 200_000, 5
     th = _oracle_theta(g, 1, R, T, D)

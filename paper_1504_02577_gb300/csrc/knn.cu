@@ -645,19 +645,23 @@ __global__ void __launch_bounds__(F_T) fp32_kernel(const uint32_t* __restrict__ 
     __shared__ int cidx[F_TILE];
     __shared__ float2 lst[F_T * KN_KMAX];
     const int64_t slot = (int64_t)blockIdx.x * F_T + threadIdx.x;
+    // candidate range blockIdx.y of gridDim.y (whole 256-candidate tiles)
+    const int64_t nch = gridDim.y, ch = blockIdx.y, nct = npad / 256;
+    const int64_t cbeg = ch * nct / nch * 256, cend = (ch + 1) * nct / nch * 256;
+    const int64_t state = slot * nch + ch;
     const float epsD = (float)(D + 3) * (1.0f / 8388608.0f);
     const int qid = slot < qpad ? qv[slot] : -1;
     // rows with every entry <= 256 give exact FP32 products and partial sums
     // (all integers below 2^24); other pairs carry the bound
     const bool qex = slot < qpad && qexact[slot] != 0;
     const RowConst rc{qid, exclude_self ? qid : -2, qex, 2.0f * epsD * (slot < qpad ? qnrm[slot] : 0.f),
-                      lst + threadIdx.x * KN_KMAX, shortlist + (slot < qpad ? slot : 0) * KN_SPLIT * KN_SCAP,
+                      lst + threadIdx.x * KN_KMAX, shortlist + (slot < qpad ? state : 0) * KN_SPLIT * KN_SCAP,
                       overflow + (slot < qpad ? slot : 0), k};
     Row r{__int_as_float(0x7f800000), 0x7fffffff, 0, 0};
     float a[KK];
 #pragma unroll
     for (int d = 0; d < KK; ++d) a[d] = (qid >= 0 && d < D) ? (float)theta_q[(int64_t)qid * D + d] : 0.f;
-    for (int64_t c0 = 0; c0 < npad; c0 += F_TILE) {
+    for (int64_t c0 = cbeg; c0 < cend; c0 += F_TILE) {
         __syncthreads();
         for (int i = threadIdx.x; i < F_TILE * KK; i += F_T) {
             int c = i / KK, d = i % KK;
@@ -682,11 +686,11 @@ __global__ void __launch_bounds__(F_T) fp32_kernel(const uint32_t* __restrict__ 
     }
     if (slot < qpad) {
         for (int i = 0; i < k; ++i) {
-            lists[(slot * KN_SPLIT) * k + i] = i < r.n ? rc.list[i] : make_float2(0.f, __int_as_float(-1));
-            for (int h = 1; h < KN_SPLIT; ++h) lists[(slot * KN_SPLIT + h) * k + i] = make_float2(0.f, __int_as_float(-1));
+            lists[(state * KN_SPLIT) * k + i] = i < r.n ? rc.list[i] : make_float2(0.f, __int_as_float(-1));
+            for (int h = 1; h < KN_SPLIT; ++h) lists[(state * KN_SPLIT + h) * k + i] = make_float2(0.f, __int_as_float(-1));
         }
-        scount[slot * KN_SPLIT] = r.scount;
-        for (int h = 1; h < KN_SPLIT; ++h) scount[slot * KN_SPLIT + h] = 0;
+        scount[state * KN_SPLIT] = r.scount;
+        for (int h = 1; h < KN_SPLIT; ++h) scount[state * KN_SPLIT + h] = 0;
     }
 }
 
@@ -1084,9 +1088,10 @@ extern "C" panther_status pantherpp_vectors(panther_ctx* ctx, const panther_inde
 // Candidate ranges per query tile: with fewer query tiles than SMs, the
 // candidate tiles are cut into ranges so that tiles x ranges work items fill
 // the GPU; the choice minimises waves x range length, at least KN_STAGES
-// candidate tiles per range. The FP32 form always takes one range.
+// candidate tiles per range (both forms).
 static int64_t knn_ranges(int64_t nqt, int64_t nct, int num_sms, bool fp32) {
-    if (fp32 || nqt >= num_sms) return 1;
+    (void)fp32;   // both forms cut the candidates the same way
+    if (nqt >= num_sms) return 1;
     const int64_t pmax = std::max<int64_t>(1, std::min<int64_t>(nct / KN_STAGES, 256));
     int64_t best = 1;
     double best_cost = (double)ceil_div(nqt, num_sms);
@@ -1187,11 +1192,11 @@ static panther_status knn_run(panther_ctx* ctx, const pantherpp_vecs* vq, const 
         ctx->launches++;
     } else {
         if (v->D <= KN_K)
-            fp32_kernel<64><<<(unsigned)(qpad / F_T), F_T, 0, s>>>(vq->theta, vc->theta, same, v->D, qv, qex, qn, qpad,
+            fp32_kernel<64><<<dim3((unsigned)(qpad / F_T), (unsigned)nch), F_T, 0, s>>>(vq->theta, vc->theta, same, v->D, qv, qex, qn, qpad,
                                                             x.nexact, x.cid,
                                                             x.cnrm, x.cncf, x.npad, k, lists, sl, sc, ovf);
         else
-            fp32_kernel<128><<<(unsigned)(qpad / F_T), F_T, 0, s>>>(vq->theta, vc->theta, same, v->D, qv, qex, qn, qpad,
+            fp32_kernel<128><<<dim3((unsigned)(qpad / F_T), (unsigned)nch), F_T, 0, s>>>(vq->theta, vc->theta, same, v->D, qv, qex, qn, qpad,
                                                             x.nexact, x.cid,
                                                             x.cnrm, x.cncf, x.npad, k, lists, sl, sc, ovf);
         ctx->launches++;

@@ -78,22 +78,22 @@ def _src_hash(*files):
 # unchanged (SHA-256 of the files), else reported as null. The capture and its
 # command are in profiles/.
 NCU_TRAFFIC = {
-    "tables": {"bytes_5M": 4367967232, "sources": {
+    "tables": {"bytes_5M": 4358919680, "sources": {
         "paper_1504_02577_gb300/csrc/graph.cu": "2e1c84b66c7ae7bb7953cb51285365d9aa6479fe7d4feb4baf6db03417cee5a6",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "b1172d07882c5268071533ae62a526e5d6c91192d0bb6e0b227b46cb30599cf0",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "6db187a84a4c2dcdac30fb3fe32dd3fcffd47b6c903c0ac4d1237a48a2c7f72e",
     }},
-    "sample": {"bytes_5M": 8123576832, "sources": {
+    "sample": {"bytes_5M": 8120442880, "sources": {
         "paper_1504_02577_gb300/csrc/sample.cu": "3ae257be8d6b2d9726f406e2f7e6bc67a92c8ee993f6cb3d6a67728924becbf3",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "b1172d07882c5268071533ae62a526e5d6c91192d0bb6e0b227b46cb30599cf0",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "6db187a84a4c2dcdac30fb3fe32dd3fcffd47b6c903c0ac4d1237a48a2c7f72e",
     }},
-    "index": {"bytes_5M": 3669556736, "sources": {
-        "paper_1504_02577_gb300/csrc/index.cu": "f7bb8dd1ec297daaac7c81820b235bbb38303bbfc52351640efe5010c595c8d5",
-        "paper_1504_02577_gb300/csrc/capi.cu": "1a53c25df292c600c1314fc954bbc3d073e4163095578b9d03d33a3337936f32",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "b1172d07882c5268071533ae62a526e5d6c91192d0bb6e0b227b46cb30599cf0",
+    "index": {"bytes_5M": 3670648320, "sources": {
+        "paper_1504_02577_gb300/csrc/index.cu": "2de8cd0b817d605fbc981a0a8b6486428bb0341e105c88205ac1a34a63041d90",
+        "paper_1504_02577_gb300/csrc/capi.cu": "9f7d85e2973fdcf982d51bc9d1f4425bd24f4668696f03bde2d3ba7559a58443",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "6db187a84a4c2dcdac30fb3fe32dd3fcffd47b6c903c0ac4d1237a48a2c7f72e",
     }},
-    "topk": {"bytes_5M": 8260542208, "sources": {
-        "paper_1504_02577_gb300/csrc/topk.cu": "0c9dfda377cdc4813ec9bfa0519d76d15dcc584d6c55d7a208f160b1a6b751fa",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "b1172d07882c5268071533ae62a526e5d6c91192d0bb6e0b227b46cb30599cf0",
+    "topk": {"bytes_5M": 8254882816, "sources": {
+        "paper_1504_02577_gb300/csrc/topk.cu": "af525e4fd7a3e6556b418d6807ea765c7e977f81f7829174b351f01ac1d2b5fd",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "6db187a84a4c2dcdac30fb3fe32dd3fcffd47b6c903c0ac4d1237a48a2c7f72e",
     }},
 }
 

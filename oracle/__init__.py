@@ -73,6 +73,8 @@ def _load():
                 "po_mt_topk_many": ([i64, ci, vp, vp, vp, vp, i64, ci, vp, vp, ci], ci),
                 "po_mt_theta_many": ([i64, ci, vp, vp, vp, vp, i64, ci, vp, ci], ci),
                 "po_mt_knn_many": ([i64, ci, vp, vp, i64, ci, vp, vp, ci], ci),
+                "po_mt_paths_at": ([i64, vp, vp, vp, vp, vp, u64, vp, i64, ci, ci, vp, ci], ci),
+                "po_mt_stream_counts": ([i64, vp, vp, vp, vp, vp, u64, i64, i64, ci, ci, vp, i64, vp, vp, ci], ci),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -165,6 +167,57 @@ def sample_paths(g, seed: int, R: int, T: int, mode: int = PREFIX, r0: int = 0, 
     if rc != 0:
         raise ValueError("po_sample_paths: bad arguments")
     return out
+
+
+def paths_at(g, seed: int, ids, T: int, mode: int = PREFIX, tables=None, threads: int = 1) -> np.ndarray:
+    """Algorithm 3 for the given path ids only: row i of the int32[m][T+1]
+    result is path ids[i], drawn as sample_paths draws it."""
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    thr = al = None
+    if mode == ALIAS:
+        thr, al = tables if tables is not None else alias_tables(g, threads)
+    out = np.empty((ids.shape[0], T + 1), dtype=np.int32)
+    col = g.col if g.m else np.zeros(1, np.int32)
+    w = g.w if g.m else np.zeros(1, np.uint32)
+    if _load().po_mt_paths_at(g.n, _p(g.row_ptr), _p(col), _p(w), _p(thr), _p(al), seed, _p(ids), ids.shape[0],
+                              T, mode, _p(out), max(1, threads)) != 0:
+        raise ValueError("po_mt_paths_at: bad arguments")
+    return out
+
+
+def stream_counts(g, seed: int, r0: int, r1: int, T: int, queries, mode: int = PREFIX, tables=None,
+                  threads: int = 1):
+    """Eq. (4) and |P_v| from their definitions, with no index: paths
+    r0..r1-1 are drawn one by one and dropped. Returns (cnt uint64[nq][n],
+    npaths int64[n]): cnt[i][u] = number of those paths holding both
+    queries[i] and u (u != queries[i]), npaths[v] = number holding v. For path
+    sets too large to keep (memory: threads x (nq + 1) x n x 8 bytes)."""
+    q = np.ascontiguousarray(queries, dtype=np.int32)
+    thr = al = None
+    if mode == ALIAS:
+        thr, al = tables if tables is not None else alias_tables(g, threads)
+    cnt = np.empty((q.shape[0], g.n), dtype=np.uint64)
+    npaths = np.empty(g.n, dtype=np.int64)
+    col = g.col if g.m else np.zeros(1, np.int32)
+    w = g.w if g.m else np.zeros(1, np.uint32)
+    if _load().po_mt_stream_counts(g.n, _p(g.row_ptr), _p(col), _p(w), _p(thr), _p(al), seed, r0, r1, T, mode,
+                                   _p(q), q.shape[0], _p(cnt), _p(npaths), max(1, threads)) != 0:
+        raise ValueError("po_mt_stream_counts: bad arguments (queries must be distinct vertices)")
+    return cnt, npaths
+
+
+def topk_from_counts(cnt_row: np.ndarray, v: int, k: int):
+    """Top-k of one dense count row (Algorithm 1's selection): the u != v with
+    cnt > 0 by (count desc, id asc), padded with (-1, 0)."""
+    c = np.asarray(cnt_row, dtype=np.uint64).copy()
+    c[v] = 0
+    u = np.nonzero(c)[0]
+    order = u[np.lexsort((u, -c[u].astype(np.int64)))][:k]
+    ids = np.full(k, -1, dtype=np.int32)
+    cnt = np.zeros(k, dtype=np.uint64)
+    ids[:order.size] = order
+    cnt[:order.size] = c[order]
+    return ids, cnt
 
 
 def build_index(n: int, paths: np.ndarray, threads: int = 1):

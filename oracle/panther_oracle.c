@@ -18,6 +18,8 @@
  *   po_topk             Algorithm 1 (count each unique co-occurring vertex of
  *                       every path in P_v once), Eq. (4), then top-k
  *   po_theta            Sec. 3.3 feature vector theta(v): the D largest S_RP
+ *   po_stream_counts    Eq. (4) and |P_v| from their definitions, path by path,
+ *                       with no index (for path sets too large to hold)
  *   po_knn              Sec. 3.3 S_RP++ = 1 / ||theta(v_i) - theta(v_j)||
  *
  * Readings of points the paper leaves open (kept identical on both sides):
@@ -331,6 +333,40 @@ int64_t po_topk(int64_t n, int L, const int32_t* paths, const int64_t* off, cons
     return m;
 }
 
+/* Eq. (4) without an index: paths r0..r1-1 are drawn one at a time, exactly
+ * as po_sample_paths_rs draws them, and dropped after use. For every
+ * distinct vertex v of a path npaths[v] += 1 (|P_v|, the length of v's list
+ * in the inverted index). If v is a query (qpos[v] = i >= 0; -1 for every
+ * other vertex), cnt[i*n + u] += 1 for every distinct u != v of the same
+ * path: cnt(v, u) as Eq. (4) defines it, the number of paths holding both v
+ * and u. Adds to cnt and npaths (the caller zeroes them). Returns 0, or -1
+ * on bad input. */
+int po_stream_counts(int64_t n, const int64_t* row_ptr, const int32_t* col, const uint32_t* w,
+                     const uint64_t* thr, const int32_t* alias, const uint64_t* rowsum,
+                     uint64_t seed, int64_t r0, int64_t r1, int T, int mode,
+                     const int32_t* qpos, uint64_t* cnt, int64_t* npaths) {
+    if (n < 1 || T < 0 || T > 65535 || (mode != 0 && mode != 1) || r1 < r0) return -1;
+    int L = T + 1;
+    int32_t* p = (int32_t*)malloc(sizeof(int32_t) * (size_t)L);
+    if (!p) return -1;
+    for (int64_t r = r0; r < r1; ++r) {
+        if (po_sample_paths_rs(n, row_ptr, col, w, thr, alias, rowsum, seed, r, r + 1, T, mode, p)) {
+            free(p);
+            return -1;
+        }
+        for (int i = 0; i < L; ++i) {
+            if (po_seen_before(p, i)) continue;
+            npaths[p[i]] += 1;
+            int32_t q = qpos[p[i]];
+            if (q < 0) continue;
+            for (int j = 0; j < L; ++j)
+                if (p[j] != p[i] && !po_seen_before(p, j)) cnt[(int64_t)q * n + p[j]] += 1;
+        }
+    }
+    free(p);
+    return 0;
+}
+
 /* Sec. 3.3: theta(v) = the D largest S_RP(v, u) over u != v, as counts,
  * descending, zero-padded. */
 void po_theta(int64_t n, int L, const int32_t* paths, const int64_t* off, const int32_t* pid,
@@ -421,10 +457,15 @@ typedef struct {
     uint32_t* cnts;
     const uint32_t* theta;
     uint64_t* d2;
+    const int64_t* rid;       /* JOB_PATHS_AT: path ids */
+    const int32_t* qpos;      /* JOB_STREAM */
+    uint64_t* cnt64;
+    int64_t* npaths;
     int rc;
 } po_job;
 
-enum { JOB_ALIAS, JOB_ROWSUM, JOB_PATHS, JOB_IDX_COUNT, JOB_IDX_FILL, JOB_TOPK, JOB_THETA, JOB_KNN };
+enum { JOB_ALIAS, JOB_ROWSUM, JOB_PATHS, JOB_IDX_COUNT, JOB_IDX_FILL, JOB_TOPK, JOB_THETA, JOB_KNN, JOB_PATHS_AT,
+       JOB_STREAM };
 
 static void* po_job_run(void* arg) {
     po_job* j = (po_job*)arg;
@@ -448,6 +489,15 @@ static void* po_job_run(void* arg) {
         break;
     case JOB_IDX_FILL:
         po_index_range(j->R, j->L, j->paths, j->a, j->b, j->cnt, j->pid);
+        break;
+    case JOB_PATHS_AT:
+        for (int64_t i = j->a; i < j->b && !j->rc; ++i)
+            j->rc = po_sample_paths_rs(j->n, j->row_ptr, j->col, j->w, j->thr_in, j->alias_in, j->rowsum, j->seed,
+                                       j->rid[i], j->rid[i] + 1, j->T, j->mode, j->out + i * (j->T + 1));
+        break;
+    case JOB_STREAM:
+        j->rc = po_stream_counts(j->n, j->row_ptr, j->col, j->w, j->thr_in, j->alias_in, j->rowsum, j->seed, j->a,
+                                 j->b, j->T, j->mode, j->qpos, j->cnt64, j->npaths);
         break;
     case JOB_KNN:
         for (int64_t i = j->a; i < j->b; ++i)
@@ -642,5 +692,101 @@ int po_mt_knn_many(int64_t n, int D, const uint32_t* theta, const int32_t* queri
     po_cut_even(0, q, nthreads, cut);
     int rc = po_run_ranges(&j, nthreads, cut);
     free(cut);
+    return rc;
+}
+
+/* S_v of every row on nthreads row ranges (malloc'd; NULL on failure) */
+static uint64_t* po_mt_row_sums(int64_t n, const int64_t* row_ptr, const uint32_t* w, int nthreads) {
+    int64_t* cut = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nthreads + 1));
+    uint64_t* S = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n);
+    if (!cut || !S) { free(cut); free(S); return NULL; }
+    po_job j;
+    memset(&j, 0, sizeof j);
+    j.kind = JOB_ROWSUM; j.row_ptr = row_ptr; j.w = w; j.S = S;
+    po_cut_rows(n, row_ptr, nthreads, cut);
+    int rc = po_run_ranges(&j, nthreads, cut);
+    free(cut);
+    if (rc) { free(S); return NULL; }
+    return S;
+}
+
+/* Paths ids[0..m) (any order, repeats allowed) as po_sample_paths draws
+ * them: row i of out (int32[m][T+1]) is path ids[i]. */
+int po_mt_paths_at(int64_t n, const int64_t* row_ptr, const int32_t* col, const uint32_t* w, const uint64_t* thr,
+                   const int32_t* alias, uint64_t seed, const int64_t* ids, int64_t m, int T, int mode, int32_t* out,
+                   int nthreads) {
+    if (n < 1 || T < 0 || T > 65535 || (mode != 0 && mode != 1) || m < 0) return -1;
+    for (int64_t i = 0; i < m; ++i) if (ids[i] < 0) return -1;
+    if (nthreads < 1) nthreads = 1;
+    uint64_t* S = po_mt_row_sums(n, row_ptr, w, nthreads);
+    int64_t* cut = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nthreads + 1));
+    if (!S || !cut) { free(S); free(cut); return -1; }
+    po_job j;
+    memset(&j, 0, sizeof j);
+    j.kind = JOB_PATHS_AT; j.n = n; j.row_ptr = row_ptr; j.col = col; j.w = w; j.thr_in = thr; j.alias_in = alias;
+    j.rowsum = S; j.seed = seed; j.T = T; j.mode = mode; j.out = out; j.rid = ids;
+    po_cut_even(0, m, nthreads, cut);
+    int rc = po_run_ranges(&j, nthreads, cut);
+    free(S);
+    free(cut);
+    return rc;
+}
+
+/* po_stream_counts over paths r0..r1-1 for the distinct vertices
+ * queries[0..nq): each thread takes one contiguous range of path ids with
+ * counters of its own, which are then added up (sums do not depend on the
+ * split). cnt is uint64[nq][n] and npaths int64[n], both overwritten. */
+int po_mt_stream_counts(int64_t n, const int64_t* row_ptr, const int32_t* col, const uint32_t* w,
+                        const uint64_t* thr, const int32_t* alias, uint64_t seed, int64_t r0, int64_t r1, int T,
+                        int mode, const int32_t* queries, int64_t nq, uint64_t* cnt, int64_t* npaths, int nthreads) {
+    if (n < 1 || T < 0 || T > 65535 || (mode != 0 && mode != 1) || r1 < r0 || nq < 0) return -1;
+    if (nthreads < 1) nthreads = 1;
+    int32_t* qpos = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    if (!qpos) return -1;
+    for (int64_t v = 0; v < n; ++v) qpos[v] = -1;
+    for (int64_t i = 0; i < nq; ++i) {
+        if (queries[i] < 0 || queries[i] >= n || qpos[queries[i]] >= 0) { free(qpos); return -1; }
+        qpos[queries[i]] = (int32_t)i;
+    }
+    size_t ncnt = (size_t)nq * (size_t)n;
+    uint64_t* S = po_mt_row_sums(n, row_ptr, w, nthreads);
+    int64_t* cut = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nthreads + 1));
+    po_job* jobs = (po_job*)malloc(sizeof(po_job) * (size_t)nthreads);
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    uint64_t* tc = (uint64_t*)malloc(sizeof(uint64_t) * (ncnt > 0 ? ncnt : 1) * (size_t)nthreads);
+    int64_t* tn = (int64_t*)malloc(sizeof(int64_t) * (size_t)n * (size_t)nthreads);
+    int rc = 0;
+    if (!S || !cut || !jobs || !th || !tc || !tn) rc = -1;
+    if (!rc) {
+        memset(tc, 0, sizeof(uint64_t) * (ncnt > 0 ? ncnt : 1) * (size_t)nthreads);
+        memset(tn, 0, sizeof(int64_t) * (size_t)n * (size_t)nthreads);
+        po_cut_even(r0, r1, nthreads, cut);
+        for (int t = 0; t < nthreads; ++t) {
+            memset(&jobs[t], 0, sizeof(po_job));
+            jobs[t].kind = JOB_STREAM; jobs[t].n = n; jobs[t].row_ptr = row_ptr; jobs[t].col = col; jobs[t].w = w;
+            jobs[t].thr_in = thr; jobs[t].alias_in = alias; jobs[t].rowsum = S; jobs[t].seed = seed;
+            jobs[t].T = T; jobs[t].mode = mode; jobs[t].qpos = qpos;
+            jobs[t].a = cut[t]; jobs[t].b = cut[t + 1];
+            jobs[t].cnt64 = tc + (size_t)t * (ncnt > 0 ? ncnt : 1);
+            jobs[t].npaths = tn + (size_t)t * (size_t)n;
+            if (pthread_create(&th[t], NULL, po_job_run, &jobs[t]) != 0) th[t] = 0;
+        }
+        for (int t = 0; t < nthreads; ++t) {
+            if (th[t]) pthread_join(th[t], NULL);
+            else po_job_run(&jobs[t]);
+            if (jobs[t].rc) rc = jobs[t].rc;
+        }
+    }
+    if (!rc) {
+        memset(cnt, 0, sizeof(uint64_t) * ncnt);
+        memset(npaths, 0, sizeof(int64_t) * (size_t)n);
+        for (int t = 0; t < nthreads; ++t) {
+            const uint64_t* c = tc + (size_t)t * (ncnt > 0 ? ncnt : 1);
+            const int64_t* m = tn + (size_t)t * (size_t)n;
+            for (size_t i = 0; i < ncnt; ++i) cnt[i] += c[i];
+            for (int64_t v = 0; v < n; ++v) npaths[v] += m[v];
+        }
+    }
+    free(qpos); free(S); free(cut); free(jobs); free(th); free(tc); free(tn);
     return rc;
 }

@@ -163,8 +163,10 @@ PANTHER_API panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int6
  * c = Uniform[0,deg) from (x0,x1), the same words and rejections as PREFIX, so
  * its paths equal PREFIX paths of the same graph with every weight 1. All
  * realise Eq. 3 exactly and the paths are reproducible bit for bit.
- *   R in [1, 2^31-1], T in [1, 127], mode PREFIX, ALIAS or UNWEIGHTED (the
- *   graph must have been built with that mode).
+ *   R in [1, 2^32-1], T in [1, 127], mode PREFIX, ALIAS or UNWEIGHTED (the
+ *   graph must have been built with that mode). The index stores path ids as
+ *   uint32; at 32 B of row and 4 B of index per vertex of each path, 2^32
+ *   paths already take more than one GPU's memory.
  * Rows live on the device as int32[R][stride], stride = 8, 16, 32, 64 or 128
  * (the smallest that holds T+1); entries past T+1 are -1.
  * Errors: EINVAL, ENOMEM, ECUDA. */
@@ -192,7 +194,8 @@ PANTHER_API panther_status panther_paths_info(const panther_paths* p, int64_t* n
 
 /* Build the inverted index P_v = { r : v in p_r } with a device LSD radix
  * sort of (vertex, path id) pairs. A path that visits v several times is
- * listed once. Layout: off int64[n+1], pid int32[nnz]; P_v is
+ * listed once. Layout: off int64[n+1], pid uint32[nnz] (ids reach 2^32 - 2;
+ * a signed 32-bit view shows ids from 2^31 up as negative); P_v is
  * pid[off[v] .. off[v+1]) in ascending path id.
  * Memory: one sort over all pairs needs about 16 B per pair (+ 5% for tile
  * counts) of temporary device memory next to the result (4 B per pair). When
@@ -214,7 +217,7 @@ PANTHER_API panther_status panther_set_index_budget(panther_ctx* ctx, int64_t by
  * owns a fixed share of the GPU and accounts for every byte itself, or a
  * latency-bound loop where an allocation could synchronise the device).
  * Same result as panther_build_index: P_v = pid[off[v] .. off[v+1]),
- * ascending. The caller passes dev_off (int64[n+1]) and dev_pid (int32,
+ * ascending. The caller passes dev_off (int64[n+1]) and dev_pid (uint32,
  * pid_capacity >= R*(T+1) entries); *nnz receives the number of pairs.
  * Temporary buffers come from one static device array of about 86 MiB that
  * every GPU loading the library reserves until the process exits; R*(T+1)
@@ -228,10 +231,10 @@ PANTHER_API panther_status panther_set_index_budget(panther_ctx* ctx, int64_t by
  * before it on that stream has finished.
  * Errors: EINVAL, EOVERFLOW, ECUDA. */
 PANTHER_API panther_status panther_build_index_noalloc(panther_ctx* ctx, const panther_paths* p, int64_t* dev_off,
-                                                       int32_t* dev_pid, int64_t pid_capacity, int64_t* nnz);
+                                                       uint32_t* dev_pid, int64_t pid_capacity, int64_t* nnz);
 
 PANTHER_API panther_status panther_index_view(const panther_index* ix, const int64_t** dev_off,
-                                  const int32_t** dev_pid, int64_t* n, int64_t* nnz);
+                                  const uint32_t** dev_pid, int64_t* n, int64_t* nnz);
 
 /* ---------------------------------------------- Algorithm 1, Eq. (4) --- */
 

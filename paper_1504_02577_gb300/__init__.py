@@ -226,7 +226,7 @@ def panther_paths_info(p: int):
 def panther_build_index_noalloc(ctx: int, p: int, dev_off, dev_pid, pid_capacity: int) -> int:
     """Index into caller buffers with no device allocation; returns nnz.
 
-    dev_pid must hold pid_capacity int32 elements (the library writes up to
+    dev_pid must hold pid_capacity 32-bit elements (uint32 path ids; the library writes up to
     R*(T+1) of them and trusts pid_capacity) and dev_off n+1 int64 elements,
     n taken from the paths handle; both are checked here, before the call. A
     NULL handle (p = 0) skips the dev_off check: the library refuses it."""
@@ -517,6 +517,9 @@ class Panther:
         return self.h.index
 
     def index_tensors(self):
+        """(off int64[n+1], pid[nnz]) copies; pid holds uint32 path ids in
+        int32 storage (ids from 2^31 up read negative: widen with
+        ``pid.to(torch.int64) & 0xFFFFFFFF``)."""
         torch = self.torch
         off, pid, n, nnz = panther_index_view(self.h.index)
         with torch.cuda.stream(self.stream):

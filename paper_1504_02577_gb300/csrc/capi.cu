@@ -195,7 +195,7 @@ panther_status panther_paths_info(const panther_paths* p, int64_t* n, int64_t* R
     return PANTHER_OK;
 }
 
-panther_status panther_index_view(const panther_index* ix, const int64_t** dev_off, const int32_t** dev_pid,
+panther_status panther_index_view(const panther_index* ix, const int64_t** dev_off, const uint32_t** dev_pid,
                                   int64_t* n, int64_t* nnz) {
     if (!ix) return PANTHER_EINVAL;
     if (dev_off) *dev_off = ix->off;

@@ -10,7 +10,7 @@
 //   32 i64      n          40 i64 R
 //   48 i64      r0 (paths) or nnz (index)
 //   56 u64      seed (paths) or 0
-// paths: int32[R][stride]; index: int64 off[n+1], int32 pid[nnz].
+// paths: int32[R][stride]; index: int64 off[n+1], uint32 pid[nnz].
 // Arrays move through a pinned staging buffer in chunks. A loaded index is
 // validated on the device (offsets monotone from 0 to nnz, path ids below R)
 // before it is handed out, so a damaged file is refused rather than read out
@@ -91,7 +91,7 @@ panther_status read_header(panther_ctx* ctx, FILE* f, const char* magic, FileHea
 }
 
 // offsets start at 0, never decrease, end at nnz; path ids in [0, R)
-__global__ void check_index_kernel(const int64_t* __restrict__ off, int64_t n, const int32_t* __restrict__ pid,
+__global__ void check_index_kernel(const int64_t* __restrict__ off, int64_t n, const uint32_t* __restrict__ pid,
                                    int64_t nnz, int64_t R, uint32_t* status) {
     const int64_t st = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += st) {
@@ -101,7 +101,7 @@ __global__ void check_index_kernel(const int64_t* __restrict__ off, int64_t n, c
         if (bad) flag_status(status, ST_BAD_INDEX);
     }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += st)
-        if (pid[i] < 0 || (int64_t)pid[i] >= R) flag_status(status, ST_BAD_INDEX);
+        if ((int64_t)pid[i] >= R) flag_status(status, ST_BAD_INDEX);
 }
 
 }  // namespace
@@ -139,7 +139,7 @@ panther_status panther_load_paths(panther_ctx* ctx, const char* path, panther_pa
     panther_status st = read_header(ctx, fl.f, "PNTHPATH", &hd);
     if (st) return st;
     if (hd.T < 1 || hd.T > (uint32_t)MAX_T || hd.L != hd.T + 1 || hd.stride != (uint32_t)path_stride((int)hd.L) || hd.n < 1 ||
-        hd.n >= (int64_t(1) << 31) || hd.R < 1 || hd.R > 0x7fffffffLL || hd.x < 0 ||
+        hd.n >= (int64_t(1) << 31) || hd.R < 1 || hd.R > 0xffffffffLL || hd.x < 0 ||
         (hd.mode != PANTHER_MODE_PREFIX && hd.mode != PANTHER_MODE_ALIAS && hd.mode != PANTHER_MODE_UNWEIGHTED))
         return set_err(ctx, PANTHER_EINVAL, "inconsistent paths checkpoint header");
     panther_paths* p = new panther_paths();
@@ -188,8 +188,8 @@ panther_status panther_load_index(panther_ctx* ctx, const char* path, panther_in
     FileHeader hd;
     panther_status st = read_header(ctx, fl.f, "PNTHINDX", &hd);
     if (st) return st;
-    if (hd.n < 1 || hd.n >= (int64_t(1) << 31) || hd.R < 1 || hd.R > 0x7fffffffLL || hd.x < 0 ||
-        hd.x > hd.R * 32)
+    if (hd.n < 1 || hd.n >= (int64_t(1) << 31) || hd.R < 1 || hd.R > 0xffffffffLL || hd.x < 0 ||
+        hd.x > hd.R * (MAX_T + 1))
         return set_err(ctx, PANTHER_EINVAL, "inconsistent index checkpoint header");
     panther_index* ix = new panther_index();
     ix->ctx = ctx;

@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(IX_T, 2) scatter_kernel(Src s, int shift, int 
 #pragma unroll
     for (int k = 0; k < IX_ROUNDS; ++k) {
         const int64_t i = base + k * 32 + lane;
-        val[k] = s.first ? (int32_t)(s.r0 + i / s.stride) : (((okmask >> k) & 1u) ? __ldg(s.vals + i) : 0);
+        val[k] = s.first ? (int32_t)(uint32_t)(s.r0 + i / s.stride) : (((okmask >> k) & 1u) ? __ldg(s.vals + i) : 0);
     }
 #pragma unroll
     for (int k = 0; k < IX_ROUNDS; ++k) {
@@ -266,11 +266,11 @@ __global__ void __launch_bounds__(IX_T) vcount_kernel(Src s, unsigned long long*
 // stays ascending
 __global__ void place_kernel(const int32_t* __restrict__ keys, const int32_t* __restrict__ vals, int64_t cn,
                              const int64_t* __restrict__ coff, const int64_t* __restrict__ cur,
-                             int32_t* __restrict__ pid) {
+                             uint32_t* __restrict__ pid) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cn) return;
     const int32_t v = keys[i];
-    pid[cur[v] + (i - coff[v])] = vals[i];
+    pid[cur[v] + (i - coff[v])] = (uint32_t)vals[i];
 }
 
 __global__ void advance_kernel(const int64_t* __restrict__ coff, int64_t n, int64_t* __restrict__ cur) {
@@ -472,7 +472,7 @@ extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_pa
         ctx->launches++;
         if ((st = index_classes(ctx, ix))) return fail(st);
         // keep the final value array as pid; release everything else
-        ix->pid = iv;
+        ix->pid = (uint32_t*)iv;
         if (iv == vA) vA = nullptr; else vB = nullptr;
     } else {
         // chunks of `rows` path rows: |P_v| of every vertex first (the
@@ -579,7 +579,7 @@ std::mutex na_mu;
 }  // namespace
 
 extern "C" panther_status panther_build_index_noalloc(panther_ctx* ctx, const panther_paths* p, int64_t* dev_off,
-                                                      int32_t* dev_pid, int64_t pid_capacity, int64_t* nnz) {
+                                                      uint32_t* dev_pid, int64_t pid_capacity, int64_t* nnz) {
     if (!ctx || !p || !dev_off || !dev_pid || !nnz) return PANTHER_EINVAL;
     *nnz = 0;
     const int64_t pairs = p->R * p->L;
@@ -639,7 +639,7 @@ extern "C" panther_status panther_build_index_noalloc(panther_ctx* ctx, const pa
             PCK(ctx, cudaMemcpyAsync(&count, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
             PCK(ctx, cudaStreamSynchronize(s));
         }
-        int32_t* outv = last ? dev_pid : ov;     // the final pass writes the caller's pid array
+        int32_t* outv = last ? (int32_t*)dev_pid : ov;     // the final pass writes the caller's pid array
         if (src.first && src.stride > 32)
             scatter_kernel<true><<<(unsigned)ntiles, IX_T, SC_SMEM, s>>>(src, pass * rb, radix, ntiles, offs, ok, outv);
         else

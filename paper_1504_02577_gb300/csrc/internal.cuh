@@ -84,7 +84,7 @@ struct panther_index {
     int64_t n = 0, nnz = 0;
     int64_t R = 0;                   // rows of the paths its ids refer to
     int64_t* off = nullptr;          // [n+1]
-    int32_t* pid = nullptr;          // [nnz]
+    uint32_t* pid = nullptr;         // [nnz] path ids (row numbers of the path set, R <= 2^32 - 1)
     uint8_t* cls = nullptr;          // [n] path_code(|P_v|) (|P_v| bounds any count with v)
     int64_t* cls_hist = nullptr;     // [256] vertices per code
 };

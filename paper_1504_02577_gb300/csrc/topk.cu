@@ -28,8 +28,18 @@
 namespace {
 
 constexpr uint64_t EMPTY = ~0ull;
+// path ids are unsigned 32-bit (R <= 2^32 - 1, so no valid id is all ones);
+// lanes without a path pass NO_PATH, which every reader rejects with r >= R
+constexpr uint32_t NO_PATH = 0xffffffffu;
 constexpr int WSLOTS = 512;      // warp-tier table slots
 constexpr int WCAP = 256;        // warp-tier candidate bound
+// A query's own path count bounds the work of the tier that takes it: one
+// warp (warp tier) or one CTA (CTA tiers) walks every path of P_v, so a query
+// with few candidates but more paths than these (a small graph with a large
+// R) goes to a wider tier, and beyond CTA_MAX_NP to the hub tier, which
+// splits P_v over many CTAs.
+constexpr int64_t WARP_MAX_NP = int64_t(1) << 16;
+constexpr int64_t CTA_MAX_NP = int64_t(1) << 20;
 constexpr int KMAX = 64;
 constexpr int WCHUNK = 16;       // warp-tier queries fetched per atomic
 
@@ -369,7 +379,7 @@ struct PathsRef {
     int64_t R;
     int L;
     const int64_t* off;
-    const int32_t* pid;
+    const uint32_t* pid;
     int64_t n;
     const uint8_t* cls;   // path_code(|P_u|) per vertex
 };
@@ -377,11 +387,11 @@ struct PathsRef {
 // insert the distinct vertices u != v of path r into the table (with thr > 0
 // only the u with cls[u] >= thr)
 template <int STRIDE, bool SHARED>
-__device__ __forceinline__ bool insert_path(const PathsRef& P, int32_t r, int32_t v, unsigned long long* tab,
+__device__ __forceinline__ bool insert_path(const PathsRef& P, uint32_t r, int32_t v, unsigned long long* tab,
                                             uint32_t nslots, uint32_t thr = 0) {
-    if ((uint32_t)r >= (uint64_t)P.R) return false;   // corrupt index entry: the caller flags it, nothing is read
+    if (r >= (uint64_t)P.R) return false;             // corrupt index entry: the caller flags it, nothing is read
     int32_t x[STRIDE];
-    const int4* src = (const int4*)(P.rows + (int64_t)r * STRIDE);
+    const int4* src = (const int4*)(P.rows + (uint64_t)r * STRIDE);
 #pragma unroll
     for (int k = 0; k < STRIDE / 4; ++k) {
         int4 q = __ldg(src + k);
@@ -456,9 +466,9 @@ __global__ void __launch_bounds__(256, NARROW ? 3 : 2) lane_kernel(PathsRef P, c
         int32_t row[LANE_NP][8];
 #pragma unroll
         for (int i = 0; i < LANE_NP; ++i) {
-            int32_t r = i < np ? P.pid[a + i] : -1;
-            if (r >= 0 && (int64_t)r < P.R) {
-                const int4* src = (const int4*)(P.rows + (int64_t)r * 8);
+            const uint32_t r = i < np ? P.pid[a + i] : NO_PATH;
+            if (r < (uint64_t)P.R) {
+                const int4* src = (const int4*)(P.rows + (uint64_t)r * 8);
                 int4 x = __ldg(src), y = __ldg(src + 1);
                 row[i][0] = x.x; row[i][1] = x.y; row[i][2] = x.z; row[i][3] = x.w;
                 row[i][4] = y.x; row[i][5] = y.y; row[i][6] = y.z; row[i][7] = y.w;
@@ -557,18 +567,18 @@ __device__ __forceinline__ bool hash_add_conv(unsigned long long* tab, uint32_t 
 // it) and if it is not v; with thr > 0 only the u with cls[u] >= thr.
 // Returns false if a table ran out of slots. Every lane must call it.
 template <int STRIDE>
-__device__ __forceinline__ bool insert_paths_warp(const PathsRef& P, int32_t r, int32_t v, unsigned long long* tab,
+__device__ __forceinline__ bool insert_paths_warp(const PathsRef& P, uint32_t r, int32_t v, unsigned long long* tab,
                                                   uint32_t nslots, bool active, uint32_t thr) {
     constexpr int NR = STRIDE / 32;
     const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
-    active &= (uint32_t)r < (uint64_t)P.R;
+    active &= r < (uint64_t)P.R;
     unsigned pend = __ballot_sync(0xffffffffu, active);
     bool ok = true;
     while (pend) {                                        // warp-uniform
         const int src = __ffs(pend) - 1;
         pend &= pend - 1;
-        const int32_t rr = __shfl_sync(0xffffffffu, r, src);
-        const int32_t* row = P.rows + (int64_t)rr * STRIDE;
+        const uint32_t rr = __shfl_sync(0xffffffffu, r, src);
+        const int32_t* row = P.rows + (uint64_t)rr * STRIDE;
         int32_t y[NR];
 #pragma unroll
         for (int m = 0; m < NR; ++m) y[m] = __ldg(row + m * 32 + lane);
@@ -588,15 +598,15 @@ __device__ __forceinline__ bool insert_paths_warp(const PathsRef& P, int32_t r, 
     return ok;
 }
 
-// insert the distinct vertices u != v of path r (lanes with active == false pass r = -1);
+// insert the distinct vertices u != v of path r (lanes with active == false pass NO_PATH);
 // with thr > 0 only the u with cls[u] >= thr
 template <int STRIDE>
-__device__ __forceinline__ bool insert_path_conv(const PathsRef& P, int32_t r, int32_t v, unsigned long long* tab,
+__device__ __forceinline__ bool insert_path_conv(const PathsRef& P, uint32_t r, int32_t v, unsigned long long* tab,
                                                  uint32_t nslots, bool active, uint32_t thr = 0) {
     if constexpr (STRIDE > 32) return insert_paths_warp<STRIDE>(P, r, v, tab, nslots, active, thr);
-    active &= (uint32_t)r < (uint64_t)P.R;
+    active &= r < (uint64_t)P.R;
     int32_t x[STRIDE];
-    const int4* src = (const int4*)(P.rows + (int64_t)(active ? r : 0) * STRIDE);
+    const int4* src = (const int4*)(P.rows + (uint64_t)(active ? r : 0u) * STRIDE);
 #pragma unroll
     for (int k = 0; k < STRIDE / 4; ++k) {
         int4 q = active ? __ldg(src + k) : make_int4(-1, -1, -1, -1);
@@ -684,10 +694,10 @@ __global__ void __launch_bounds__(256) group_kernel(PathsRef P, const int32_t* _
         }
         uint32_t x[8];
         {
-            const int32_t r = (int)gl < np ? P.pid[a + gl] : -1;
+            const uint32_t r = (int)gl < np ? P.pid[a + gl] : NO_PATH;
             int4 q0 = make_int4(-1, -1, -1, -1), q1 = q0;
-            if (r >= 0 && (int64_t)r < P.R) {
-                const int4* src = (const int4*)(P.rows + (int64_t)r * 8);
+            if (r < (uint64_t)P.R) {
+                const int4* src = (const int4*)(P.rows + (uint64_t)r * 8);
                 q0 = __ldg(src);
                 q1 = __ldg(src + 1);
             }
@@ -799,7 +809,8 @@ __global__ void __launch_bounds__(256) classify_kernel(const int32_t* __restrict
                     else if (np <= 8 && np <= group_max) t = 4;
                     else if (np <= 16 && np <= group_max) t = 5;
                     else if (np <= 32 && np <= group_max) t = 6;
-                    else t = cap <= WCAP ? 0 : (cap <= ccap ? 1 : (cap <= ccap_big ? 7 : 2));
+                    else if (np > CTA_MAX_NP) t = 2;
+                    else t = (cap <= WCAP && np <= WARP_MAX_NP) ? 0 : (cap <= ccap ? 1 : (cap <= ccap_big ? 7 : 2));
                 }
             }
             if (t < 0) {
@@ -938,7 +949,7 @@ __device__ void cta_query(const PathsRef& P, int32_t v, int64_t qi, unsigned lon
     for (int64_t base = a + (threadIdx.x & ~31u); base < b; base += blockDim.x) {   // warp-uniform
         const int64_t e = base + (threadIdx.x & 31);
         const bool act = e < b;
-        ok &= insert_path_conv<STRIDE>(P, act ? P.pid[e] : -1, v, tab, nslots, act);
+        ok &= insert_path_conv<STRIDE>(P, act ? P.pid[e] : NO_PATH, v, tab, nslots, act);
     }
     if (!ok) flag_status(status, ST_HASH_FULL);
     __syncthreads();
@@ -957,7 +968,7 @@ __device__ void warp_query(const PathsRef& P, int32_t v, int64_t qi, unsigned lo
     for (int64_t base = a; base < b; base += 32) {                   // warp-uniform trip count
         const int64_t e = base + lane;
         const bool act = e < b;
-        ok &= insert_path_conv<STRIDE>(P, act ? P.pid[e] : -1, v, tab, ns, act);
+        ok &= insert_path_conv<STRIDE>(P, act ? P.pid[e] : NO_PATH, v, tab, ns, act);
     }
     if (!ok) flag_status(status, ST_HASH_FULL);
     __syncwarp();
@@ -1004,11 +1015,11 @@ __device__ __forceinline__ bool hash_add32_conv(uint32_t* tab, uint32_t nslots, 
 }
 
 template <int STRIDE>
-__device__ __forceinline__ bool insert_path32(const PathsRef& P, int32_t r, int32_t v, uint32_t* tab, uint32_t nslots,
+__device__ __forceinline__ bool insert_path32(const PathsRef& P, uint32_t r, int32_t v, uint32_t* tab, uint32_t nslots,
                                               int cb, bool active) {
-    active &= (uint32_t)r < (uint64_t)P.R;
+    active &= r < (uint64_t)P.R;
     int32_t x[STRIDE];
-    const int4* src = (const int4*)(P.rows + (int64_t)(active ? r : 0) * STRIDE);
+    const int4* src = (const int4*)(P.rows + (uint64_t)(active ? r : 0u) * STRIDE);
 #pragma unroll
     for (int k = 0; k < STRIDE / 4; ++k) {
         int4 q = active ? __ldg(src + k) : make_int4(-1, -1, -1, -1);
@@ -1095,7 +1106,7 @@ __device__ bool warp_query32(const PathsRef& P, int32_t v, int64_t qi, uint32_t*
     for (int64_t base = a; base < b; base += 32) {                   // warp-uniform trip count
         const int64_t e = base + lane;
         const bool act = e < b;
-        ok &= insert_path32<STRIDE>(P, act ? P.pid[e] : -1, v, tab, ns, cb, act);
+        ok &= insert_path32<STRIDE>(P, act ? P.pid[e] : NO_PATH, v, tab, ns, cb, act);
     }
     if (!ok) flag_status(status, ST_HASH_FULL);
     __syncwarp();
@@ -1204,7 +1215,7 @@ __global__ void __launch_bounds__(1024, 1) single_kernel(PathsRef P, const int32
         for (int64_t base = P.off[v] + (threadIdx.x & ~31u); base < P.off[v + 1]; base += blockDim.x) {
             const int64_t e = base + (threadIdx.x & 31);
             const bool act = e < P.off[v + 1];
-            ok &= insert_paths_warp<STRIDE>(P, act ? P.pid[e] : -1, (int32_t)v, gtab, gslots, act, 0);
+            ok &= insert_paths_warp<STRIDE>(P, act ? P.pid[e] : NO_PATH, (int32_t)v, gtab, gslots, act, 0);
         }
     } else {
         for (int64_t e = P.off[v] + threadIdx.x; e < P.off[v + 1]; e += blockDim.x)
@@ -1271,7 +1282,7 @@ __global__ void g_count_kernel(PathsRef P, const int32_t* __restrict__ queries, 
         for (int64_t base = a + (threadIdx.x & ~31u); base < b; base += blockDim.x) {   // warp-uniform
             const int64_t e = base + (threadIdx.x & 31);
             const bool act = e < b;
-            ok &= insert_paths_warp<STRIDE>(P, act ? P.pid[e] : -1, v, tab, G.tab_n[g], act, thr);
+            ok &= insert_paths_warp<STRIDE>(P, act ? P.pid[e] : NO_PATH, v, tab, G.tab_n[g], act, thr);
         }
     } else {
         for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x)
@@ -1304,7 +1315,7 @@ __global__ void __launch_bounds__(256) g_count_warp_kernel(PathsRef P, const int
         for (int64_t base = a; base < b; base += 32) {            // warp-uniform
             const int64_t e = base + lane;
             const bool act = e < b;
-            ok &= insert_paths_warp<STRIDE>(P, act ? P.pid[e] : -1, v, tab, ns, act, thr);
+            ok &= insert_paths_warp<STRIDE>(P, act ? P.pid[e] : NO_PATH, v, tab, ns, act, thr);
         }
     } else {
         for (int64_t e = a + lane; e < b; e += 32) ok &= insert_path<STRIDE, false>(P, P.pid[e], v, tab, ns, thr);
@@ -1476,7 +1487,7 @@ __global__ void __launch_bounds__(512) b_scatter_kernel(PathsRef P, const int32_
     for (int64_t base = a + (threadIdx.x & ~31u); base < b; base += blockDim.x) {   // warp-uniform
         const int64_t e = base + (threadIdx.x & 31);
         const bool act = e < b;
-        ok &= insert_path_conv<STRIDE>(P, act ? P.pid[e] : -1, v, tab, nslots, act, thr);
+        ok &= insert_path_conv<STRIDE>(P, act ? P.pid[e] : NO_PATH, v, tab, nslots, act, thr);
     }
     if (!ok) flag_status(status, ST_HASH_FULL);
     __syncthreads();

@@ -1110,19 +1110,44 @@ __device__ bool warp_query32(const PathsRef& P, int32_t v, int64_t qi, uint32_t*
     }
     if (!ok) flag_status(status, ST_HASH_FULL);
     __syncwarp();
-    // top-k: compact the filled slots in place (at most 64: one sort), else offer them
-    int filled = 0;
-    for (uint32_t base = 0; base < ns; base += 32)
-        filled += __popc(__ballot_sync(0xffffffffu, tab[base + lane] != EMPTY32));
+    // top-k: the slots with count >= c* are compacted in place and sorted
+    // once. c* = 1 when at most 64 slots are filled; otherwise the k-th
+    // largest count, found bit by bit (counts are below 2^cb) by counting the
+    // slots at or above a threshold on a register copy of the table. More
+    // than 64 slots at or above c* (many ties at c*): every slot is offered to
+    // a running list instead.
+    constexpr int NR = WSLOTS / 32;
+    const uint32_t cmask = (1u << cb) - 1u;
+    uint32_t wv[NR];
+#pragma unroll
+    for (int g = 0; g < NR; ++g) wv[g] = (uint32_t)g * 32u < ns ? tab[g * 32 + lane] : EMPTY32;
+    auto at_least = [&](uint32_t c) {
+        int s = 0;
+#pragma unroll
+        for (int g = 0; g < NR; ++g)
+            s += __popc(__ballot_sync(0xffffffffu, wv[g] != EMPTY32 && (wv[g] & cmask) >= c));
+        return s;
+    };
+    uint32_t cstar = 1;
+    int filled = at_least(1);
+    if (filled > 64) {
+        cstar = 0;
+        for (int bit = cb - 1; bit >= 0; --bit)                       // warp-uniform
+            if (at_least(cstar | (1u << bit)) >= o.k) cstar |= 1u << bit;
+        filled = at_least(cstar);
+    }
     WarpTopK t;
     if (filled > 64) {
-        for (uint32_t base = 0; base < ns; base += 32) t.offer(widen_score(slot_score32(tab[base + lane], cb), cb), o.k);
+#pragma unroll
+        for (int g = 0; g < NR; ++g)
+            if ((uint32_t)g * 32u < ns) t.offer(widen_score(slot_score32(wv[g], cb), cb), o.k);
     } else {
         int pos = 0;
-        for (uint32_t base = 0; base < ns; base += 32) {
-            const uint32_t sc = slot_score32(tab[base + lane], cb);
-            const unsigned m = __ballot_sync(0xffffffffu, sc != 0);
-            if (sc) tab[pos + __popc(m & lt)] = sc;   // every lane read its slot before the ballot
+#pragma unroll
+        for (int g = 0; g < NR; ++g) {
+            const bool pass = wv[g] != EMPTY32 && (wv[g] & cmask) >= cstar;
+            const unsigned m = __ballot_sync(0xffffffffu, pass);
+            if (pass) tab[pos + __popc(m & lt)] = slot_score32(wv[g], cb);   // the table is in registers
             pos += __popc(m);
         }
         __syncwarp();
@@ -1577,6 +1602,13 @@ __global__ void fill_empty_kernel(unsigned long long* p, int64_t n) {
     for (; i < n; i += st) p[i] = EMPTY;
 }
 
+// slots of a hub device table: twice the candidate bound, rounded up to a
+// multiple of lo (a multiple of 32: the selection reads whole warps of slots)
+static uint32_t table_slots(int64_t bound, uint32_t lo) {
+    const int64_t x = std::max<int64_t>(2 * bound, lo);
+    return (uint32_t)((x + lo - 1) / lo * lo);
+}
+
 uint32_t pow2_at_least(int64_t x, uint32_t lo = 1024) {
     uint32_t p = lo;
     while ((int64_t)p < x && p < (1u << 31)) p <<= 1;
@@ -1771,7 +1803,7 @@ static panther_status hub_tables(panther_ctx* ctx, const PathsRef& P, const int3
         while (pos < hubs.size()) {
             const HubQuery& h = hubs[pos];
             // k > 64 sends every query here: small ones get small tables
-            uint32_t slots = pow2_at_least(hub_bound(P, h, above) * 2, k > KMAX ? 64u : 1024u);
+            uint32_t slots = table_slots(hub_bound(P, h, above), k > KMAX ? 64u : 1024u);
             if (!rq.empty() && used + slots > budget_slots) break;
             rq.push_back(h.qi);
             rt.push_back(h.thr);

@@ -45,6 +45,17 @@ __device__ __forceinline__ int32_t load_raw(const Src& s, int64_t i) {
 // is item i a pair (pass 0: inside the path, first occurrence in its row)?
 // Every lane of the warp must call it (one __match_any_sync in pass 0).
 __device__ __forceinline__ bool item_ok(const Src& s, int64_t i, int32_t x) {
+    if (s.first && s.stride == 8) {
+        // 8-entry rows: compare with the (at most 7) earlier entries of the row
+        const unsigned lane = threadIdx.x & 31, j8 = lane & 7u;
+        bool dup = false;
+#pragma unroll
+        for (unsigned o = 1; o < 8; ++o) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            dup |= j8 >= o && y == x;
+        }
+        return i < s.R * s.stride && (int)(i & 7) < s.L && !dup;
+    }
     if (s.first) {
         const unsigned lane = threadIdx.x & 31;
         const unsigned peers = __match_any_sync(0xffffffffu, x);
@@ -139,12 +150,20 @@ __global__ void __launch_bounds__(IX_T, 2) scatter_kernel(Src s, int shift, int 
         okmask &= ~long_row_repeats(s, base, xk);
     }
     __syncthreads();
-    // phase 1: per-warp digit counts and each item's rank within its warp
+    // phase 1: per-warp digit counts and each item's rank within its warp.
+    // The lanes holding the same digit: one ballot per digit bit, each kept or
+    // inverted by the lane's own bit (no match instruction on the MIO pipe).
+    const int rb = 31 - __clz(radix);
 #pragma unroll
     for (int k = 0; k < IX_ROUNDS; ++k) {
         bool ok = (okmask >> k) & 1u;
         uint32_t d = ok ? ((key[k] >> shift) & (radix - 1)) : 0xffffffffu;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned peers = __ballot_sync(0xffffffffu, ok);
+        for (int b = 0; b < rb; ++b) {                     // warp-uniform
+            const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bb : ~bb;
+        }
+        if (!ok) peers = 0;
         unsigned before = ok ? wc[w][d] : 0u;
         uint32_t r = before + __popc(peers & lt);
         if (k & 1) lrank[k >> 1] |= r << 16; else lrank[k >> 1] = r;

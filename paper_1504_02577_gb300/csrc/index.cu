@@ -139,6 +139,9 @@ __global__ void __launch_bounds__(IX_T, 2) scatter_kernel(Src s, int shift, int 
     uint32_t key[IX_ROUNDS];
     uint32_t lrank[IX_ROUNDS / 2];
     uint32_t okmask = 0;
+    // this tile's global start of digit threadIdx.x (final before the launch):
+    // loaded now, so its latency overlaps the item loads and the ranking
+    const long long my_off = (int)threadIdx.x < radix ? offs[(int64_t)threadIdx.x * ntiles + blockIdx.x] : 0;
 #pragma unroll
     for (int k = 0; k < IX_ROUNDS; ++k) key[k] = (uint32_t)load_raw(s, base + k * 32 + lane);   // loads in flight
 #pragma unroll
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(IX_T, 2) scatter_kernel(Src s, int shift, int 
     unsigned tot = 0;
     const int d2 = threadIdx.x;               // IX_T >= MAX_RADIX: one digit per thread
     if (d2 < radix) {
-        toff[d2] = offs[(int64_t)d2 * ntiles + blockIdx.x];
+        toff[d2] = my_off;
         for (int ww = 0; ww < IX_WARPS; ++ww) {
             unsigned c = wc[ww][d2];
             wc[ww][d2] = tot;

@@ -22,12 +22,14 @@ constexpr int IX_WARPS = IX_T / 32;
 constexpr int IX_ROUNDS = 12;              // 32-item rounds per warp
 constexpr int IX_TILE = IX_T * IX_ROUNDS;  // 6144 items per tile
 constexpr int MAX_RADIX = 512;
+constexpr int MAX_RB = 9;                  // log2(MAX_RADIX)
 
 struct Src {
     // pass 0 source
     const int32_t* rows;
     int64_t R;
     int L, stride;
+    int lstride;        // log2(stride): row of item i = i >> lstride
     // later-pass source
     const int32_t* keys;
     const int32_t* vals;
@@ -77,12 +79,12 @@ __device__ __forceinline__ uint32_t long_row_repeats(const Src& s, int64_t wbase
     uint32_t rep = 0;
 #pragma unroll
     for (int k = 1; k < IX_ROUNDS; ++k) {
-        const int64_t row = (wbase + k * 32) / s.stride;
+        const int64_t row = (wbase + k * 32) >> s.lstride;
         bool d = false;
 #pragma unroll
         for (int o = 1; o <= 3; ++o) {
             if (k - o < 0) continue;
-            if ((wbase + (k - o) * 32) / s.stride != row) continue;     // warp-uniform
+            if (((wbase + (k - o) * 32) >> s.lstride) != row) continue;  // warp-uniform
 #pragma unroll 8
             for (int sl = 0; sl < 32; ++sl) d |= __shfl_sync(0xffffffffu, x[k - o], sl) == x[k];
         }
@@ -162,7 +164,9 @@ __global__ void __launch_bounds__(IX_T, 2) scatter_kernel(Src s, int shift, int 
         bool ok = (okmask >> k) & 1u;
         uint32_t d = ok ? ((key[k] >> shift) & (radix - 1)) : 0xffffffffu;
         unsigned peers = __ballot_sync(0xffffffffu, ok);
-        for (int b = 0; b < rb; ++b) {                     // warp-uniform
+#pragma unroll
+        for (int b = 0; b < MAX_RB; ++b) {
+            if (b >= rb) break;                            // warp-uniform
             const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
             peers &= ((d >> b) & 1u) ? bb : ~bb;
         }
@@ -213,7 +217,7 @@ __global__ void __launch_bounds__(IX_T, 2) scatter_kernel(Src s, int shift, int 
 #pragma unroll
     for (int k = 0; k < IX_ROUNDS; ++k) {
         const int64_t i = base + k * 32 + lane;
-        val[k] = s.first ? (int32_t)(uint32_t)(s.r0 + i / s.stride) : (((okmask >> k) & 1u) ? __ldg(s.vals + i) : 0);
+        val[k] = s.first ? (int32_t)(uint32_t)(s.r0 + (i >> s.lstride)) : (((okmask >> k) & 1u) ? __ldg(s.vals + i) : 0);
     }
 #pragma unroll
     for (int k = 0; k < IX_ROUNDS; ++k) {
@@ -481,6 +485,7 @@ extern "C" panther_status panther_build_index(panther_ctx* ctx, const panther_pa
     src.R = p->R;
     src.L = p->L;
     src.stride = p->stride;
+    src.lstride = 31 - __builtin_clz((unsigned)p->stride);
     src.first = 1;
     src.r0 = 0;
     cudaError_t e;
@@ -643,6 +648,7 @@ extern "C" panther_status panther_build_index_noalloc(panther_ctx* ctx, const pa
     src.R = p->R;
     src.L = p->L;
     src.stride = p->stride;
+    src.lstride = 31 - __builtin_clz((unsigned)p->stride);
     src.first = 1;
     int32_t *ik = nullptr, *ok = kA, *ov = vA;
     int64_t count = 0;

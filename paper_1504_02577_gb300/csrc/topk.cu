@@ -418,10 +418,12 @@ __device__ __forceinline__ bool insert_path(const PathsRef& P, uint32_t r, int32
 constexpr int LANE_NP = 6;
 constexpr int LANE_K = 16;
 
+// does one of the first LP entries of row r hold u?
+template <int LP>
 __device__ __forceinline__ bool row_has(const int32_t (&r)[8], int32_t u) {
     bool h = false;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) h |= (r[j] == u);
+    for (int j = 0; j < LP; ++j) h |= (r[j] == u);
     return h;
 }
 
@@ -441,7 +443,9 @@ struct LaneScore {
     static __device__ __forceinline__ uint32_t count(T s) { return NARROW ? (uint32_t)s >> 29 : (uint32_t)((uint64_t)s >> 32); }
 };
 
-template <bool NARROW>
+// LP: the row positions compared (T+1 = 6, the paper's T = 5, or all 8 with
+// the positions past T+1 masked); KP: the length of the running list (k <= KP)
+template <bool NARROW, int LP, int KP>
 __global__ void __launch_bounds__(256, NARROW ? 3 : 2) lane_kernel(PathsRef P, const int32_t* __restrict__ queries,
                                                    const int32_t* __restrict__ list, const int* __restrict__ count,
                                                    int slot, OutRef o) {
@@ -486,27 +490,27 @@ __global__ void __launch_bounds__(256, NARROW ? 3 : 2) lane_kernel(PathsRef P, c
             na = P.off[nv];
             nb = P.off[nv + 1];
         }
-        T best[LANE_K];
+        T best[KP];
 #pragma unroll
-        for (int t = 0; t < LANE_K; ++t) best[t] = 0;
+        for (int t = 0; t < KP; ++t) best[t] = 0;
 #pragma unroll
         for (int i = 0; i < LANE_NP; ++i) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < LP; ++j) {
                 const int32_t u = row[i][j];
                 bool first = u >= 0 && u != v;
 #pragma unroll
                 for (int jj = 0; jj < j; ++jj) first &= row[i][jj] != u;
 #pragma unroll
-                for (int ii = 0; ii < i; ++ii) first &= !row_has(row[ii], u);
+                for (int ii = 0; ii < i; ++ii) first &= !row_has<LP>(row[ii], u);
                 if (first) {
                     uint32_t c = 1;
 #pragma unroll
-                    for (int ii = i + 1; ii < LANE_NP; ++ii) c += row_has(row[ii], u) ? 1u : 0u;
+                    for (int ii = i + 1; ii < LANE_NP; ++ii) c += row_has<LP>(row[ii], u) ? 1u : 0u;
                     T sc = LS::make(c, u);
                     // sorted insertion (descending)
 #pragma unroll
-                    for (int t = 0; t < LANE_K; ++t) {
+                    for (int t = 0; t < KP; ++t) {
                         T hi = best[t] > sc ? best[t] : sc;
                         T lo = best[t] > sc ? sc : best[t];
                         best[t] = hi;
@@ -516,7 +520,7 @@ __global__ void __launch_bounds__(256, NARROW ? 3 : 2) lane_kernel(PathsRef P, c
             }
         }
 #pragma unroll
-        for (int t = 0; t < LANE_K; ++t) {
+        for (int t = 0; t < KP; ++t) {
             if (t < o.k) {
                 const T sc = best[t];
                 if (o.ids) o.ids[qi * o.k + t] = sc ? LS::id(sc) : -1;
@@ -1617,6 +1621,22 @@ uint32_t pow2_at_least(int64_t x, uint32_t lo = 1024) {
 
 }  // namespace
 
+// the lane kernel instantiation for this batch: 32-bit scores when ids are
+// below 2^29, exactly T+1 = 6 row positions at the paper's T = 5, a 12-entry
+// list when k <= 12
+static void launch_lane(bool narrow, bool l6, bool k12, unsigned blocks, cudaStream_t s, const PathsRef& P,
+                        const int32_t* queries, const int32_t* list, const int* counts, const OutRef& o) {
+#define PANTHER_LANE(NW, LPV, KPV) lane_kernel<NW, LPV, KPV><<<blocks, 256, 0, s>>>(P, queries, list, counts, 5, o)
+    if (narrow) {
+        if (l6) { if (k12) PANTHER_LANE(true, 6, 12); else PANTHER_LANE(true, 6, LANE_K); }
+        else { if (k12) PANTHER_LANE(true, 8, 12); else PANTHER_LANE(true, 8, LANE_K); }
+    } else {
+        if (l6) { if (k12) PANTHER_LANE(false, 6, 12); else PANTHER_LANE(false, 6, LANE_K); }
+        else { if (k12) PANTHER_LANE(false, 8, 12); else PANTHER_LANE(false, 8, LANE_K); }
+    }
+#undef PANTHER_LANE
+}
+
 // ------------------------------------------------------------ host side ---
 constexpr int BIG_T = 1024;
 constexpr uint32_t BIG_SLOTS = 24576;
@@ -1990,10 +2010,8 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
         PCK(ctx, cudaStreamWaitEvent(s1, ctx->fork, 0));
     }
     if (lane_ok) {
-        if (ix->n <= (int64_t(1) << 29))
-            lane_kernel<true><<<(unsigned)(ctx->num_sms * 8), 256, 0, s0>>>(P, queries, lists + 3 * q, counts, 5, o);
-        else
-            lane_kernel<false><<<(unsigned)(ctx->num_sms * 8), 256, 0, s0>>>(P, queries, lists + 3 * q, counts, 5, o);
+        launch_lane(ix->n <= (int64_t(1) << 29), P.L == 6, k <= 12, (unsigned)(ctx->num_sms * 8), s0, P, queries,
+                    lists + 3 * q, counts, o);
         ctx->launches++;
     }
     if (group_max >= 16) {

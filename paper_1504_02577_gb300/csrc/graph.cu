@@ -714,9 +714,10 @@ constexpr int SMALL_DEG = 16;
 __global__ void __launch_bounds__(256) alias_thread_kernel(const uint4* __restrict__ vrec, int64_t n,
                                                            const int32_t* __restrict__ col,
                                                            const uint32_t* __restrict__ w, uint4* tab) {
-    // the worklists live in shared memory, one column per thread (no local
-    // memory, no bank conflicts)
+    // the worklists and the row's columns live in shared memory, one column
+    // per thread (no local memory, no bank conflicts)
     __shared__ uint64_t qs[SMALL_DEG][256];
+    __shared__ int32_t cs[SMALL_DEG][256];
     __shared__ int8_t sms[SMALL_DEG][256], lgs[SMALL_DEG][256];
     const int t = threadIdx.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
@@ -726,30 +727,42 @@ __global__ void __launch_bounds__(256) alias_thread_kernel(const uint4* __restri
         const int64_t start = r.x;
         const uint64_t S = (uint64_t)r.z | ((uint64_t)r.w << 32);
         auto q = [&](int j) -> uint64_t& { return qs[j][t]; };
+        auto c = [&](int j) -> int32_t& { return cs[j][t]; };
         auto sm = [&](int j) -> int8_t& { return sms[j][t]; };
         auto lg = [&](int j) -> int8_t& { return lgs[j][t]; };
+        // the row's weights and columns: every load issued before the first use
+        uint32_t wr[SMALL_DEG];
+        int32_t cr[SMALL_DEG];
+#pragma unroll
+        for (int j = 0; j < SMALL_DEG; ++j)
+            if (j < d) {
+                wr[j] = w[start + j];
+                cr[j] = col[start + j];
+            }
         int ns = 0, nl = 0;
-        for (int j = 0; j < d; ++j) {
-            const uint64_t qj = (uint64_t)w[start + j] * (uint64_t)d;
-            q(j) = qj;
-            if (qj < S) sm(ns++) = (int8_t)j; else lg(nl++) = (int8_t)j;
-        }
+#pragma unroll
+        for (int j = 0; j < SMALL_DEG; ++j)
+            if (j < d) {
+                const uint64_t qj = (uint64_t)wr[j] * (uint64_t)d;
+                q(j) = qj;
+                c(j) = cr[j];
+                if (qj < S) sm(ns++) = (int8_t)j; else lg(nl++) = (int8_t)j;
+            }
         while (ns > 0 && nl > 0) {
             const int a = sm(--ns), b = lg(--nl);
             const uint64_t qa = q(a);
-            tab[start + a] = make_uint4((uint32_t)qa, (uint32_t)(qa >> 32), (uint32_t)col[start + a],
-                                        (uint32_t)col[start + b]);
+            tab[start + a] = make_uint4((uint32_t)qa, (uint32_t)(qa >> 32), (uint32_t)c(a), (uint32_t)c(b));
             const uint64_t qb = q(b) - (S - qa);
             q(b) = qb;
             if (qb < S) sm(ns++) = (int8_t)b; else lg(nl++) = (int8_t)b;
         }
         while (nl > 0) {
             const int b = lg(--nl);
-            tab[start + b] = make_uint4((uint32_t)S, (uint32_t)(S >> 32), (uint32_t)col[start + b], (uint32_t)col[start + b]);
+            tab[start + b] = make_uint4((uint32_t)S, (uint32_t)(S >> 32), (uint32_t)c(b), (uint32_t)c(b));
         }
         while (ns > 0) {
             const int a = sm(--ns);
-            tab[start + a] = make_uint4((uint32_t)S, (uint32_t)(S >> 32), (uint32_t)col[start + a], (uint32_t)col[start + a]);
+            tab[start + a] = make_uint4((uint32_t)S, (uint32_t)(S >> 32), (uint32_t)c(a), (uint32_t)c(a));
         }
     }
 }

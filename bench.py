@@ -78,22 +78,22 @@ def _src_hash(*files):
 # unchanged (SHA-256 of the files), else reported as null. The capture and its
 # command are in profiles/.
 NCU_TRAFFIC = {
-    "tables": {"bytes_5M": 4358919680, "sources": {
-        "paper_1504_02577_gb300/csrc/graph.cu": "2e1c84b66c7ae7bb7953cb51285365d9aa6479fe7d4feb4baf6db03417cee5a6",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "6db187a84a4c2dcdac30fb3fe32dd3fcffd47b6c903c0ac4d1237a48a2c7f72e",
+    "tables": {"bytes_5M": 4315955456, "sources": {
+        "paper_1504_02577_gb300/csrc/graph.cu": "b6931b5c408e955ddf424f6cfd8c6481c3034578e74a627fbdca5f15e3f9914c",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "3cae532383c14b26b3e266aa306722dccf3f619429e5d83d1545da44e042d3f1",
     }},
-    "sample": {"bytes_5M": 8120442880, "sources": {
-        "paper_1504_02577_gb300/csrc/sample.cu": "3ae257be8d6b2d9726f406e2f7e6bc67a92c8ee993f6cb3d6a67728924becbf3",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "6db187a84a4c2dcdac30fb3fe32dd3fcffd47b6c903c0ac4d1237a48a2c7f72e",
+    "sample": {"bytes_5M": 8111835136, "sources": {
+        "paper_1504_02577_gb300/csrc/sample.cu": "f81ab32e35641e9aecf9ba28871b1e5fbad1e23fb12e14c96b8c41ea743d3061",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "3cae532383c14b26b3e266aa306722dccf3f619429e5d83d1545da44e042d3f1",
     }},
-    "index": {"bytes_5M": 3670648320, "sources": {
-        "paper_1504_02577_gb300/csrc/index.cu": "2de8cd0b817d605fbc981a0a8b6486428bb0341e105c88205ac1a34a63041d90",
-        "paper_1504_02577_gb300/csrc/capi.cu": "9f7d85e2973fdcf982d51bc9d1f4425bd24f4668696f03bde2d3ba7559a58443",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "6db187a84a4c2dcdac30fb3fe32dd3fcffd47b6c903c0ac4d1237a48a2c7f72e",
+    "index": {"bytes_5M": 3645406976, "sources": {
+        "paper_1504_02577_gb300/csrc/index.cu": "fa0f5dab980d0de4713e0c3156ace87a85d808fb2021d8f29faa0242470ea345",
+        "paper_1504_02577_gb300/csrc/capi.cu": "597a6e25fa600a1f563883e2c94d998c5ec6145ce2ced5b02c85790390861551",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "3cae532383c14b26b3e266aa306722dccf3f619429e5d83d1545da44e042d3f1",
     }},
-    "topk": {"bytes_5M": 8254882816, "sources": {
-        "paper_1504_02577_gb300/csrc/topk.cu": "af525e4fd7a3e6556b418d6807ea765c7e977f81f7829174b351f01ac1d2b5fd",
-        "paper_1504_02577_gb300/csrc/internal.cuh": "6db187a84a4c2dcdac30fb3fe32dd3fcffd47b6c903c0ac4d1237a48a2c7f72e",
+    "topk": {"bytes_5M": 7911721984, "sources": {
+        "paper_1504_02577_gb300/csrc/topk.cu": "20a0fbd516dfd6587bbfcc13c2c9a1235fbcab028d04242971bceed7d3810c82",
+        "paper_1504_02577_gb300/csrc/internal.cuh": "3cae532383c14b26b3e266aa306722dccf3f619429e5d83d1545da44e042d3f1",
     }},
 }
 

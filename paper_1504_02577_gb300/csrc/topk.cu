@@ -683,6 +683,9 @@ __global__ void __launch_bounds__(256) group_kernel(PathsRef P, const int32_t* _
     const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
     constexpr int UB = group_ub(G), RB = group_rb(G);
     constexpr uint32_t UMASK = (1u << UB) - 1u;
+    // G >= 16: the scores above c* of each group, gathered for ranking
+    __shared__ uint32_t gbuf[G >= 16 ? 256 / G : 1][KMAX];
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
     for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;; it += ngroups) {
         const bool active = it < n;
         if (!__any_sync(0xffffffffu, active)) break;   // warp-uniform: the whole warp shuffles together
@@ -754,19 +757,91 @@ __global__ void __launch_bounds__(256) group_kernel(PathsRef P, const int32_t* _
             const uint32_t u = x[r] >> RB;
             sc[r] = (last && x[r] != 0xffffffffu) ? (cnt << UB) | (UMASK - u) : 0u;
         }
-        group_sort<G, false>(sc, gl);
-        if (active) {
+        if constexpr (G >= 16) {
+            // Ranks without a second sort. The run ends lie in ascending u,
+            // the order that breaks ties. c* = the k-th largest count (1 when
+            // fewer than k ends have a count of 2 or more); the g < k ends
+            // above c* are gathered and ranked by comparison, the ends at c*
+            // take ranks g, g+1, ... in their order.
+            auto at_least = [&](uint32_t c) {
+                int s = 0;
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+                    s += __popc(__ballot_sync(0xffffffffu, sc[r] != 0u && (sc[r] >> UB) >= c) & gmask);
+                return s;
+            };
+            uint32_t cstar = 1;
+            if (__any_sync(0xffffffffu, at_least(2) >= o.k)) {            // warp-uniform
+                constexpr int CB = G == 32 ? 6 : 5;                         // counts <= G
+                uint32_t cs = 0;
+#pragma unroll
+                for (int bit = CB - 1; bit >= 0; --bit)
+                    if (at_least(cs | (1u << bit)) >= o.k) cs |= 1u << bit;
+                cstar = cs > 1u ? cs : 1u;
+            }
+            // exclusive prefix over the group's lanes of a per-lane count
+            auto group_excl = [&](uint32_t v) {
+                uint32_t x = v;
+#pragma unroll
+                for (int d = 1; d < G; d <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d, G);
+                    if ((int)gl >= d) x += y;
+                }
+                return x - v;
+            };
+            uint32_t ngt = 0, neq = 0;
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
-                const int e = (int)gl * 8 + r;
-                if (e < o.k) {
-                    if (o.ids) o.ids[qi * o.k + e] = sc[r] ? (int32_t)(UMASK - (sc[r] & UMASK)) : -1;
-                    o.cnt[qi * o.k + e] = sc[r] >> UB;
+                const uint32_t c = sc[r] >> UB;
+                ngt += (sc[r] != 0u && c > cstar) ? 1u : 0u;
+                neq += (sc[r] != 0u && c == cstar) ? 1u : 0u;
+            }
+            uint32_t pgt = group_excl(ngt), peq = group_excl(neq);
+            const uint32_t g = __shfl_sync(0xffffffffu, pgt + ngt, G - 1, G);      // ends above c*
+            const uint32_t tot = g + __shfl_sync(0xffffffffu, peq + neq, G - 1, G);
+            uint32_t* buf = gbuf[(threadIdx.x & 255) / G];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const uint32_t c = sc[r] >> UB;
+                if (sc[r] != 0u && c > cstar) buf[pgt++] = sc[r];          // g < k <= KMAX entries
+                if (active && sc[r] != 0u && c == cstar) {
+                    const uint32_t rank = g + peq++;
+                    if ((int)rank < o.k) {
+                        if (o.ids) o.ids[qi * o.k + rank] = (int32_t)(UMASK - (sc[r] & UMASK));
+                        o.cnt[qi * o.k + rank] = c;
+                    }
                 }
             }
-            for (int e = 8 * G + (int)gl; e < o.k; e += G) {   // k beyond the group's 8G ranks: padding
-                if (o.ids) o.ids[qi * o.k + e] = -1;
-                o.cnt[qi * o.k + e] = 0;
+            __syncwarp();
+            if (active) {
+                for (uint32_t i = gl; i < g; i += G) {
+                    const uint32_t s = buf[i];
+                    uint32_t rank = 0;
+                    for (uint32_t j = 0; j < g; ++j) rank += buf[j] > s ? 1u : 0u;
+                    if (o.ids) o.ids[qi * o.k + rank] = (int32_t)(UMASK - (s & UMASK));
+                    o.cnt[qi * o.k + rank] = s >> UB;
+                }
+                for (int e = (int)tot + (int)gl; e < o.k; e += G) {              // fewer than k ends: padding
+                    if (o.ids) o.ids[qi * o.k + e] = -1;
+                    o.cnt[qi * o.k + e] = 0;
+                }
+            }
+            __syncwarp();
+        } else {
+            group_sort<G, false>(sc, gl);
+            if (active) {
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int e = (int)gl * 8 + r;
+                    if (e < o.k) {
+                        if (o.ids) o.ids[qi * o.k + e] = sc[r] ? (int32_t)(UMASK - (sc[r] & UMASK)) : -1;
+                        o.cnt[qi * o.k + e] = sc[r] >> UB;
+                    }
+                }
+                for (int e = 8 * G + (int)gl; e < o.k; e += G) {   // k beyond the group's 8G ranks: padding
+                    if (o.ids) o.ids[qi * o.k + e] = -1;
+                    o.cnt[qi * o.k + e] = 0;
+                }
             }
         }
     }

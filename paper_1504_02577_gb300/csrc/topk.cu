@@ -1713,7 +1713,7 @@ static void launch_lane(bool narrow, bool l6, bool k12, unsigned blocks, cudaStr
 }
 
 // ------------------------------------------------------------ host side ---
-constexpr int BIG_T = 1024;
+constexpr int BIG_T = 512;
 constexpr uint32_t BIG_SLOTS = 24576;
 constexpr size_t BIG_SMEM = (size_t)BIG_SLOTS * 8 + (size_t)(BIG_T / 32) * KMAX * 8;
 

@@ -123,12 +123,13 @@ def _hub_rows_graph():
     return synth.graph_from_edges(n, edges, ws)
 
 
-_SHORT_DEGS = [17, 24, 32, 33, 50, 64, 65, 100, 128, 129]
+_SHORT_DEGS = [17, 24, 32, 33, 50, 64, 65, 100, 128, 129, 511, 512, 513, 1000, 2048]
 
 
 def _short_rows_graph():
     # rows on both sides of the 8/16/32-lane and warp boundaries (32, 64, 128)
-    # with equal, random, one dominant, and log-uniform weights
+    # and across the warp rows up to the longest (2048), with equal, random,
+    # one dominant, and log-uniform weights
     n = 3000
     rng = np.random.default_rng(13)
     edges, ws = [], []

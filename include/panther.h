@@ -243,9 +243,10 @@ PANTHER_API panther_status panther_index_view(const panther_index* ix, const int
  * largest by (cnt desc, u asc). Writes out_ids int32[q][k] and
  * out_counts uint32[q][k] (similarity S_RP(v,u) = cnt / R).
  *   q >= 0 (q = 0 is a no-op), 1 <= k <= 128, queries in [0, n). With
- *   k <= 64 every tier runs; with 64 < k <= 128 every query is counted in a
- *   per-query device table and selected with 128-entry lists (slower, same
- *   results); the PLAIN form then runs that path once per query.
+ *   k <= 64 every tier runs; with 64 < k <= 128 queries of up to 32 paths
+ *   stay in the group tiers and every other query is counted in a per-query
+ *   device table and selected with 128-entry lists (slower, same results);
+ *   the PLAIN form then runs that path once per query.
  *   flags: PANTHER_TOPK_BATCHED or PANTHER_TOPK_PLAIN, optionally
  *          | PANTHER_IO_HOST (queries/outputs in host memory; the call then
  *          synchronises; batches of 4M queries or more run in four chunks

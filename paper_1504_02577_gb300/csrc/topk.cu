@@ -683,8 +683,9 @@ __global__ void __launch_bounds__(256) group_kernel(PathsRef P, const int32_t* _
     const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
     constexpr int UB = group_ub(G), RB = group_rb(G);
     constexpr uint32_t UMASK = (1u << UB) - 1u;
-    // G >= 16: the scores above c* of each group, gathered for ranking
-    __shared__ uint32_t gbuf[G >= 16 ? 256 / G : 1][KMAX];
+    // G >= 16: the scores above c* of each group (fewer than k <= 128),
+    // gathered for ranking
+    __shared__ uint32_t gbuf[G >= 16 ? 256 / G : 1][KMAX4];
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
     for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;; it += ngroups) {
         const bool active = it < n;
@@ -803,7 +804,7 @@ __global__ void __launch_bounds__(256) group_kernel(PathsRef P, const int32_t* _
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
                 const uint32_t c = sc[r] >> UB;
-                if (sc[r] != 0u && c > cstar) buf[pgt++] = sc[r];          // g < k <= KMAX entries
+                if (sc[r] != 0u && c > cstar) buf[pgt++] = sc[r];          // g < k <= KMAX4 entries
                 if (active && sc[r] != 0u && c == cstar) {
                     const uint32_t rank = g + peq++;
                     if ((int)rank < o.k) {
@@ -883,11 +884,11 @@ __global__ void __launch_bounds__(256) classify_kernel(const int32_t* __restrict
                 int64_t cap = np * (P.L - 1);
                 if (cap > P.n - 1) cap = P.n - 1;
                 if (cap > 0) {
-                    if (all_hub) t = 2;          // k > 64: every query in a device table
-                    else if (lane_ok && np <= LANE_NP) t = 3;
+                    if (lane_ok && np <= LANE_NP) t = 3;
                     else if (np <= 8 && np <= group_max) t = 4;
                     else if (np <= 16 && np <= group_max) t = 5;
                     else if (np <= 32 && np <= group_max) t = 6;
+                    else if (all_hub) t = 2;     // k > 64: the rest in device tables
                     else if (np > CTA_MAX_NP) t = 2;
                     else t = (cap <= WCAP && np <= WARP_MAX_NP) ? 0 : (cap <= ccap ? 1 : (cap <= ccap_big ? 7 : 2));
                 }
@@ -2067,7 +2068,8 @@ panther_status topk_run(panther_ctx* ctx, const panther_index* ix, const panther
                 counts};
     const bool all_hub = k > KMAX;                      // 64 < k <= 128: device tables only
     // largest |P_v| the group tiers take: ids must fit below 2^group_ub(G)
-    const int group_max = (p->stride != 8 || all_hub) ? 0
+    // (any k: G = 8 ranks at most 56 candidates, larger groups rank directly)
+    const int group_max = p->stride != 8 ? 0
                           : ix->n <= (int64_t(1) << group_ub(32)) ? 32
                           : ix->n <= (int64_t(1) << group_ub(16)) ? 16 : 0;
     const bool lane_ok = p->stride == 8 && k <= LANE_K;

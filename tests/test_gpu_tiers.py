@@ -204,15 +204,24 @@ def test_long_path_revisits_and_limits(pk):
 
 @pytest.mark.parametrize("k", [65, 100, 128])
 def test_topk_k_above_64(pk, small, k):
-    # 64 < k <= 128: every query counted in a device table, 128-entry lists;
-    # all 2,000 vertices (many with fewer than k candidates: padding), the
-    # plain form on a subset, and a long-path case
+    # 64 < k <= 128: queries of up to 32 paths stay in the group tiers, every
+    # other query is counted in a device table with 128-entry lists; all
+    # 2,000 vertices (many with fewer than k candidates: padding), a batch of
+    # short path lists that the group tiers take, the plain form on a subset,
+    # and a long-path case
     g, ref, o = small
     q = np.arange(g.n, dtype=np.int32)
     ids, cnt, st = _topk_routed(pk, g, 200_000, 5, 1, q, k, 0, 0)
     rid, rcnt = o.topk_many(q, k, threads=THREADS)
     assert np.array_equal(ids, rid) and np.array_equal(cnt, rcnt)
-    assert st[7] > 1000 and st[1] == st[2] == st[3] == st[4] == 0
+    assert st[7] > 1000 and st[1] == st[3] == st[4] == 0 and st[7] >= st[5]
+    R3 = 5_000                                        # about 15 paths per vertex
+    ref3 = oracle.sample_paths(g, 4, R3, 5, oracle.ALIAS, threads=THREADS)
+    o3 = oracle.Oracle(g.n, ref3)
+    ids3, cnt3, st3 = _topk_routed(pk, g, R3, 5, 4, q, k, 0, 0)
+    rid3, rcnt3 = o3.topk_many(q, k, threads=THREADS)
+    assert np.array_equal(ids3, rid3) and np.array_equal(cnt3, rcnt3)
+    assert st3[2] > 1000 and st3[1] == st3[3] == st3[4] == 0
     with pk.Panther(0) as P:
         P.build_graph(g.row_ptr, g.col, g.w, pk.MODE_ALIAS)
         P.sample_paths(1, 200_000, 5, pk.MODE_ALIAS)

@@ -166,10 +166,11 @@ PANTHER_API panther_status panther_build_graph(panther_ctx* ctx, int64_t n, int6
  *   R in [1, 2^32-1], T in [1, 127], mode PREFIX, ALIAS or UNWEIGHTED (the
  *   graph must have been built with that mode). The index stores path ids as
  *   uint32; at 32 B of row and 4 B of index per vertex of each path, 2^32
- *   paths already take more than one GPU's memory.
+ *   paths already take more than one GPU's memory; R >= 2^32 returns
+ *   EOVERFLOW.
  * Rows live on the device as int32[R][stride], stride = 8, 16, 32, 64 or 128
  * (the smallest that holds T+1); entries past T+1 are -1.
- * Errors: EINVAL, ENOMEM, ECUDA. */
+ * Errors: EINVAL, EOVERFLOW, ENOMEM, ECUDA. */
 PANTHER_API panther_status panther_sample_paths(panther_ctx* ctx, const panther_graph* g, uint64_t seed,
                                     int64_t R, int T, int mode, panther_paths** out);
 

@@ -206,7 +206,8 @@ extern "C" panther_status panther_sample_paths_range(panther_ctx* ctx, const pan
                                                      int64_t r0, int64_t R, int T, int mode, panther_paths** out) {
     if (!ctx || !g || !out) return PANTHER_EINVAL;
     *out = nullptr;
-    if (R < 1 || R > 0xffffffffLL) return set_err(ctx, PANTHER_EINVAL, "R must be in [1, 2^32-1]");
+    if (R < 1) return set_err(ctx, PANTHER_EINVAL, "R must be at least 1");
+    if (R > 0xffffffffLL) return set_err(ctx, PANTHER_EOVERFLOW, "R exceeds the 32-bit path ids (at most 2^32-1 paths)");
     if (r0 < 0 || r0 > INT64_MAX - R) return set_err(ctx, PANTHER_EINVAL, "r0 must be >= 0 and r0 + R < 2^63");
     if (T < 1 || T > MAX_T) return set_err(ctx, PANTHER_EINVAL, "T must be in [1, 127]");
     if (mode != PANTHER_MODE_PREFIX && mode != PANTHER_MODE_ALIAS && mode != PANTHER_MODE_UNWEIGHTED)

@@ -13,7 +13,9 @@ accumulated, nothing stored) and draws single paths by id (oracle.paths_at).
 An index list is proven equal to P_v by three facts: it ascends strictly,
 every listed path holds v, and its length is |P_v|.
 
-Device memory: about 110 GB at the peak (70 GB of rows, two 17 GB indexes).
+Device memory: 70 GB of rows and two 17 GB indexes, plus the index build's
+temporary buffers (the build goes to chunks of paths when they do not fit):
+the tests want about 150 GB free.
 """
 import os
 
@@ -63,7 +65,7 @@ def test_r_above_2_32_is_refused(pk):
         P.build_graph(g.row_ptr, g.col, g.w, pk.MODE_ALIAS)
         with pytest.raises(pk.PantherError) as ei:
             P.sample_paths(1, 2**32, 3, pk.MODE_ALIAS)
-        assert ei.value.code == pk.EINVAL
+        assert ei.value.code == pk.EOVERFLOW
 
 
 def test_two_vertex_graph_closed_form(pk):
